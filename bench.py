@@ -1,0 +1,449 @@
+#!/usr/bin/env python3
+"""Benchmark of the eager sparse BM25 hot path on one GB300.
+
+One step = the whole hot path over one batch of synthetic input:
+index build from device-resident tokens (|D|, TF, DF, IDF, S0, CSC of
+S - S0) followed by batched top-k retrieval of the whole query batch.
+`value` = queries per second of that step.  Beside it the JSON line reports
+retrieval alone on a resident index (batched, and one query per launch with
+p50/p99 latency), the build alone (docs/s), the end-to-end rate through the
+host-buffer entry points, the roofline of the dominant kernel and the CPU
+oracle's rate on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2407_03618_gb300 import synth  # noqa: E402
+
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="1m", choices=sorted(synth.WORKLOADS))
+    p.add_argument("--variant", default="lucene", choices=list(synth.ALL_VARIANTS))
+    p.add_argument("--k", type=int, default=10)
+    p.add_argument("--plain-queries", type=int, default=1000)
+    p.add_argument("--cpu-sample-queries", type=int, default=48)
+    p.add_argument("--no-extras", action="store_true",
+                   help="only the timed steps (used for profiler runs)")
+    return p.parse_args()
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ------------------------------------------------------------ clocks ------
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------- CPU oracle -------
+
+def oracle_rate(corpus, queries, variant, k, n_sample, threads, params):
+    """Oracle (FP64 C, lazy exhaustive) on a bounded sample: the full build,
+    then top-k for n_sample queries on `threads` threads; the rate is
+    extrapolated to the whole step (build + every query of the batch)."""
+    import oracle
+    t0 = time.perf_counter()
+    orc = oracle.build(corpus.tokens, corpus.doc_offsets, corpus.vocab, oracle.VARIANTS[variant],
+                       params["k1"], params["b"], params["delta"])
+    t_build = time.perf_counter() - t0
+    idx = np.linspace(0, queries.n_queries - 1, n_sample).astype(np.int64)
+    sub = queries.subset(idx)
+    t0 = time.perf_counter()
+    oracle.topk(orc, sub.tokens, sub.offsets, k, n_threads=threads)
+    t_q = (time.perf_counter() - t0) / n_sample
+    step = t_build + t_q * queries.n_queries
+    return orc, {"value": queries.n_queries / step, "unit": "queries/s", "cores": threads,
+                 "kind": "oracle",
+                 "sample": (f"oracle build of the full corpus ({t_build:.2f} s, 1 thread) + "
+                            f"lazy exhaustive top-{k} of {n_sample} evenly spaced queries on "
+                            f"{threads} threads ({t_q * 1e3:.2f} ms/query), extrapolated to "
+                            f"build + {queries.n_queries} queries"),
+                 "build_s": t_build, "ms_per_query": t_q * 1e3}
+
+
+def reference_arm(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    w = synth.WORKLOADS[args.workload]
+    corpus, queries = w.corpus(), w.queries()
+    threads = os.cpu_count() or 1
+    import oracle
+    t0 = time.perf_counter()
+    orc = oracle.build(corpus.tokens, corpus.doc_offsets, corpus.vocab,
+                       oracle.VARIANTS[args.variant], w.params["k1"], w.params["b"],
+                       w.params["delta"])
+    t_build = time.perf_counter() - t0
+    n_sample = max(1, args.cpu_sample_queries)
+    rng = np.random.default_rng(7)
+    times = []
+    for step in range(args.warmup + args.steps):
+        idx = rng.integers(0, queries.n_queries, n_sample)
+        sub = queries.subset(idx)
+        t0 = time.perf_counter()
+        oracle.topk(orc, sub.tokens, sub.offsets, args.k, n_threads=threads)
+        if step >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t_q = sum(times) / (len(times) * n_sample)
+    step_s = t_build + t_q * queries.n_queries
+    value = queries.n_queries / step_s
+    line = {"impl": "reference", "metric": f"queries/s @k={args.k}", "value": value,
+            "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {**w.describe(), "variant": args.variant, "k": args.k},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": threads,
+                             "kind": "oracle",
+                             "sample": (f"oracle build of the full corpus ({t_build:.2f} s, "
+                                        f"1 thread) once; each step = lazy exhaustive top-"
+                                        f"{args.k} of {n_sample} random queries on {threads} "
+                                        f"threads; rate extrapolated to build + "
+                                        f"{queries.n_queries} queries")},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------ GPU arm -----
+
+def kernel_bytes(name, ctx):
+    """Algorithmic bytes per launch of the kernels a roofline is quoted for."""
+    if name == "k_tile_topk":
+        return ctx["retrieval_bytes"]
+    if name == "k_radix_downsweep":
+        return 16 * ctx["n_tokens"]  # read key + doc, write key + doc, 4 B each
+    if name == "k_radix_upsweep":
+        return 4 * ctx["n_tokens"]
+    if name == "k_score":
+        return 20 * ctx["nnz"]  # run start x2, term, doc in; tf, score out (4 B each)
+    return None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2407_03618_gb300 import bm25
+
+    w = synth.WORKLOADS[args.workload]
+    prm = w.params
+    corpus = w.corpus()
+    queries = w.queries(seed=1 + rank)  # each rank answers its own batch (weak scaling)
+    k = args.k
+    nq = queries.n_queries
+
+    tok = torch.from_numpy(corpus.tokens).to(dev)
+    off = torch.from_numpy(corpus.doc_offsets).to(dev)
+    qt = torch.from_numpy(queries.tokens).to(dev)
+    qo = torch.from_numpy(queries.offsets).to(dev)
+    ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
+    sc = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ix = bm25.Index.build(tok, off, corpus.vocab, args.variant, prm["k1"], prm["b"],
+                              prm["delta"])
+        ix.retrieve(qt, qo, k, out=(ids, sc))
+        ix.close()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = str(local)
+    clocks = ClockSampler(gpu_id) if rank == 0 else None
+    launches0 = bm25.launch_count()
+    bm25.profile_begin()
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    prof = bm25.profile_end()
+    launches = bm25.launch_count() - launches0
+    clock_info = clocks.stop() if clocks else None
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = nq * world / (ms / 1e3)
+
+    line = {"metric": f"queries/s @k={k}", "value": value, "unit": "queries/s",
+            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {**w.describe(), "variant": args.variant, "k": k,
+                       "step": "index build + batched top-k retrieval of the query batch",
+                       "l2": "inputs larger than L2 (no flush needed)",
+                       "parallelism": f"replicated index, {nq} queries per GPU"},
+            "clocks": clock_info, "gpu_launches": launches * world}
+
+    if not args.no_extras and rank == 0:
+        extras(args, line, bm25, corpus, queries, tok, off, qt, qo, ids, sc, dev, prof, w)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def extras(args, line, bm25, corpus, queries, tok, off, qt, qo, ids, sc, dev, prof, w):
+    import torch
+    prm = w.params
+    k = args.k
+    nq = queries.n_queries
+    stream = torch.cuda.current_stream(dev)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    ix = bm25.Index.build(tok, off, corpus.vocab, args.variant, prm["k1"], prm["b"], prm["delta"])
+    info = ix.info()
+    ex_indptr = ix.export()["indptr"]
+    df = np.diff(ex_indptr)
+    qlen = np.diff(queries.offsets)
+    postings = int(df[queries.tokens].sum())
+    retrieval_bytes = 8 * postings + 20 * int(qlen.sum()) + 8 * k * nq
+    ctx = {"retrieval_bytes": retrieval_bytes, "n_tokens": corpus.n_tokens, "nnz": info["nnz"]}
+
+    # kernel shares over the timed region
+    total_ms = sum(v[1] for v in prof.values()) or 1.0
+    kernels = {n: {"launches": c, "ms_per_launch": t / max(c, 1), "share": t / total_ms}
+               for n, (c, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    line["kernels"] = kernels
+    top = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+
+    def roofline_for(name, c, t):
+        b = kernel_bytes(name, ctx)
+        if b is None:
+            return None
+        avg_s = t / c / 1e3
+        achieved = b / avg_s / 1e9
+        traffic = None
+        tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+        try:
+            with open(tr_path) as f:
+                tr = json.load(f)
+            from paper_2407_03618_gb300 import build_ext
+            ent = tr.get(name)
+            if ent and ent.get("build_stamp") == build_ext._stamp() and \
+                    ent.get("workload") == w.name:
+                traffic = ent["bytes_per_launch"]
+        except (OSError, ValueError):
+            pass
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                "algorithmic_bytes_per_launch": b, "ms_per_launch": t / c,
+                "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy)"}
+
+    if top is not None:
+        c, t = prof[top]
+        line["roofline"] = roofline_for(top, c, t)
+        if line["roofline"] is None:
+            line["roofline"] = {"kernel": top, "bound": "hbm", "achieved": None,
+                                "peak": hbm_peak, "unit": "GB/s", "frac": None, "traffic": None}
+        others = {}
+        for n in ("k_tile_topk", "k_radix_downsweep"):
+            if n in prof and n != top:
+                others[n] = roofline_for(n, *prof[n])
+        line["roofline_other"] = others
+
+    # retrieval alone on the resident index, batched (k and 100)
+    def time_retrieval(kk, reps=10):
+        o = (torch.empty((nq, kk), dtype=torch.int32, device=dev),
+             torch.empty((nq, kk), dtype=torch.float32, device=dev))
+        for _ in range(3):
+            ix.retrieve(qt, qo, kk, out=o)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            ix.retrieve(qt, qo, kk, out=o)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    r_ms = time_retrieval(k)
+    r100_ms = time_retrieval(100)
+    line["retrieval"] = {"qps": nq / (r_ms / 1e3), "ms_per_batch": r_ms,
+                         "qps_k100": nq / (r100_ms / 1e3), "ms_per_batch_k100": r100_ms,
+                         "postings_per_query": postings / nq,
+                         "algorithmic_GBps": retrieval_bytes / (r_ms / 1e3) / 1e9,
+                         "hbm_frac": retrieval_bytes / (r_ms / 1e3) / 1e9 / hbm_peak}
+
+    # plain path: one query per launch, untuned, latency per query
+    P = min(args.plain_queries, nq)
+    singles = []
+    for i in range(P):
+        a0, a1 = int(queries.offsets[i]), int(queries.offsets[i + 1])
+        singles.append((qt[a0:a1].clone(),
+                        torch.tensor([0, a1 - a0], dtype=torch.int64, device=dev)))
+    o1 = (torch.empty((1, k), dtype=torch.int32, device=dev),
+          torch.empty((1, k), dtype=torch.float32, device=dev))
+    for i in range(min(20, P)):
+        ix.retrieve(singles[i][0], singles[i][1], k, out=o1)
+    torch.cuda.synchronize(dev)
+    lat = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(P)]
+    t0 = time.perf_counter()
+    for i in range(P):
+        ev[i][0].record(stream)
+        ix.retrieve(singles[i][0], singles[i][1], k, out=o1)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    lat = sorted(e[0].elapsed_time(e[1]) for e in ev)
+    line["plain_path"] = {"queries": P, "qps": P / wall,
+                          "p50_ms": lat[len(lat) // 2], "p99_ms": lat[int(0.99 * (len(lat) - 1))],
+                          "batched_speedup": (nq / (r_ms / 1e3)) / (P / wall)}
+    line["batched_latency_ms"] = {"p50": r_ms, "p99": r_ms,
+                                  "note": "every query of a batch completes with the batch"}
+
+    # index build alone
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ix.close()
+    torch.cuda.synchronize(dev)
+    a.record(stream)
+    for _ in range(3):
+        bm25.Index.build(tok, off, corpus.vocab, args.variant, prm["k1"], prm["b"],
+                         prm["delta"]).close()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    b_ms = a.elapsed_time(b) / 3
+    build_bytes = (4 * corpus.n_tokens + 8 * (corpus.n_docs + 1) + 8 * info["nnz"]
+                   + 8 * (corpus.vocab + 1) + 16 * corpus.vocab)
+    line["index_build"] = {"ms": b_ms, "docs_per_s": corpus.n_docs / (b_ms / 1e3),
+                           "nnz": info["nnz"], "n_tokens": corpus.n_tokens,
+                           "algorithmic_GBps": build_bytes / (b_ms / 1e3) / 1e9}
+
+    # end to end through the host-buffer entry points (pinned host memory)
+    h_tok = torch.from_numpy(corpus.tokens).pin_memory()
+    h_off = torch.from_numpy(corpus.doc_offsets).pin_memory()
+    h_qt = torch.from_numpy(queries.tokens).pin_memory()
+    h_qo = torch.from_numpy(queries.offsets).pin_memory()
+    h_ids = torch.empty((nq, k), dtype=torch.int32).pin_memory()
+    h_sc = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        ih = bm25.Index.build_host(h_tok, h_off, corpus.vocab, args.variant, prm["k1"], prm["b"],
+                                   prm["delta"])
+        ih.retrieve_host(h_qt, h_qo, k, out=(h_ids, h_sc))
+        ih.close()
+
+    e2e_step()
+    steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        e2e_step()
+    e2e_s = (time.perf_counter() - t0) / steps
+    h2d = 4 * corpus.n_tokens + 8 * (corpus.n_docs + 1) + 4 * queries.tokens.shape[0] + 8 * (nq + 1)
+    line["e2e"] = {"value": nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": 8 * nq * k, "ms_per_step": e2e_s * 1e3}
+
+    # CPU oracle on a bounded sample (rank 0, N = 1 only)
+    if line["n_gpus"] == 1:
+        _, cpu = oracle_rate(corpus, queries, args.variant, k, args.cpu_sample_queries,
+                             os.cpu_count() or 1, prm)
+        line["cpu_baseline"] = cpu
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,231 @@
+/*
+ * bm25.h -- C ABI of libbm25gpu, a GB300 (sm_103a) implementation of the
+ * eager sparse scoring of BM25S (arXiv 2407.03618).
+ *
+ * The method (Sec. 2): every score S(t,D) a future query token could need is
+ * computed at index time and stored in a sparse term-major matrix; a query is
+ * answered by slicing its tokens' columns, summing them into per-document
+ * scores and keeping the top k.  BM25L and BM25+ store the shifted score
+ * S(t,D) - S0(t) and add the per-query constant sum_i S0(q_i) back (Sec. 2.1).
+ *
+ * Conventions for every entry point:
+ *   - Return value: BM25_OK (0) or a negative bm25_status.  On failure a
+ *     message is available from bm25_last_error() on the calling thread.
+ *   - Pointers are DEVICE pointers (cudaMalloc / torch CUDA memory on the
+ *     index's device) unless the entry point's name ends in _host or the
+ *     argument is documented as host memory.
+ *   - `cuda_stream` is a cudaStream_t (NULL = legacy default stream).  Device
+ *     work is enqueued on it; functions return before it finishes unless
+ *     stated otherwise.
+ *   - The caller owns every array it passes in.  The library owns an index
+ *     (and a workspace) until the matching *_free call.
+ *   - Errors found by kernels (a token id outside [0, vocab), malformed
+ *     offsets) are recorded in a per-index device status word and reported
+ *     by bm25_sync_status(); host-side argument checks fail immediately with
+ *     BM25_E_INVALID and launch nothing.
+ *
+ * Variant formulas (K_D = 1 - b + b |D| / Lavg, |D| and Lavg in tokens):
+ *   LUCENE     IDF = ln((N - DF + 0.5)/(DF + 0.5) + 1), S = IDF TF/(TF + k1 K_D)   (Sec. 2)
+ *   ROBERTSON  IDF = ln((N - DF + 0.5)/(DF + 0.5)),     S as Lucene
+ *   ATIRE      IDF = ln(N / DF),                         S = IDF (k1+1) TF/(TF + k1 K_D)
+ *   BM25L      IDF = ln((N + 1)/(DF + 0.5)), c = TF/K_D, S = IDF (k1+1)(c + delta)/(k1 + c + delta)
+ *   BM25PLUS   IDF = ln((N + 1)/DF),                     S = IDF ((k1+1) TF/(k1 K_D + TF) + delta)
+ * (the last four as the paper adopts them from Kamphuis et al. 2020,
+ * Sec. 2 "Alternative BM25 implementations").  A term with DF = 0 has
+ * IDF = 0 and S0 = 0.
+ */
+#ifndef BM25_GPU_H
+#define BM25_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bm25_index bm25_index;
+typedef struct bm25_workspace bm25_workspace;
+
+enum bm25_variant {
+    BM25_LUCENE = 0,
+    BM25_ROBERTSON = 1,
+    BM25_ATIRE = 2,
+    BM25_L = 3,
+    BM25_PLUS = 4
+};
+
+enum bm25_status {
+    BM25_OK = 0,
+    BM25_E_INVALID = -1,     /* bad argument (host-side check) */
+    BM25_E_TOKEN_RANGE = -2, /* a token id outside [0, vocab) or malformed offsets */
+    BM25_E_OOM = -3,         /* device allocation failed */
+    BM25_E_CUDA = -4,        /* a CUDA runtime call failed */
+    BM25_E_TIMEOUT = -5      /* a bounded device-side wait gave up */
+};
+
+/* Accumulator strategies for retrieval. */
+enum bm25_accumulator {
+    BM25_ACC_AUTO = 0,       /* pick per query batch (autotuned plan if one is set) */
+    BM25_ACC_SMEM_TILED = 1, /* doc-tiled FP32 accumulators in shared memory */
+    BM25_ACC_L2_DENSE = 2    /* one dense FP32 vector per in-flight query, L2-resident */
+};
+
+/* Upper bound on min(k, n_docs) for one retrieval call. */
+#define BM25_MAX_K 4096
+
+/* ------------------------------------------------------------------ index */
+
+/* Eager index build (Sec. 2 "Eager index-time scoring", "Efficient Matrix
+ * Sparsity"; Sec. 2.1 for the shift).
+ *
+ *   token_ids[n_tokens]    int32, device.  Document D owns
+ *                          token_ids[doc_offsets[D] .. doc_offsets[D+1]).
+ *   doc_offsets[n_docs+1]  int64, device, non-decreasing, doc_offsets[0] = 0,
+ *                          doc_offsets[n_docs] = n_tokens.  Empty documents
+ *                          are allowed and count in N.
+ *   vocab                  number of term ids; every token must be in [0, vocab).
+ *   variant                enum bm25_variant.
+ *   k1 >= 0, 0 <= b <= 1, delta >= 0 (delta is used by BM25L and BM25PLUS;
+ *                          BM25L also needs k1 + delta > 0).
+ *   n_docs in [1, 2^31 - 2], n_tokens in [0, 2^31 - 2].
+ *
+ * Computes |D|, Lavg (FP64), TF per distinct (term, doc) pair, DF, IDF and
+ * S0 per term (FP64), and the term-major CSC: indptr[vocab+1] (int64),
+ * indices[nnz] (int32 doc ids, strictly ascending within a term), data[nnz]
+ * (FP32 S(t,D) - S0(t)).  Stream-ordered; synchronises `cuda_stream` once to
+ * learn nnz and returns after the build has been enqueued (the index is usable
+ * on `cuda_stream` at once and on other streams after that stream syncs).
+ * Returns BM25_E_TOKEN_RANGE (and no index) if a token or offset is invalid. */
+int bm25_index_build(const int32_t* token_ids, int64_t n_tokens,
+                     const int64_t* doc_offsets, int64_t n_docs, int32_t vocab,
+                     int variant, double k1, double b, double delta,
+                     void* cuda_stream, bm25_index** out);
+
+/* Same as bm25_index_build with token_ids and doc_offsets in HOST memory
+ * (pinned memory makes the copies asynchronous).  Copies them to the current
+ * device on `cuda_stream`, builds, and returns once the build has finished. */
+int bm25_index_build_host(const int32_t* token_ids, int64_t n_tokens,
+                          const int64_t* doc_offsets, int64_t n_docs, int32_t vocab,
+                          int variant, double k1, double b, double delta,
+                          void* cuda_stream, bm25_index** out);
+
+/* Scalars of an index.  Any output pointer may be NULL.  Host memory. */
+int bm25_index_info(const bm25_index* index, int64_t* n_docs, int64_t* n_tokens,
+                    int64_t* nnz, int32_t* vocab, int* variant, double* k1,
+                    double* b, double* delta, double* lavg);
+
+/* Copies the index's arrays to HOST memory; any pointer may be NULL.
+ *   indptr[vocab+1] int64, indices[nnz] int32, data[nnz] float (S - S0),
+ *   tf[nnz] int32, df[vocab] int32, doc_len[n_docs] int32,
+ *   idf[vocab] double, s0[vocab] double.
+ * Synchronous.  This is the save path of a checkpoint (see bm25_index_import). */
+int bm25_index_export(const bm25_index* index, int64_t* indptr, int32_t* indices,
+                      float* data, int32_t* tf, int32_t* df, int32_t* doc_len,
+                      double* idf, double* s0);
+
+/* Rebuilds an index on the current device from arrays previously exported
+ * (HOST memory, layouts as in bm25_index_export; tf may be NULL, then TF is
+ * stored as 0).  lavg and the parameters are taken as given.  Synchronous. */
+int bm25_index_import(int64_t n_docs, int64_t n_tokens, int64_t nnz, int32_t vocab,
+                      int variant, double k1, double b, double delta, double lavg,
+                      const int64_t* indptr, const int32_t* indices, const float* data,
+                      const int32_t* tf, const int32_t* df, const int32_t* doc_len,
+                      const double* idf, const double* s0, bm25_index** out);
+
+/* Synchronises `cuda_stream`, then returns and clears the first error any
+ * kernel recorded for this index since the last call (BM25_OK if none). */
+int bm25_sync_status(const bm25_index* index, void* cuda_stream);
+
+/* Releases the index, its default workspace and its device memory.  The caller
+ * must make sure no work using the index is still in flight.  NULL is a no-op. */
+void bm25_index_free(bm25_index* index);
+
+/* -------------------------------------------------------------- retrieval */
+
+/* Batched top-k retrieval (Sec. 2 "Assigning Query Scores": slice the query
+ * tokens' columns and sum them; "Top-k selection").
+ *
+ *   query_tokens[n_query_tokens]  int32, device.  Query q owns
+ *                 query_tokens[query_offsets[q] .. query_offsets[q+1]).
+ *                 A token repeated in a query counts once per occurrence.
+ *   query_offsets[n_queries+1]  int64, device, non-decreasing, starting at 0
+ *                 and ending at n_query_tokens (checked on the device:
+ *                 violations record BM25_E_TOKEN_RANGE and the offending
+ *                 ranges are clamped).
+ *   k >= 1.  Let k' = min(k, n_docs); k' <= BM25_MAX_K.
+ *   out_ids[n_queries*k] int32 and out_scores[n_queries*k] float, device.
+ *
+ * Row q of the outputs holds the k' documents with the highest B(Q,D),
+ * sorted by score descending and doc id ascending among equal scores
+ * (documents the query does not touch score exactly sum_i S0(q_i) and are
+ * eligible like any other).  Scores are B(Q,D) including the shift of
+ * Sec. 2.1.  Slots k' .. k-1 get id -1 and score -inf.  A token id outside
+ * [0, vocab) contributes nothing and records BM25_E_TOKEN_RANGE (see
+ * bm25_sync_status).  Asynchronous on `cuda_stream`.  Uses the index's
+ * default workspace, so calls on one index must not overlap on the device
+ * (serialise them on one stream, or use bm25_retrieve_ws). */
+int bm25_retrieve(const bm25_index* index, const int32_t* query_tokens,
+                  int64_t n_query_tokens, const int64_t* query_offsets,
+                  int32_t n_queries, int32_t k, int32_t* out_ids, float* out_scores,
+                  void* cuda_stream);
+
+/* bm25_retrieve with query_tokens, query_offsets, out_ids and out_scores in
+ * HOST memory (pinned memory makes the copies asynchronous).  Copies the
+ * queries in, retrieves, copies the results out and returns when they are in
+ * host memory.  query_offsets[0] must be 0; n_query_tokens =
+ * query_offsets[n_queries]. */
+int bm25_retrieve_host(const bm25_index* index, const int32_t* query_tokens,
+                       const int64_t* query_offsets, int32_t n_queries, int32_t k,
+                       int32_t* out_ids, float* out_scores, void* cuda_stream);
+
+/* A workspace holds the scratch memory of retrieval.  Sized for at most
+ * max_queries queries, max_query_tokens tokens in total and k' <= max_k; a
+ * call within those limits allocates nothing (and can be captured in a CUDA
+ * graph).  One workspace serves one call at a time. */
+int bm25_workspace_create(const bm25_index* index, int32_t max_queries,
+                          int64_t max_query_tokens, int32_t max_k,
+                          bm25_workspace** out);
+void bm25_workspace_free(bm25_workspace* ws);
+
+/* bm25_retrieve with an explicit workspace and accumulator strategy
+ * (enum bm25_accumulator) and doc-tile width (0 = the index's plan).  Calls
+ * with different workspaces may overlap on the device. */
+int bm25_retrieve_ws(const bm25_index* index, bm25_workspace* ws,
+                     const int32_t* query_tokens, int64_t n_query_tokens,
+                     const int64_t* query_offsets, int32_t n_queries, int32_t k,
+                     int32_t* out_ids, float* out_scores, int accumulator,
+                     int32_t tile_docs, void* cuda_stream);
+
+/* Sets the index's default plan: accumulator strategy and doc-tile width in
+ * documents (a multiple of 1024 between 1024 and 49152; 0 keeps the current
+ * value). */
+int bm25_index_set_plan(bm25_index* index, int accumulator, int32_t tile_docs);
+
+/* --------------------------------------------------------------- utility */
+
+/* Message for the last failure on the calling thread ("" if none). */
+const char* bm25_last_error(void);
+
+/* Total number of kernels this library has launched in this process. */
+int64_t bm25_launch_count(void);
+
+/* Library version string. */
+const char* bm25_version(void);
+
+/* Per-kernel timing.  Between bm25_profile_begin() and bm25_profile_end()
+ * every kernel launch of this library is bracketed by two CUDA events on the
+ * stream it is launched on (not while that stream is being captured).
+ * bm25_profile_end() waits for the recorded events and aggregates them per
+ * kernel name; bm25_profile_count() and bm25_profile_get() read the result
+ * (entry i: NUL-terminated name truncated to name_cap bytes, launch count,
+ * summed milliseconds).  Off by default. */
+int bm25_profile_begin(void);
+int bm25_profile_end(void);
+int bm25_profile_count(void);
+int bm25_profile_get(int i, char* name, int name_cap, int64_t* launches, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BM25_GPU_H */

@@ -67,7 +67,7 @@ def _load():
                                          P, P, P, P, P, P, P, P, P, P, P, P]
             lib.oracle_score_all.restype = None
             lib.oracle_score_all.argtypes = [P, i64, i64, i32, cint, f64, f64, f64,
-                                             P, f64, P, P, P, P, P]
+                                             P, f64, P, P, P, P, P, P]
             lib.oracle_rank.restype = None
             lib.oracle_rank.argtypes = [P, i64, P]
             lib.oracle_topk.restype = None
@@ -152,14 +152,17 @@ def build(tokens, doc_offsets, vocab: int, variant: int = LUCENE, k1: float = 1.
                        indices[:nnz], csc_tf[:nnz], csc_delta[:nnz])
 
 
-def score_all(ix: OracleIndex, query) -> np.ndarray:
-    """Lazy B(Q,D) for every document, FP64."""
+def score_all(ix: OracleIndex, query, with_abs: bool = False):
+    """Lazy B(Q,D) for every document, FP64.  With with_abs, also returns
+    sum_i |S(q_i, D)| per document."""
     q = np.ascontiguousarray(query, dtype=np.int32)
     out = np.zeros(ix.n_docs, np.float64)
+    ab = np.zeros(ix.n_docs, np.float64) if with_abs else None
     _load().oracle_score_all(_p(q), q.shape[0], ix.n_docs, ix.vocab, ix.variant, ix.k1,
                              ix.b, ix.delta, _p(ix.doc_len), ix.lavg, _p(ix.pair_start),
-                             _p(ix.pair_term), _p(ix.pair_tf), _p(ix.idf), _p(out))
-    return out
+                             _p(ix.pair_term), _p(ix.pair_tf), _p(ix.idf), _p(out),
+                             _p(ab) if with_abs else None)
+    return (out, ab) if with_abs else out
 
 
 def rank(scores: np.ndarray) -> np.ndarray:

@@ -232,24 +232,31 @@ static int32_t lookup_tf(const int64_t* pair_start, const int32_t* pair_term,
 
 /* Lazy exhaustive B(Q,D) = sum_i S(q_i, D) for every document (Sec. 2),
  * TF = 0 terms included.  q has q_len tokens (duplicates count per
- * occurrence).  Tokens outside [0, vocab) contribute nothing. */
+ * occurrence).  Tokens outside [0, vocab) contribute nothing.  If abs_out is
+ * not NULL it receives sum_i |S(q_i, D)|, the scale of the rounding error of
+ * any summation order. */
 void oracle_score_all(const int32_t* q, int64_t q_len, int64_t n_docs,
                       int32_t vocab, int variant, double k1, double b,
                       double delta, const int64_t* doc_len, double lavg,
                       const int64_t* pair_start, const int32_t* pair_term,
-                      const int32_t* pair_tf, const double* idf, double* out)
+                      const int32_t* pair_tf, const double* idf, double* out,
+                      double* abs_out)
 {
     for (int64_t d = 0; d < n_docs; d++) {
-        double s = 0.0;
+        double s = 0.0, a = 0.0;
         for (int64_t i = 0; i < q_len; i++) {
             int32_t t = q[i];
             if (t < 0 || t >= vocab)
                 continue;
             int32_t tf = lookup_tf(pair_start, pair_term, pair_tf, d, t);
-            s += oracle_term_score(variant, idf[t], (double)tf, (double)doc_len[d],
-                                   lavg, k1, b, delta);
+            double st = oracle_term_score(variant, idf[t], (double)tf, (double)doc_len[d],
+                                          lavg, k1, b, delta);
+            s += st;
+            a += fabs(st);
         }
         out[d] = s;
+        if (abs_out)
+            abs_out[d] = a;
     }
 }
 
@@ -300,7 +307,7 @@ static void* topk_worker(void* arg)
         oracle_score_all(j->q_tokens + j->q_off[q], j->q_off[q + 1] - j->q_off[q],
                          j->n_docs, j->vocab, j->variant, j->k1, j->b, j->delta,
                          j->doc_len, j->lavg, j->pair_start, j->pair_term,
-                         j->pair_tf, j->idf, sc);
+                         j->pair_tf, j->idf, sc, NULL);
         oracle_rank(sc, j->n_docs, order);
         for (int64_t r = 0; r < j->k; r++) {
             if (r < j->n_docs) {

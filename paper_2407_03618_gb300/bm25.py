@@ -1,0 +1,322 @@
+"""Python binding of libbm25gpu: argument marshalling only.
+
+Every step of index build and retrieval runs in the library's CUDA kernels;
+this module converts torch tensors / numpy arrays to pointers, passes the
+current torch CUDA stream, and raises on a non-zero status.  PyTorch is used
+for device memory and streams, nothing else.  If the library has not been
+built the module raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build_ext
+
+VARIANTS = {"lucene": 0, "robertson": 1, "atire": 2, "bm25l": 3, "bm25+": 4}
+ACC_AUTO, ACC_SMEM_TILED, ACC_L2_DENSE = 0, 1, 2
+STATUS = {0: "BM25_OK", -1: "BM25_E_INVALID", -2: "BM25_E_TOKEN_RANGE", -3: "BM25_E_OOM",
+          -4: "BM25_E_CUDA", -5: "BM25_E_TIMEOUT"}
+MAX_K = 4096
+
+
+class BM25Error(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/bm25.h."""
+    with open(os.path.join(build_ext.INCLUDE, "bm25.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return re.findall(r"\b(bm25_\w+)\s*\(", text)
+
+
+def load(path: str | None = None):
+    """Load libbm25gpu.so (built by build_ext.build()); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or build_ext.LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libbm25gpu.so is not built ({path}); run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    P, i32, i64, f64, cint = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
+                              ctypes.c_int)
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "bm25_index_build": (cint, [P, i64, P, i64, i32, cint, f64, f64, f64, P, PP]),
+        "bm25_index_build_host": (cint, [P, i64, P, i64, i32, cint, f64, f64, f64, P, PP]),
+        "bm25_index_info": (cint, [P, P, P, P, P, P, P, P, P, P]),
+        "bm25_index_export": (cint, [P, P, P, P, P, P, P, P, P]),
+        "bm25_index_import": (cint, [i64, i64, i64, i32, cint, f64, f64, f64, f64,
+                                     P, P, P, P, P, P, P, P, PP]),
+        "bm25_sync_status": (cint, [P, P]),
+        "bm25_index_free": (None, [P]),
+        "bm25_retrieve": (cint, [P, P, i64, P, i32, i32, P, P, P]),
+        "bm25_retrieve_host": (cint, [P, P, P, i32, i32, P, P, P]),
+        "bm25_workspace_create": (cint, [P, i32, i64, i32, PP]),
+        "bm25_workspace_free": (None, [P]),
+        "bm25_retrieve_ws": (cint, [P, P, P, i64, P, i32, i32, P, P, cint, i32, P]),
+        "bm25_index_set_plan": (cint, [P, cint, i32]),
+        "bm25_last_error": (ctypes.c_char_p, []),
+        "bm25_launch_count": (i64, []),
+        "bm25_version": (ctypes.c_char_p, []),
+        "bm25_profile_begin": (cint, []),
+        "bm25_profile_end": (cint, []),
+        "bm25_profile_count": (cint, []),
+        "bm25_profile_get": (cint, [cint, ctypes.c_char_p, cint, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise BM25Error(rc, load().bm25_last_error().decode())
+
+
+def launch_count() -> int:
+    return int(load().bm25_launch_count())
+
+
+def profile_begin():
+    """Start bracketing every library kernel launch with CUDA events."""
+    _check(load().bm25_profile_begin())
+
+
+def profile_end() -> dict:
+    """Stop; returns {kernel name: (launches, total milliseconds)}."""
+    lib = load()
+    _check(lib.bm25_profile_end())
+    out = {}
+    buf = ctypes.create_string_buffer(128)
+    for i in range(lib.bm25_profile_count()):
+        n, ms = ctypes.c_int64(), ctypes.c_double()
+        _check(lib.bm25_profile_get(i, buf, 128, ctypes.byref(n), ctypes.byref(ms)))
+        out[buf.value.decode()] = (n.value, ms.value)
+    return out
+
+
+def _stream(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dev_tensor(x, dtype):
+    import torch
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if x.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {x.dtype}")
+    return x.contiguous()
+
+
+def _np(x, dtype):
+    return np.ascontiguousarray(x, dtype=dtype)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Workspace:
+    """Scratch memory for retrieval, sized once (no allocation inside calls
+    that stay within its limits)."""
+
+    def __init__(self, index: "Index", max_queries: int, max_query_tokens: int, max_k: int):
+        h = ctypes.c_void_p()
+        _check(load().bm25_workspace_create(index.handle, max_queries, max_query_tokens, max_k,
+                                            ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            load().bm25_workspace_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Index:
+    """A BM25 index resident on one GPU (term-major CSC of S - S0)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self._refs = []
+
+    # ---- construction ----
+    @classmethod
+    def build(cls, tokens, doc_offsets, vocab: int, variant="lucene", k1: float = 1.5,
+              b: float = 0.75, delta: float = 0.5, stream=None) -> "Index":
+        """tokens: CUDA int32 [T]; doc_offsets: CUDA int64 [N+1]."""
+        import torch
+        tok = _dev_tensor(tokens, torch.int32)
+        off = _dev_tensor(doc_offsets, torch.int64)
+        h = ctypes.c_void_p()
+        v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        _check(load().bm25_index_build(tok.data_ptr(), tok.numel(), off.data_ptr(),
+                                       off.numel() - 1, vocab, v, k1, b, delta,
+                                       _stream(stream), ctypes.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def build_host(cls, tokens, doc_offsets, vocab: int, variant="lucene", k1: float = 1.5,
+                   b: float = 0.75, delta: float = 0.5, stream=None) -> "Index":
+        """tokens / doc_offsets in host memory (numpy or pinned CPU tensors)."""
+        tok = _host_array(tokens, np.int32)
+        off = _host_array(doc_offsets, np.int64)
+        h = ctypes.c_void_p()
+        v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        _check(load().bm25_index_build_host(_hptr(tok), _hlen(tok), _hptr(off), _hlen(off) - 1,
+                                            vocab, v, k1, b, delta, _stream(stream),
+                                            ctypes.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def load_arrays(cls, arrays: dict) -> "Index":
+        """Rebuild an index from export() output (checkpoint resume)."""
+        a = arrays
+        h = ctypes.c_void_p()
+        keep = {k: _np(a[k], dt) for k, dt in (("indptr", np.int64), ("indices", np.int32),
+                                               ("data", np.float32), ("tf", np.int32),
+                                               ("df", np.int32), ("doc_len", np.int32),
+                                               ("idf", np.float64), ("s0", np.float64))}
+        _check(load().bm25_index_import(int(a["n_docs"]), int(a["n_tokens"]), int(a["nnz"]),
+                                        int(a["vocab"]), int(a["variant"]), float(a["k1"]),
+                                        float(a["b"]), float(a["delta"]), float(a["lavg"]),
+                                        *[_ptr(keep[k]) for k in ("indptr", "indices", "data",
+                                                                  "tf", "df", "doc_len", "idf",
+                                                                  "s0")],
+                                        ctypes.byref(h)))
+        return cls(h)
+
+    # ---- queries ----
+    def info(self) -> dict:
+        n, t, z = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        v, var = ctypes.c_int32(), ctypes.c_int()
+        k1, b, d, la = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(load().bm25_index_info(self.handle, *[ctypes.byref(x) for x in
+                                                     (n, t, z, v, var, k1, b, d, la)]))
+        return {"n_docs": n.value, "n_tokens": t.value, "nnz": z.value, "vocab": v.value,
+                "variant": var.value, "k1": k1.value, "b": b.value, "delta": d.value,
+                "lavg": la.value}
+
+    def export(self) -> dict:
+        inf = self.info()
+        V, N, Z = inf["vocab"], inf["n_docs"], inf["nnz"]
+        out = {"indptr": np.zeros(V + 1, np.int64), "indices": np.zeros(Z, np.int32),
+               "data": np.zeros(Z, np.float32), "tf": np.zeros(Z, np.int32),
+               "df": np.zeros(V, np.int32), "doc_len": np.zeros(N, np.int32),
+               "idf": np.zeros(V, np.float64), "s0": np.zeros(V, np.float64)}
+        _check(load().bm25_index_export(self.handle, *[_ptr(out[k]) for k in
+                                                       ("indptr", "indices", "data", "tf", "df",
+                                                        "doc_len", "idf", "s0")]))
+        out.update(inf)
+        return out
+
+    def set_plan(self, accumulator: int = ACC_AUTO, tile_docs: int = 0):
+        _check(load().bm25_index_set_plan(self.handle, accumulator, tile_docs))
+
+    def sync_status(self, stream=None):
+        _check(load().bm25_sync_status(self.handle, _stream(stream)))
+
+    def retrieve(self, q_tokens, q_offsets, k: int, out=None, stream=None,
+                 workspace: Workspace | None = None, accumulator: int = ACC_AUTO,
+                 tile_docs: int = 0):
+        """Device path.  q_tokens CUDA int32, q_offsets CUDA int64 [nQ+1].
+        Returns (ids int32 [nQ, k], scores float32 [nQ, k]) CUDA tensors."""
+        import torch
+        qt = _dev_tensor(q_tokens, torch.int32)
+        qo = _dev_tensor(q_offsets, torch.int64)
+        nq = qo.numel() - 1
+        if out is None:
+            ids = torch.empty((nq, k), dtype=torch.int32, device=qo.device)
+            sc = torch.empty((nq, k), dtype=torch.float32, device=qo.device)
+        else:
+            ids, sc = out
+        if workspace is None and accumulator == ACC_AUTO and tile_docs == 0:
+            _check(load().bm25_retrieve(self.handle, qt.data_ptr(), qt.numel(), qo.data_ptr(), nq,
+                                        k, ids.data_ptr(), sc.data_ptr(), _stream(stream)))
+        else:
+            if workspace is None:
+                workspace = self._default_workspace(nq, qt.numel(), k)
+            _check(load().bm25_retrieve_ws(self.handle, workspace.handle, qt.data_ptr(),
+                                           qt.numel(), qo.data_ptr(), nq, k, ids.data_ptr(),
+                                           sc.data_ptr(), accumulator, tile_docs,
+                                           _stream(stream)))
+        return ids, sc
+
+    def _default_workspace(self, nq, ntok, k):
+        ws = Workspace(self, max(nq, 1), ntok, k)
+        self._refs.append(ws)
+        return ws
+
+    def retrieve_host(self, q_tokens, q_offsets, k: int, out=None, stream=None):
+        """Host path: inputs and outputs in host memory (numpy or pinned CPU
+        tensors).  Returns (ids, scores) as given in `out` or new numpy arrays."""
+        qt = _host_array(q_tokens, np.int32)
+        qo = _host_array(q_offsets, np.int64)
+        nq = _hlen(qo) - 1
+        if out is None:
+            ids = np.zeros((nq, k), np.int32)
+            sc = np.zeros((nq, k), np.float32)
+        else:
+            ids, sc = out
+        _check(load().bm25_retrieve_host(self.handle, _hptr(qt), _hptr(qo), nq, k, _hptr(ids),
+                                         _hptr(sc), _stream(stream)))
+        return ids, sc
+
+    def close(self):
+        if self.handle:
+            for ws in self._refs:
+                ws.close()
+            self._refs = []
+            load().bm25_index_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _host_array(x, dtype):
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if x.is_cuda:
+                raise TypeError("expected host memory")
+            return x.contiguous()
+    except ImportError:
+        pass
+    return _np(x, dtype)
+
+
+def _hptr(x):
+    if isinstance(x, np.ndarray):
+        return _ptr(x)
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _hlen(x) -> int:
+    return int(x.shape[0]) if isinstance(x, np.ndarray) else int(x.numel())

@@ -1,0 +1,105 @@
+// Device-side helpers: block scans, the ordered (score, doc) key, status word.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace bm25 {
+
+__device__ __forceinline__ void set_status(int* status, int code)
+{
+    atomicCAS(status, 0, code);
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Inclusive warp scan (sum).
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_sum(T v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o)
+            v += n;
+    }
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Exclusive scan across the block (blockDim.x a multiple of 32, <= 1024).
+// `warp_buf` holds 33 elements of shared memory.  Returns the exclusive
+// prefix of v; *total receives the block sum.  Contains __syncthreads().
+template <typename T>
+__device__ __forceinline__ T block_exclusive_sum(T v, T* warp_buf, T* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    T inc = warp_inclusive_sum(v);
+    if (lane == 31)
+        warp_buf[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        T w = (lane < nwarps) ? warp_buf[lane] : T(0);
+        T wi = warp_inclusive_sum(w);
+        if (lane < nwarps)
+            warp_buf[lane] = wi - w;  // exclusive
+        if (lane == nwarps - 1)
+            warp_buf[32] = wi;
+    }
+    __syncthreads();
+    T r = warp_buf[warp] + inc - v;
+    *total = warp_buf[32];
+    __syncthreads();
+    return r;
+}
+
+// ---- ranking keys -------------------------------------------------------
+// A candidate is a 64-bit key whose unsigned order is the ranking order:
+// high word = FP32 score mapped to an order-preserving uint32 (-0.0 folded
+// onto +0.0), low word = ~doc so that the lower doc id wins a tie.  Every
+// non-NaN score maps to a high word >= 0x007fffff, so key 0 never names a
+// real candidate and serves as the empty slot.
+__device__ __forceinline__ uint32_t order_f32(float s)
+{
+    uint32_t u = __float_as_uint(s == 0.0f ? 0.0f : s);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float unorder_f32(uint32_t o)
+{
+    uint32_t u = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+    return __uint_as_float(u);
+}
+
+__device__ __forceinline__ unsigned long long make_key(float s, uint32_t doc)
+{
+    return ((unsigned long long)order_f32(s) << 32) | (unsigned long long)(~doc);
+}
+
+__device__ __forceinline__ uint32_t key_doc(unsigned long long k)
+{
+    return ~(uint32_t)(k & 0xffffffffull);
+}
+
+__device__ __forceinline__ float key_score(unsigned long long k)
+{
+    return unorder_f32((uint32_t)(k >> 32));
+}
+
+}  // namespace bm25

@@ -1,0 +1,633 @@
+// Eager index build (arXiv 2407.03618 Sec. 2 "Eager index-time scoring" and
+// "Efficient Matrix Sparsity"; Sec. 2.1 for the non-occurrence shift).
+//
+// Pipeline, all on the caller's stream:
+//   K1 k_doc_prep        |D| per document, the doc id of every token, and the
+//                        per-document length factor of the score
+//   K2 k_radix_*         stable LSD radix sort of the tokens by term id with
+//                        the doc id as payload.  The input is in document order,
+//                        so the result is term-major with doc ids ascending
+//                        inside each term, and equal (term, doc) pairs adjacent
+//   K3 k_rle_*           run-length reduce of the sorted pairs: one run per
+//                        distinct (term, doc) = one CSC entry, TF = run length
+//   K4/K5 k_indptr       column starts (the exclusive prefix sum of DF) by a
+//                        lower bound over the term of each run; DF = difference
+//   K6 k_idf             IDF and S0 per term in FP64, FP32 score coefficient
+//   K7 k_score           S(t,D) - S0(t) per CSC entry in FP32
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace bm25 {
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortIpt = 16;
+constexpr int kSortTile = kSortThreads * kSortIpt;  // 4096 items per tile
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kMaxDigitBits = 8;
+constexpr int kMaxBuckets = 1 << kMaxDigitBits;
+
+// ---- K1 -------------------------------------------------------------------
+// One warp per document: |D|, the doc id of each of its tokens, and the FP32
+// length factor used by the score kernel (k1 * K_D, or 1 / K_D for BM25L,
+// with K_D = 1 - b + b |D| / Lavg evaluated in FP64).  Offsets are checked;
+// a malformed range records BM25_E_TOKEN_RANGE and writes nothing outside
+// [0, n_tokens).
+__global__ void k_doc_prep(const int64_t* __restrict__ off, int64_t n_docs, int64_t n_tokens,
+                           int32_t* __restrict__ tok_doc, int32_t* __restrict__ doc_len,
+                           float* __restrict__ len_factor, int variant, double k1, double b,
+                           double lavg, int* status)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    if (warp0 == 0 && lane == 0 && (off[0] != 0 || off[n_docs] != n_tokens))
+        set_status(status, BM25_E_TOKEN_RANGE);
+    for (int64_t d = warp0; d < n_docs; d += nwarps) {
+        int64_t lo = off[d], hi = off[d + 1];
+        bool bad = lo < 0 || hi < lo || hi > n_tokens;
+        if (lane == 0) {
+            if (bad)
+                set_status(status, BM25_E_TOKEN_RANGE);
+            int64_t len = bad ? 0 : hi - lo;
+            doc_len[d] = (int32_t)len;
+            double kd = 1.0 - b + b * (double)len / lavg;
+            len_factor[d] = (variant == BM25_L) ? (float)(1.0 / kd) : (float)(k1 * kd);
+        }
+        if (bad)
+            continue;
+        for (int64_t p = lo + lane; p < hi; p += 32)
+            tok_doc[p] = (int32_t)d;
+    }
+}
+
+// ---- K2: stable LSD radix sort -------------------------------------------
+// Reduce-then-scan per pass (Satish et al. 2009; Merrill and Grimshaw 2011):
+// per-tile digit counts, one exclusive scan over the digit-major count table,
+// then a scatter that ranks each tile's items stably.  No kernel waits on
+// another block.
+
+// Per-tile digit histogram.  counts is digit-major: counts[d * n_tiles + tile].
+// With vocab > 0 it also checks every key against [0, vocab).
+__global__ void __launch_bounds__(kSortThreads)
+    k_radix_upsweep(const uint32_t* __restrict__ keys, int64_t n, int shift, int bits,
+                    uint32_t* __restrict__ counts, int64_t n_tiles, uint32_t vocab, int* status)
+{
+    __shared__ uint32_t hist[kMaxBuckets];
+    const int nb = 1 << bits;
+    const uint32_t mask = (uint32_t)nb - 1u;
+    for (int d = threadIdx.x; d < nb; d += kSortThreads)
+        hist[d] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    bool bad = false;
+#pragma unroll 4
+    for (int i = 0; i < kSortIpt; i++) {
+        int64_t p = base + (int64_t)i * kSortThreads + threadIdx.x;
+        uint32_t dg = 0xffffffffu;
+        if (p < n) {
+            uint32_t k = keys[p];
+            bad |= (vocab != 0u && k >= vocab);
+            dg = (k >> shift) & mask;
+        }
+        uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        if (dg != 0xffffffffu && (peers & lanemask_lt()) == 0)
+            atomicAdd(&hist[dg], (uint32_t)__popc(peers));
+    }
+    if (bad)
+        set_status(status, BM25_E_TOKEN_RANGE);
+    __syncthreads();
+    for (int d = threadIdx.x; d < nb; d += kSortThreads)
+        counts[(int64_t)d * n_tiles + blockIdx.x] = hist[d];
+}
+
+// Stable scatter.  Warp w owns items [w*512, w*512+512) of the tile and
+// walks them in 16 rounds of 32 consecutive items; __match_any_sync groups a
+// round's lanes by digit, so each item's rank among equal digits follows its
+// position.  Per-warp counters are then turned into per-warp bases by an
+// exclusive scan over warps, which keeps warp order = item order.
+__global__ void __launch_bounds__(kSortThreads)
+    k_radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                      uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n,
+                      int shift, int bits, const uint32_t* __restrict__ offsets, int64_t n_tiles)
+{
+    __shared__ uint32_t wcnt[kSortWarps][kMaxBuckets];
+    __shared__ uint32_t gbase[kMaxBuckets];
+    const int nb = 1 << bits;
+    const uint32_t mask = (uint32_t)nb - 1u;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kSortWarps * kMaxBuckets; i += kSortThreads)
+        (&wcnt[0][0])[i] = 0;
+    for (int d = threadIdx.x; d < nb; d += kSortThreads)
+        gbase[d] = offsets[(int64_t)d * n_tiles + blockIdx.x];
+    __syncthreads();
+
+    const int64_t base = (int64_t)blockIdx.x * kSortTile + warp * (kSortIpt * 32);
+    const uint32_t lt = lanemask_lt();
+    uint32_t k[kSortIpt], v[kSortIpt], rank[kSortIpt];
+#pragma unroll
+    for (int r = 0; r < kSortIpt; r++) {
+        int64_t p = base + r * 32 + lane;
+        bool ok = p < n;
+        k[r] = ok ? keys_in[p] : 0u;
+        v[r] = ok ? vals_in[p] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kSortIpt; r++) {
+        int64_t p = base + r * 32 + lane;
+        bool ok = p < n;
+        uint32_t dg = ok ? ((k[r] >> shift) & mask) : 0xffffffffu;
+        uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        uint32_t before = ok ? wcnt[warp][dg] : 0u;
+        __syncwarp();
+        if (ok && (peers & lt) == 0)
+            wcnt[warp][dg] = before + (uint32_t)__popc(peers);
+        __syncwarp();
+        rank[r] = before + (uint32_t)__popc(peers & lt);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nb; d += kSortThreads) {
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; w++) {
+            uint32_t t = wcnt[w][d];
+            wcnt[w][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortIpt; r++) {
+        int64_t p = base + r * 32 + lane;
+        if (p < n) {
+            uint32_t dg = (k[r] >> shift) & mask;
+            uint32_t pos = gbase[dg] + wcnt[warp][dg] + rank[r];
+            keys_out[pos] = k[r];
+            vals_out[pos] = v[r];
+        }
+    }
+}
+
+// ---- K3: run-length reduce -------------------------------------------------
+// Tile of 4096 sorted positions; thread t owns 16 consecutive positions.  A
+// position starts a run (a distinct (term, doc) pair) when its pair differs
+// from the previous position's.
+__device__ __forceinline__ uint32_t heads_in_chunk(const uint32_t* __restrict__ keys,
+                                                   const uint32_t* __restrict__ vals,
+                                                   int64_t n, int64_t p0, uint32_t& flags)
+{
+    uint32_t pk, pv;
+    if (p0 == 0) {
+        pk = ~keys[0];
+        pv = 0;
+    } else {
+        pk = keys[p0 - 1];
+        pv = vals[p0 - 1];
+    }
+    uint32_t c = 0;
+    flags = 0;
+#pragma unroll
+    for (int i = 0; i < kSortIpt; i++) {
+        int64_t p = p0 + i;
+        if (p < n) {
+            uint32_t kk = keys[p], vv = vals[p];
+            if (kk != pk || vv != pv) {
+                flags |= 1u << i;
+                c++;
+            }
+            pk = kk;
+            pv = vv;
+        }
+    }
+    return c;
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+    k_rle_count(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t n,
+                uint32_t* __restrict__ tile_heads)
+{
+    __shared__ uint32_t buf[33];
+    const int64_t p0 = (int64_t)blockIdx.x * kSortTile + threadIdx.x * kSortIpt;
+    uint32_t flags = 0, c = 0;
+    if (p0 < n)
+        c = heads_in_chunk(keys, vals, n, p0, flags);
+    uint32_t tot;
+    block_exclusive_sum(c, buf, &tot);
+    if (threadIdx.x == 0)
+        tile_heads[blockIdx.x] = tot;
+}
+
+// Writes one CSC entry per run: its start position (TF = distance to the next
+// start), its term (for the score kernel) and its doc id (the CSC row index).
+__global__ void __launch_bounds__(kSortThreads)
+    k_rle_emit(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t n,
+               const uint32_t* __restrict__ tile_off, const uint32_t* __restrict__ d_nnz,
+               int32_t* __restrict__ run_pos, int32_t* __restrict__ run_term,
+               int32_t* __restrict__ indices)
+{
+    __shared__ uint32_t buf[33];
+    const int64_t p0 = (int64_t)blockIdx.x * kSortTile + threadIdx.x * kSortIpt;
+    uint32_t flags = 0, c = 0;
+    if (p0 < n)
+        c = heads_in_chunk(keys, vals, n, p0, flags);
+    uint32_t tot;
+    uint32_t j = block_exclusive_sum(c, buf, &tot) + tile_off[blockIdx.x];
+    while (flags) {
+        int i = __ffs(flags) - 1;
+        flags &= flags - 1;
+        int64_t p = p0 + i;
+        run_pos[j] = (int32_t)p;
+        run_term[j] = (int32_t)keys[p];
+        indices[j] = (int32_t)vals[p];
+        j++;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        run_pos[*d_nnz] = (int32_t)n;
+}
+
+// ---- K4/K5: column starts -------------------------------------------------
+// indptr[t] = number of runs whose term is < t (runs are term-major), i.e.
+// the exclusive prefix sum of DF; found by a lower bound per term.
+__global__ void k_indptr(const int32_t* __restrict__ run_term, const uint32_t* __restrict__ d_nnz,
+                         int32_t vocab, int64_t* __restrict__ indptr)
+{
+    const int64_t nnz = *d_nnz;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= vocab;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = nnz;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (run_term[mid] < t)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        indptr[t] = lo;
+    }
+}
+
+// ---- K6: per-term IDF, S0 and FP32 coefficient ------------------------------
+// Written in simplified but equal forms: Lucene's argument
+// (N - DF + 0.5)/(DF + 0.5) + 1 equals (N + 1)/(DF + 0.5).
+__device__ double idf_of(int variant, double n, double df)
+{
+    if (df <= 0.0)
+        return 0.0;  // a term that occurs nowhere contributes nothing
+    switch (variant) {
+    case BM25_LUCENE:
+    case BM25_L:
+        return log((n + 1.0) / (df + 0.5));
+    case BM25_ROBERTSON:
+        return log((n - df + 0.5) / (df + 0.5));
+    case BM25_ATIRE:
+        return log(n / df);
+    default:  // BM25_PLUS
+        return log((n + 1.0) / df);
+    }
+}
+
+__global__ void k_idf(const int64_t* __restrict__ indptr, int32_t vocab, int64_t n_docs,
+                      int variant, double k1, double delta, int32_t* __restrict__ df_out,
+                      double* __restrict__ idf_out, double* __restrict__ s0_out,
+                      float* __restrict__ coef)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < vocab;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t df = indptr[t + 1] - indptr[t];
+        double w = idf_of(variant, (double)n_docs, (double)df);
+        double s0 = 0.0, c = w;
+        if (variant == BM25_ATIRE || variant == BM25_PLUS)
+            c = w * (k1 + 1.0);
+        if (variant == BM25_L) {
+            s0 = w * (k1 + 1.0) * delta / (k1 + delta);
+            c = w * (k1 + 1.0) * k1 / (k1 + delta);
+        } else if (variant == BM25_PLUS) {
+            s0 = w * delta;
+        }
+        df_out[t] = (int32_t)df;
+        idf_out[t] = w;
+        s0_out[t] = s0;
+        coef[t] = (float)c;
+    }
+}
+
+// ---- K7: scores ----------------------------------------------------------
+// FP32 per entry, in forms free of cancellation (S - S0 written out):
+//   Lucene, Robertson:  coef TF / (TF + k1 K_D)                  coef = IDF
+//   ATIRE, BM25+:       coef TF / (TF + k1 K_D)                  coef = IDF (k1+1)
+//   BM25L:              coef c / (k1 + delta + c), c = TF / K_D  coef = IDF (k1+1) k1/(k1+delta)
+__global__ void k_score(const int32_t* __restrict__ run_pos, const int32_t* __restrict__ run_term,
+                        const int32_t* __restrict__ indices, const uint32_t* __restrict__ d_nnz,
+                        const float* __restrict__ coef, const float* __restrict__ len_factor,
+                        int variant, float k1_plus_delta, int32_t* __restrict__ tf_out,
+                        float* __restrict__ data)
+{
+    const int64_t nnz = *d_nnz;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int32_t tf = run_pos[j + 1] - run_pos[j];
+        float f = (float)tf;
+        float a = len_factor[indices[j]];
+        float c = coef[run_term[j]];
+        float s;
+        if (variant == BM25_L) {
+            float cc = f * a;
+            s = c * cc / (k1_plus_delta + cc);
+        } else {
+            s = c * f / (f + a);
+        }
+        tf_out[j] = tf;
+        data[j] = s;
+    }
+}
+
+// ---- memory --------------------------------------------------------------
+cudaMemPool_t g_pools[64];
+std::mutex g_pool_mu;
+
+int pool_for_device(int dev, cudaMemPool_t* out)
+{
+    std::lock_guard<std::mutex> g(g_pool_mu);
+    if (dev < 0 || dev >= 64)
+        return set_error(BM25_E_CUDA, "device ordinal %d out of range", dev);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        BM25_CUDA_TRY(cudaMemPoolCreate(&g_pools[dev], &props));
+        uint64_t keep = ~0ull;  // keep freed blocks for the next build
+        BM25_CUDA_TRY(cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+    }
+    *out = g_pools[dev];
+    return BM25_OK;
+}
+
+template <typename T>
+int pool_alloc(T** p, int64_t count, cudaMemPool_t pool, cudaStream_t s)
+{
+    size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+    cudaError_t e = cudaMallocFromPoolAsync((void**)p, bytes, pool, s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return set_error(e == cudaErrorMemoryAllocation ? BM25_E_OOM : BM25_E_CUDA,
+                         "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    return BM25_OK;
+}
+
+struct TempSet {
+    std::vector<void*> ptrs;
+    cudaStream_t s;
+    explicit TempSet(cudaStream_t st) : s(st) {}
+    template <typename T>
+    int alloc(T** p, int64_t count, cudaMemPool_t pool)
+    {
+        int r = pool_alloc(p, count, pool, s);
+        if (r == BM25_OK)
+            ptrs.push_back((void*)*p);
+        return r;
+    }
+    ~TempSet()
+    {
+        for (void* p : ptrs)
+            cudaFreeAsync(p, s);
+    }
+};
+
+int grid_for(int64_t n, int threads, int max_blocks)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1)
+        b = 1;
+    if (b > max_blocks)
+        b = max_blocks;
+    return (int)b;
+}
+
+}  // namespace
+
+int pool_for_current_device(cudaMemPool_t* out)
+{
+    int dev = 0;
+    BM25_CUDA_TRY(cudaGetDevice(&dev));
+    return pool_for_device(dev, out);
+}
+
+// Index arrays live in the library's stream-ordered pool (freed blocks are
+// kept for the next build).  Sizes come from the index's scalars.
+int alloc_index_arrays(bm25_index* ix, cudaStream_t s, bool fixed, bool per_entry)
+{
+    cudaMemPool_t pool;
+    BM25_TRY(pool_for_current_device(&pool));
+    if (fixed) {
+        BM25_TRY(pool_alloc(&ix->indptr, (int64_t)ix->vocab + 1, pool, s));
+        BM25_TRY(pool_alloc(&ix->df, ix->vocab, pool, s));
+        BM25_TRY(pool_alloc(&ix->doc_len, ix->n_docs, pool, s));
+        BM25_TRY(pool_alloc(&ix->idf, ix->vocab, pool, s));
+        BM25_TRY(pool_alloc(&ix->s0, ix->vocab, pool, s));
+        BM25_TRY(pool_alloc(&ix->status, 1, pool, s));
+        BM25_CUDA_TRY(cudaMemsetAsync(ix->status, 0, sizeof(int), s));
+    }
+    if (per_entry) {
+        BM25_TRY(pool_alloc(&ix->indices, ix->nnz, pool, s));
+        BM25_TRY(pool_alloc(&ix->data, ix->nnz, pool, s));
+        BM25_TRY(pool_alloc(&ix->tf, ix->nnz, pool, s));
+    }
+    return BM25_OK;
+}
+
+void free_index_arrays(bm25_index* ix, cudaStream_t s)
+{
+    void* ps[] = {ix->indptr, ix->indices, ix->data, ix->tf, ix->df,
+                  ix->doc_len, ix->idf, ix->s0, ix->status};
+    for (void* p : ps)
+        if (p)
+            cudaFreeAsync(p, s);
+    ix->indptr = nullptr;
+    ix->indices = nullptr;
+    ix->data = nullptr;
+    ix->tf = nullptr;
+    ix->df = nullptr;
+    ix->doc_len = nullptr;
+    ix->idf = nullptr;
+    ix->s0 = nullptr;
+    ix->status = nullptr;
+}
+
+int build_index_device(const int32_t* d_tokens, int64_t n_tokens, const int64_t* d_offsets,
+                       int64_t n_docs, int32_t vocab, int variant, double k1, double b,
+                       double delta, cudaStream_t s, bm25_index** out)
+{
+    DeviceInfo di;
+    BM25_TRY(device_info(&di));
+    cudaMemPool_t pool;
+    BM25_TRY(pool_for_device(di.device, &pool));
+    const int max_blocks = di.sm_count * 16;
+    const double lavg = (double)n_tokens / (double)n_docs;
+    const int64_t T = n_tokens;
+
+    bm25_index* ix = new bm25_index();
+    ix->device = di.device;
+    ix->n_docs = n_docs;
+    ix->n_tokens = n_tokens;
+    ix->vocab = vocab;
+    ix->variant = variant;
+    ix->k1 = k1;
+    ix->b = b;
+    ix->delta = delta;
+    ix->lavg = lavg;
+    auto fail = [&](int code) {
+        free_index_arrays(ix, s);
+        delete ix;
+        return code;
+    };
+    {
+        int r = alloc_index_arrays(ix, s, true, false);  // arrays sized by V and N
+        if (r != BM25_OK)
+            return fail(r);
+    }
+    int rc = BM25_OK;
+    uint32_t h_nnz = 0;
+    int h_status = 0;
+    {
+        TempSet tmp(s);
+        int32_t* tok_doc = nullptr;
+        float* len_factor = nullptr;
+        uint32_t *ka = nullptr, *va = nullptr, *kb = nullptr, *vb = nullptr;
+        uint32_t *counts = nullptr, *scan_tmp = nullptr, *tile_heads = nullptr, *d_total = nullptr;
+        int32_t *run_pos = nullptr, *run_term = nullptr;
+        float* coef = nullptr;
+        const int64_t n_tiles = (T + kSortTile - 1) / kSortTile;
+        int nbits = 1;
+        while (nbits < 31 && ((int64_t)1 << nbits) < (int64_t)vocab)
+            nbits++;
+        const int passes = (nbits + kMaxDigitBits - 1) / kMaxDigitBits;
+        const int dbits = (nbits + passes - 1) / passes;
+        const int64_t ncounts = ((int64_t)1 << dbits) * n_tiles;
+        int r = BM25_OK;
+        if (r == BM25_OK) r = tmp.alloc(&tok_doc, T, pool);
+        if (r == BM25_OK) r = tmp.alloc(&len_factor, n_docs, pool);
+        if (r == BM25_OK) r = tmp.alloc(&ka, T, pool);
+        if (r == BM25_OK) r = tmp.alloc(&va, T, pool);
+        if (r == BM25_OK) r = tmp.alloc(&kb, T, pool);
+        if (r == BM25_OK) r = tmp.alloc(&counts, ncounts, pool);
+        if (r == BM25_OK) r = tmp.alloc(&scan_tmp, scan_tmp_elems(ncounts > n_tiles ? ncounts : n_tiles), pool);
+        if (r == BM25_OK) r = tmp.alloc(&tile_heads, n_tiles, pool);
+        if (r == BM25_OK) r = tmp.alloc(&d_total, 2, pool);
+        if (r == BM25_OK) r = tmp.alloc(&coef, vocab, pool);
+        if (r != BM25_OK)
+            return fail(r);
+        vb = (uint32_t*)tok_doc;  // reused once pass 0 has consumed the doc ids
+
+        {
+
+            ProfileScope ps_("k_doc_prep", s);
+
+            k_doc_prep<<<grid_for(n_docs * 32, 256, max_blocks), 256, 0, s>>>(
+                d_offsets, n_docs, T, tok_doc, ix->doc_len, len_factor, variant, k1, b, lavg,
+                ix->status);
+
+        }
+        count_launch();
+        BM25_LAUNCH_CHECK();
+
+        const uint32_t* kin = (const uint32_t*)d_tokens;
+        const uint32_t* vin = (const uint32_t*)tok_doc;
+        if (T > 0) {
+            for (int pass = 0; pass < passes; pass++) {
+                uint32_t* kout = (pass % 2 == 0) ? ka : kb;
+                uint32_t* vout = (pass % 2 == 0) ? va : vb;
+                const int shift = pass * dbits;
+                const int bits = (nbits - shift < dbits) ? nbits - shift : dbits;
+                {
+                    ProfileScope ps_("k_radix_upsweep", s);
+                    k_radix_upsweep<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(
+                        kin, T, shift, bits, counts, n_tiles, pass == 0 ? (uint32_t)vocab : 0u,
+                        ix->status);
+                }
+                count_launch();
+                BM25_LAUNCH_CHECK();
+                BM25_TRY(exclusive_scan_u32(counts, counts, ((int64_t)1 << bits) * n_tiles,
+                                            d_total, scan_tmp, s));
+                {
+                    ProfileScope ps_("k_radix_downsweep", s);
+                    k_radix_downsweep<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(
+                        kin, vin, kout, vout, T, shift, bits, counts, n_tiles);
+                }
+                count_launch();
+                BM25_LAUNCH_CHECK();
+                kin = kout;
+                vin = vout;
+            }
+            {
+                ProfileScope ps_("k_rle_count", s);
+                k_rle_count<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(kin, vin, T, tile_heads);
+            }
+            count_launch();
+            BM25_LAUNCH_CHECK();
+            BM25_TRY(exclusive_scan_u32(tile_heads, tile_heads, n_tiles, d_total, scan_tmp, s));
+        } else {
+            BM25_CUDA_TRY(cudaMemsetAsync(d_total, 0, sizeof(uint32_t), s));
+        }
+        BM25_CUDA_TRY(cudaMemcpyAsync(&h_nnz, d_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        BM25_CUDA_TRY(cudaMemcpyAsync(&h_status, ix->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        BM25_CUDA_TRY(cudaStreamSynchronize(s));
+        if (h_status != 0) {
+            rc = set_error(h_status, "index build: a token id is outside [0, %d) or the doc "
+                                     "offsets are malformed", vocab);
+        } else {
+            const int64_t nnz = h_nnz;
+            ix->nnz = nnz;
+            int r2 = alloc_index_arrays(ix, s, false, true);  // arrays sized by nnz
+            if (r2 == BM25_OK) r2 = tmp.alloc(&run_pos, nnz + 1, pool);
+            if (r2 == BM25_OK) r2 = tmp.alloc(&run_term, nnz, pool);
+            if (r2 != BM25_OK)
+                return fail(r2);
+            if (T > 0) {
+                {
+                    ProfileScope ps_("k_rle_emit", s);
+                    k_rle_emit<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(
+                        kin, vin, T, tile_heads, d_total, run_pos, run_term, ix->indices);
+                }
+                count_launch();
+                BM25_LAUNCH_CHECK();
+            }
+            {
+                ProfileScope ps_("k_indptr", s);
+                k_indptr<<<grid_for((int64_t)vocab + 1, 256, max_blocks), 256, 0, s>>>(
+                    run_term, d_total, vocab, ix->indptr);
+            }
+            {
+                ProfileScope ps_("k_idf", s);
+                k_idf<<<grid_for(vocab, 256, max_blocks), 256, 0, s>>>(
+                    ix->indptr, vocab, n_docs, variant, k1, delta, ix->df, ix->idf, ix->s0, coef);
+            }
+            count_launch(2);
+            BM25_LAUNCH_CHECK();
+            if (nnz > 0) {
+                {
+                    ProfileScope ps_("k_score", s);
+                    k_score<<<grid_for(nnz, 256, max_blocks), 256, 0, s>>>(
+                        run_pos, run_term, ix->indices, d_total, coef, len_factor, variant,
+                        (float)(k1 + delta), ix->tf, ix->data);
+                }
+                count_launch();
+                BM25_LAUNCH_CHECK();
+            }
+        }
+    }  // temporaries are released (stream-ordered) here
+    if (rc != BM25_OK)
+        return fail(rc);
+    *out = ix;
+    return BM25_OK;
+}
+
+}  // namespace bm25

@@ -1,0 +1,141 @@
+// Internal declarations shared by the libbm25gpu translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <mutex>
+
+#include "bm25.h"
+
+namespace bm25 {
+
+// ---- errors -----------------------------------------------------------
+int set_error(int code, const char* fmt, ...);
+void clear_error();
+
+#define BM25_CUDA_TRY(expr)                                                         \
+    do {                                                                            \
+        cudaError_t e_ = (expr);                                                    \
+        if (e_ != cudaSuccess)                                                      \
+            return ::bm25::set_error(e_ == cudaErrorMemoryAllocation ? BM25_E_OOM   \
+                                                                     : BM25_E_CUDA, \
+                                     "%s failed: %s (%s:%d)", #expr,                \
+                                     cudaGetErrorString(e_), __FILE__, __LINE__);   \
+    } while (0)
+
+#define BM25_LAUNCH_CHECK() BM25_CUDA_TRY(cudaGetLastError())
+
+#define BM25_TRY(expr)          \
+    do {                        \
+        int r_ = (expr);        \
+        if (r_ != BM25_OK)      \
+            return r_;          \
+    } while (0)
+
+// Kernel launch accounting (bm25_launch_count).
+extern std::atomic<int64_t> g_launches;
+inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Brackets one kernel launch with CUDA events while bm25_profile_begin() is
+// active (no-op otherwise, and while the stream is being captured).
+class ProfileScope {
+public:
+    ProfileScope(const char* name, cudaStream_t s);
+    ~ProfileScope();
+    ProfileScope(const ProfileScope&) = delete;
+    ProfileScope& operator=(const ProfileScope&) = delete;
+
+private:
+    const char* name_;
+    cudaStream_t s_;
+    void* a_ = nullptr;
+};
+
+// Device properties of the current device, cached.
+struct DeviceInfo {
+    int device = -1;
+    int sm_count = 0;
+    int max_smem_optin = 0;
+    int l2_bytes = 0;
+};
+int device_info(DeviceInfo* out);
+
+// ---- the index --------------------------------------------------------
+struct Plan {
+    int accumulator = BM25_ACC_AUTO;
+    int32_t tile_docs = 16384;
+};
+
+}  // namespace bm25
+
+struct bm25_index {
+    int device = 0;
+    int64_t n_docs = 0, n_tokens = 0, nnz = 0;
+    int32_t vocab = 0;
+    int variant = 0;
+    double k1 = 0, b = 0, delta = 0, lavg = 0;
+    // device arrays (owned)
+    int64_t* indptr = nullptr;   // [vocab+1]
+    int32_t* indices = nullptr;  // [nnz]   doc ids, ascending per term
+    float* data = nullptr;       // [nnz]   S(t,D) - S0(t), FP32
+    int32_t* tf = nullptr;       // [nnz]
+    int32_t* df = nullptr;       // [vocab]
+    int32_t* doc_len = nullptr;  // [n_docs]
+    double* idf = nullptr;       // [vocab]
+    double* s0 = nullptr;        // [vocab]
+    int* status = nullptr;       // device status word (first error code)
+    bm25::Plan plan;
+    bm25_workspace* default_ws = nullptr;
+    std::mutex mu;
+};
+
+struct bm25_workspace {
+    int device = 0;
+    int32_t max_queries = 0;
+    int64_t max_query_tokens = 0;
+    int32_t max_k = 0;
+    int64_t max_tiles = 0;       // doc tiles the buffers are sized for
+    // device scratch (owned)
+    int32_t* q_tokens = nullptr;     // staging for the _host entry point
+    int64_t* q_offsets = nullptr;    // staging for the _host entry point
+    int32_t* out_ids = nullptr;      // staging for the _host entry point
+    float* out_scores = nullptr;     // staging for the _host entry point
+    double* shift = nullptr;         // [max_queries]  sum_i S0(q_i)
+    int32_t* seg = nullptr;          // [max_query_tokens * (max_tiles + 1)]
+    unsigned long long* cand = nullptr;  // [max_queries * max_tiles * max_k]
+    size_t seg_cap = 0, cand_cap = 0;    // element capacities
+    size_t staging_cap[4] = {0, 0, 0, 0};  // byte capacities of the staging buffers
+    bool owns_staging = false;
+};
+
+namespace bm25 {
+
+// ---- build (index_build.cu) --------------------------------------------
+int build_index_device(const int32_t* d_tokens, int64_t n_tokens, const int64_t* d_offsets,
+                       int64_t n_docs, int32_t vocab, int variant, double k1, double b,
+                       double delta, cudaStream_t stream, bm25_index** out);
+// Allocates the index's V/N-sized arrays (fixed) and/or its nnz-sized arrays
+// (per_entry) from the library's pool on stream s.
+int alloc_index_arrays(bm25_index* ix, cudaStream_t s, bool fixed, bool per_entry);
+void free_index_arrays(bm25_index* ix, cudaStream_t s);
+int pool_for_current_device(cudaMemPool_t* out);
+
+// ---- retrieval (retrieve.cu) -------------------------------------------
+int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_tokens,
+                    const int64_t* q_offsets, int32_t n_queries, int64_t n_query_tokens,
+                    int32_t k, int32_t* out_ids, float* out_scores, int accumulator,
+                    int32_t tile_docs, cudaStream_t stream);
+int workspace_reserve(const bm25_index* ix, bm25_workspace* ws, int32_t n_queries,
+                      int64_t n_query_tokens, int32_t kprime, int64_t n_tiles);
+void workspace_release(bm25_workspace* ws);
+
+// ---- scan (scan.cu) ------------------------------------------------------
+// Exclusive prefix sum of n uint32 values (in and out may alias).  The total
+// goes to d_total (device).  tmp needs scan_tmp_elems(n) uint32 of scratch.
+int64_t scan_tmp_elems(int64_t n);
+int exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* d_total,
+                       uint32_t* tmp, cudaStream_t stream);
+
+}  // namespace bm25

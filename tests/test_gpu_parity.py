@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Structure (|D|, TF, DF, indptr, indices) must be bit-exact; IDF and S0 are
+FP64 on both sides; stored scores S - S0 and returned scores are FP32 and
+must lie within 1e-5 of the oracle's scale; top-k ids must equal the
+oracle's up to ties within that tolerance (oracle/compare.py).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.compare import check_topk
+from paper_2407_03618_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = ["lucene", "robertson", "atire", "bm25l", "bm25+"]
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "toy_corpus.json")
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return torch.device("cuda:0")
+
+
+def _to(dev, a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+
+def _build(dev, corpus, variant, k1=1.5, b=0.75, delta=0.5):
+    from paper_2407_03618_gb300 import bm25
+    return bm25.Index.build(_to(dev, corpus.tokens), _to(dev, corpus.doc_offsets), corpus.vocab,
+                            variant, k1, b, delta)
+
+
+def _check_structure(ix, orc, k1=1.5, b=0.75, delta=0.5):
+    ex = ix.export()
+    assert ex["nnz"] == orc.nnz
+    assert np.array_equal(ex["doc_len"], orc.doc_len.astype(np.int32))
+    assert np.array_equal(ex["df"], orc.df.astype(np.int32))
+    assert np.array_equal(ex["indptr"], orc.indptr)
+    assert np.array_equal(ex["indices"], orc.indices)
+    assert np.array_equal(ex["tf"], orc.csc_tf)
+    assert ex["lavg"] == pytest.approx(orc.lavg, rel=1e-15)
+    np.testing.assert_allclose(ex["idf"], orc.idf, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(ex["s0"], orc.s0, rtol=1e-13, atol=1e-15)
+    # stored S - S0 in FP32: within 1e-5 of the term's full score scale
+    full = orc.csc_delta + np.repeat(orc.s0, np.diff(orc.indptr))
+    scale = np.maximum(np.abs(orc.csc_delta), np.abs(full))
+    err = np.abs(ex["data"].astype(np.float64) - orc.csc_delta)
+    assert (err <= 1e-5 * scale + 1e-30).all(), f"max rel err {np.max(err / (scale + 1e-300))}"
+    return ex
+
+
+def _check_retrieval(dev, ix, orc, queries, k, sample=None, where=""):
+    ids, sc = ix.retrieve(_to(dev, queries.tokens), _to(dev, queries.offsets), k)
+    ix.sync_status()
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    qs = range(queries.n_queries) if sample is None else sample
+    for q in qs:
+        full, ab = oracle.score_all(orc, queries.query(q), with_abs=True)
+        check_topk(ids[q], sc[q], full, ab, k, where=f"{where} q{q}")
+    return ids, sc
+
+
+# ------------------------------------------------------------- build -----
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_toy_corpus_build_and_retrieve(torch_dev, variant):
+    with open(GOLDEN) as f:
+        g = json.load(f)
+    docs = g["docs"]
+    c = synth.Corpus(np.array([t for d in docs for t in d], np.int32),
+                     synth.offsets_from_lengths(np.array([len(d) for d in docs])), g["vocab"])
+    ix = _build(torch_dev, c, variant)
+    ex = ix.export()
+    assert ex["doc_len"].tolist() == g["doc_len"]
+    assert ex["df"].tolist() == g["df"]
+    assert ex["indptr"].tolist() == g["indptr"]
+    assert ex["indices"].tolist() == g["indices"]
+    np.testing.assert_allclose(ex["idf"], g["variants"][variant]["idf"], atol=5e-11)
+    for case in g["variants"][variant]["queries"]:
+        q = synth.Queries(np.array(case["q"], np.int32), np.array([0, len(case["q"])], np.int64))
+        ids, sc = ix.retrieve(_to(torch_dev, q.tokens), _to(torch_dev, q.offsets), 3)
+        ix.sync_status()
+        assert ids.cpu().numpy()[0].tolist() == case["order"]
+        np.testing.assert_allclose(sc.cpu().numpy()[0], np.array(case["B"])[case["order"]],
+                                   rtol=1e-6, atol=1e-6)
+    ix.close()
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_build_parity_random_small(torch_dev, seed):
+    rng = np.random.default_rng(1000 + seed)
+    c = synth.random_tiny_corpus(rng, max_docs=int(rng.integers(1, 400)),
+                                 max_vocab=int(rng.integers(1, 3000)), max_len=40)
+    variant = VARIANTS[seed % 5]
+    k1, b, d = float(rng.uniform(0.3, 2.0)), float(rng.uniform(0, 1)), float(rng.uniform(0, 1))
+    ix = _build(torch_dev, c, variant, k1, b, d)
+    orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.VARIANTS[variant], k1, b, d)
+    _check_structure(ix, orc, k1, b, d)
+    ix.close()
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_tiny_workload_build_and_retrieve(torch_dev, variant):
+    """2,000 docs, vocab 5,000, Zipf 1.1, Poisson(60); 100 queries; k=10."""
+    w = synth.WORKLOADS["tiny"]
+    c, q = w.corpus(), w.queries()
+    ix = _build(torch_dev, c, variant)
+    orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.VARIANTS[variant], 1.5, 0.75, 0.5)
+    _check_structure(ix, orc)
+    for k in (1, 10, 100):
+        _check_retrieval(torch_dev, ix, orc, q, k, where=f"{variant} k={k}")
+    ix.close()
+
+
+def test_sort_spans_many_tiles_and_passes(torch_dev):
+    """Enough tokens for thousands of sort tiles, a vocabulary needing three
+    radix passes, and a ragged last tile."""
+    c = synth.make_corpus(40_001, 150_000, 1.05, ("lognormal", 60, 0.6), seed=5)
+    ix = _build(torch_dev, c, "lucene")
+    orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, 0)
+    _check_structure(ix, orc)
+    ix.close()
+
+
+# --------------------------------------------------------- retrieval -----
+
+@pytest.mark.parametrize("tile_docs", [1024, 2048, 16384])
+def test_retrieval_across_tiles(torch_dev, tile_docs):
+    """Small doc tiles force many (query, tile) items and a ragged last tile."""
+    c = synth.make_corpus(9_999, 3_000, 1.1, ("poisson", 30), seed=2)
+    q = synth.make_queries(64, 3_000, 1.1, ("uniform", 0, 12), seed=3)
+    ix = _build(torch_dev, c, "bm25+")
+    ix.set_plan(0, tile_docs)
+    orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.BM25PLUS)
+    for k in (1, 7, 100, 1000):
+        _check_retrieval(torch_dev, ix, orc, q, k, where=f"W={tile_docs} k={k}")
+    ix.close()
+
+
+@pytest.mark.parametrize("variant", ["robertson", "atire"])
+def test_negative_and_zero_idf(torch_dev, variant):
+    """Robertson IDF < 0 for common terms, so untouched documents (score 0)
+    outrank matched ones; ATIRE IDF = 0 when DF = N."""
+    rng = np.random.default_rng(11)
+    n = 300
+    lens = rng.integers(1, 12, n)
+    tok = rng.integers(0, 6, int(lens.sum())).astype(np.int32)  # every term very common
+    tok[::7] = 0
+    c = synth.Corpus(tok, synth.offsets_from_lengths(lens), 6)
+    ix = _build(torch_dev, c, variant)
+    orc = oracle.build(c.tokens, c.doc_offsets, 6, oracle.VARIANTS[variant])
+    if variant == "robertson":
+        assert (orc.idf[:6] < 0).any()
+    q = synth.random_queries(rng, 6, 40, 5)
+    for k in (5, 50, 299, 300):
+        _check_retrieval(torch_dev, ix, orc, q, k, where=f"{variant} k={k}")
+    ix.close()
+
+
+def test_edge_cases(torch_dev):
+    """k > N, empty queries, duplicate tokens, DF = 0 terms, empty documents,
+    a single document and a one-term vocabulary."""
+    # empty docs, and terms 3,4 never occur
+    c = synth.Corpus(np.array([0, 1, 1, 2, 0], np.int32), np.array([0, 0, 3, 3, 5, 5], np.int64), 5)
+    for variant in VARIANTS:
+        ix = _build(torch_dev, c, variant)
+        orc = oracle.build(c.tokens, c.doc_offsets, 5, oracle.VARIANTS[variant])
+        _check_structure(ix, orc)
+        q = synth.Queries(np.array([1, 1, 0, 3, 4, 4, 2], np.int32),
+                          np.array([0, 0, 3, 5, 7], np.int64))  # empty, dups, DF=0, mixed
+        for k in (1, 3, 5, 9):
+            _check_retrieval(torch_dev, ix, orc, q, k, where=f"{variant} edge k={k}")
+        ix.close()
+    one = synth.Corpus(np.array([0, 0, 0], np.int32), np.array([0, 3], np.int64), 1)
+    ix = _build(torch_dev, one, "lucene")
+    orc = oracle.build(one.tokens, one.doc_offsets, 1, 0)
+    q = synth.Queries(np.array([0], np.int32), np.array([0, 1, 1], np.int64))
+    _check_retrieval(torch_dev, ix, orc, q, 4, where="single doc")
+    ix.close()
+    # a corpus of empty documents only
+    e = synth.Corpus(np.zeros(0, np.int32), np.zeros(4, np.int64), 3)
+    ix = _build(torch_dev, e, "bm25l")
+    assert ix.info()["nnz"] == 0
+    ids, sc = ix.retrieve(_to(torch_dev, np.array([1], np.int32)),
+                          _to(torch_dev, np.array([0, 1], np.int64)), 2)
+    ix.sync_status()
+    assert ids.cpu().numpy().tolist() == [[0, 1]]
+    assert sc.cpu().numpy().tolist() == [[0.0, 0.0]]
+    ix.close()
+
+
+def test_out_of_range_tokens_are_reported(torch_dev):
+    from paper_2407_03618_gb300 import bm25
+    c = synth.Corpus(np.array([0, 1, 2, 1], np.int32), np.array([0, 2, 4], np.int64), 3)
+    bad = synth.Corpus(np.array([0, 1, 7, 1], np.int32), c.doc_offsets, 3)
+    with pytest.raises(bm25.BM25Error) as e:
+        _build(torch_dev, bad, "lucene")
+    assert e.value.code == -2
+    neg = synth.Corpus(np.array([0, -1, 2, 1], np.int32), c.doc_offsets, 3)
+    with pytest.raises(bm25.BM25Error):
+        _build(torch_dev, neg, "lucene")
+    badoff = synth.Corpus(c.tokens, np.array([0, 3, 2], np.int64), 3)
+    with pytest.raises(bm25.BM25Error):
+        _build(torch_dev, badoff, "lucene")
+    ix = _build(torch_dev, c, "lucene")
+    ids, sc = ix.retrieve(_to(torch_dev, np.array([1, 9, -3], np.int32)),
+                          _to(torch_dev, np.array([0, 3], np.int64)), 2)
+    with pytest.raises(bm25.BM25Error) as e:
+        ix.sync_status()
+    assert e.value.code == -2
+    ix.sync_status()  # the status word was cleared
+    # the valid token still scored
+    orc = oracle.build(c.tokens, c.doc_offsets, 3, 0)
+    full, ab = oracle.score_all(orc, [1], with_abs=True)
+    check_topk(ids.cpu().numpy()[0], sc.cpu().numpy()[0], full, ab, 2)
+    ix.close()
+
+
+def test_host_entry_points_and_checkpoint(torch_dev):
+    from paper_2407_03618_gb300 import bm25
+    w = synth.WORKLOADS["tiny"]
+    c, q = w.corpus(), w.queries()
+    ix = _build(torch_dev, c, "bm25l")
+    ih = bm25.Index.build_host(c.tokens, c.doc_offsets, c.vocab, "bm25l")
+    a, b_ = ix.export(), ih.export()
+    for key in ("indptr", "indices", "tf", "df", "doc_len", "idf", "s0", "data"):
+        assert np.array_equal(a[key], b_[key]), key
+    ids_d, sc_d = ix.retrieve(_to(torch_dev, q.tokens), _to(torch_dev, q.offsets), 10)
+    ids_h, sc_h = ih.retrieve_host(q.tokens, q.offsets, 10)
+    assert np.array_equal(ids_d.cpu().numpy(), ids_h)
+    assert np.array_equal(sc_d.cpu().numpy(), sc_h)
+    # export -> import -> the same answers
+    im = bm25.Index.load_arrays(a)
+    ids_i, sc_i = im.retrieve(_to(torch_dev, q.tokens), _to(torch_dev, q.offsets), 10)
+    assert np.array_equal(ids_d.cpu().numpy(), ids_i.cpu().numpy())
+    assert np.array_equal(sc_d.cpu().numpy(), sc_i.cpu().numpy())
+    for x in (ix, ih, im):
+        x.close()
+
+
+def test_workspace_and_bad_retrieve_args(torch_dev):
+    from paper_2407_03618_gb300 import bm25
+    w = synth.WORKLOADS["tiny"]
+    c, q = w.corpus(), w.queries()
+    ix = _build(torch_dev, c, "lucene")
+    orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, 0)
+    ws = bm25.Workspace(ix, q.n_queries, q.tokens.shape[0], 10)
+    ids, sc = ix.retrieve(_to(torch_dev, q.tokens), _to(torch_dev, q.offsets), 10, workspace=ws,
+                          accumulator=bm25.ACC_SMEM_TILED, tile_docs=1024)
+    ix.sync_status()
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    for i in range(q.n_queries):
+        full, ab = oracle.score_all(orc, q.query(i), with_abs=True)
+        check_topk(ids[i], sc[i], full, ab, 10)
+    for k in (0, -3):
+        with pytest.raises(bm25.BM25Error):
+            ix.retrieve(_to(torch_dev, q.tokens), _to(torch_dev, q.offsets), k)
+    with pytest.raises(bm25.BM25Error):
+        ix.set_plan(0, 1000)
+    ws.close()
+    ix.close()
