@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--k", type=int, default=10)
     p.add_argument("--plain-queries", type=int, default=1000)
     p.add_argument("--cpu-sample-queries", type=int, default=48)
+    p.add_argument("--queries", type=int, default=0,
+                   help="use only the first N queries of the batch (small profiler cases)")
     p.add_argument("--no-extras", action="store_true",
                    help="only the timed steps (used for profiler runs)")
     return p.parse_args()
@@ -208,6 +210,8 @@ def main():
     prm = w.params
     corpus = w.corpus()
     queries = w.queries(seed=1 + rank)  # each rank answers its own batch (weak scaling)
+    if args.queries:
+        queries = queries.subset(np.arange(min(args.queries, queries.n_queries)))
     k = args.k
     nq = queries.n_queries
 

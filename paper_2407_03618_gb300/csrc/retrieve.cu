@@ -33,7 +33,8 @@ constexpr int kMergeThreads = 512;
 __global__ void k_query_prep(const int32_t* __restrict__ q_tokens, int64_t n_tok,
                              const int64_t* __restrict__ q_off, int32_t nq,
                              const double* __restrict__ s0, int32_t vocab,
-                             double* __restrict__ shift, int* status)
+                             double* __restrict__ shift, uint32_t* __restrict__ thresh,
+                             uint32_t* __restrict__ ccount, int* status)
 {
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
          q += (int64_t)gridDim.x * blockDim.x) {
@@ -53,6 +54,8 @@ __global__ void k_query_prep(const int32_t* __restrict__ q_tokens, int64_t n_tok
             sum += s0[t];
         }
         shift[q] = sum;
+        thresh[q] = 0u;  // below every real score key
+        ccount[q] = 0u;
     }
 }
 
@@ -103,8 +106,8 @@ __global__ void k_seg_bounds(const int32_t* __restrict__ q_tokens, int64_t n_tok
 // final prefix.
 struct SelectState {
     uint32_t hist[256];
-    u64 prefix, pmask;
-    uint32_t need, bucket, ctr, cnt;
+    u64 prefix, pmask, minkey;
+    uint32_t need, bucket, ctr, cnt, tau, base;
     uint32_t red[33];
 };
 
@@ -179,20 +182,80 @@ __device__ void block_select(SelectState& st, uint32_t n, uint32_t k, ForEach fo
     __syncthreads();
 }
 
+// Same selection over an indexable candidate set: get(i) returns the key of
+// candidate i < n.  The loops are warp-uniform, so histogram updates are
+// aggregated per warp with __match_any_sync (candidates that share a score
+// prefix would otherwise serialise on one counter).
+template <class Get, class Emit>
+__device__ void block_select_idx(SelectState& st, uint32_t n, uint32_t k, Get get, Emit emit)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t stride = blockDim.x;
+    const uint32_t base0 = threadIdx.x & ~31u;
+    if (n <= k) {
+        for (uint32_t i = threadIdx.x; i < n; i += stride)
+            emit(get(i));
+        __syncthreads();
+        return;
+    }
+    if (threadIdx.x == 0) {
+        st.prefix = 0;
+        st.pmask = 0;
+        st.need = k;
+    }
+    for (int pass = 0; pass < 8; pass++) {
+        const int shift = 56 - 8 * pass;
+        for (int i = threadIdx.x; i < 256; i += blockDim.x)
+            st.hist[i] = 0;
+        __syncthreads();
+        const u64 pm = st.pmask, pf = st.prefix;
+        for (uint32_t b = base0; b < n; b += stride) {
+            const uint32_t i = b + lane;
+            uint32_t dg = 0xffffffffu;
+            if (i < n) {
+                u64 key = get(i);
+                if ((key & pm) == pf)
+                    dg = (uint32_t)(key >> shift) & 0xffu;
+            }
+            uint32_t peers = __match_any_sync(0xffffffffu, dg);
+            if (dg != 0xffffffffu && (peers & lanemask_lt()) == 0)
+                atomicAdd(&st.hist[dg], (uint32_t)__popc(peers));
+        }
+        __syncthreads();
+        if (threadIdx.x < 32)
+            select_bucket(st, shift);
+        __syncthreads();
+        if (st.bucket == st.need)
+            break;
+    }
+    const u64 pm = st.pmask, pf = st.prefix;
+    for (uint32_t i = threadIdx.x; i < n; i += stride) {
+        u64 key = get(i);
+        if ((key & pm) >= pf)
+            emit(key);
+    }
+    __syncthreads();
+}
+
 // ---- R2 -----------------------------------------------------------------------
 // Dynamic shared memory: acc[W] FP32 | mask[W/32] | SelectState | token stage.
+constexpr uint32_t kSurvCap = 2048;  // survivors kept in shared memory per item
+
 struct TileStage {
     int32_t lo[kTokChunk];
     int32_t pre[kTokChunk + 1];
     uint32_t scan[33];
+    uint32_t n_surv, n_pos;
+    uint16_t surv[kSurvCap];  // local doc ids of the item's candidates
 };
 
-__global__ void __launch_bounds__(kTileThreads)
+__global__ void __launch_bounds__(kTileThreads, 3)
     k_tile_topk(const int32_t* __restrict__ q_tokens, int64_t n_tok,
                 const int64_t* __restrict__ q_off, int32_t nq, int64_t n_docs,
                 const int32_t* __restrict__ indices, const float* __restrict__ data,
                 const int32_t* __restrict__ seg, int32_t W, int32_t n_tiles, int32_t kprime,
-                u64* __restrict__ cand)
+                uint32_t* __restrict__ thresh, uint32_t* __restrict__ ccount,
+                u64* __restrict__ cand, int64_t cand_cap)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     float* acc = reinterpret_cast<float*>(smem);
@@ -209,33 +272,76 @@ __global__ void __launch_bounds__(kTileThreads)
 
     const int64_t n_items = (int64_t)nq * n_tiles;
     const int64_t per = (int64_t)n_tiles + 1;
+    // tile-major order: tile 0 of every query first, so that the running
+    // per-query threshold is usually known when a query's later tiles run,
+    // and the segments in flight at once all belong to one doc tile
+    auto item_qt = [&](int64_t item, int64_t& q, int32_t& tile) {
+        tile = (int32_t)(item / nq);
+        q = item - (int64_t)tile * nq;
+    };
+    // warp 0 prefetches the first token chunk's segment bounds of its next
+    // item (lane l: tokens 2l, 2l+1) and thread 0 the query's threshold
+    int32_t pf_lo0 = 0, pf_lo1 = 0, pf_hi0 = 0, pf_hi1 = 0;
+    uint32_t pf_tau = 0;
+#define BM25_PREFETCH(ITEM)                                                          \
+    do {                                                                             \
+        const int64_t it_ = (ITEM);                                                  \
+        if (tid < 32 && it_ < n_items) {                                             \
+            int64_t q_;                                                              \
+            int32_t t_;                                                              \
+            item_qt(it_, q_, t_);                                                    \
+            int64_t a_ = q_off[q_], b_ = q_off[q_ + 1];                              \
+            a_ = a_ < 0 ? 0 : (a_ > n_tok ? n_tok : a_);                             \
+            b_ = b_ < a_ ? a_ : (b_ > n_tok ? n_tok : b_);                           \
+            const int64_t m_ = a_ + 2 * tid;                                         \
+            pf_lo0 = pf_hi0 = pf_lo1 = pf_hi1 = 0;                                   \
+            if (m_ < b_) {                                                           \
+                pf_lo0 = seg[m_ * per + t_];                                         \
+                pf_hi0 = seg[m_ * per + t_ + 1];                                     \
+            }                                                                        \
+            if (m_ + 1 < b_) {                                                       \
+                pf_lo1 = seg[(m_ + 1) * per + t_];                                   \
+                pf_hi1 = seg[(m_ + 1) * per + t_ + 1];                               \
+            }                                                                        \
+            if (tid == 0)                                                            \
+                pf_tau = *(volatile uint32_t*)&thresh[q_];                           \
+        }                                                                            \
+    } while (0)
+    BM25_PREFETCH(blockIdx.x);
+
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int64_t q = item / n_tiles;
-        const int32_t tile = (int32_t)(item - q * n_tiles);
+        int64_t q;
+        int32_t tile;
+        item_qt(item, q, tile);
         const int64_t d0 = (int64_t)tile * W;
         const int32_t wd = (int32_t)min((int64_t)W, n_docs - d0);
         const int32_t nwords = (wd + 31) >> 5;
         int64_t m0 = q_off[q], m1 = q_off[q + 1];
         m0 = m0 < 0 ? 0 : (m0 > n_tok ? n_tok : m0);
         m1 = m1 < m0 ? m0 : (m1 > n_tok ? n_tok : m1);
+        const uint32_t my_tau = pf_tau;  // thread 0's copy is the one used
 
         // scatter-add the item's postings, a chunk of query tokens at a time
         for (int64_t mb = m0; mb < m1; mb += kTokChunk) {
             const int cnt = (int)min((int64_t)kTokChunk, m1 - mb);
             if (tid < 32) {
-                // lane l stages tokens 2l and 2l+1 of the chunk
                 int32_t len[2];
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
-                    int i = 2 * tid + h;
-                    int32_t lo = 0, hi = 0;
-                    if (i < cnt) {
+                    const int i = 2 * tid + h;
+                    int32_t l = 0, hh = 0;
+                    if (mb == m0) {  // prefetched
+                        l = h ? pf_lo1 : pf_lo0;
+                        hh = h ? pf_hi1 : pf_hi0;
+                    } else if (i < cnt) {
                         const int32_t* sg = seg + (mb + i) * per + tile;
-                        lo = sg[0];
-                        hi = sg[1];
+                        l = sg[0];
+                        hh = sg[1];
                     }
-                    ts.lo[i] = lo;
-                    len[h] = hi - lo;
+                    if (i >= cnt)
+                        l = hh = 0;
+                    len[h] = hh - l;
+                    ts.lo[i] = l;
                 }
                 int32_t s2 = len[0] + len[1];
                 int32_t inc = warp_inclusive_sum(s2);
@@ -244,33 +350,86 @@ __global__ void __launch_bounds__(kTileThreads)
                 if (tid == 31)
                     ts.pre[kTokChunk] = inc;
             }
+            if (mb == m0)
+                BM25_PREFETCH(item + gridDim.x);  // overlaps with this item's work
             __syncthreads();
             const int32_t total = ts.pre[kTokChunk];
-            for (int32_t e = tid; e < total; e += kTileThreads) {
-                // token i of the chunk: the last i with pre[i] <= e
-                int a = 0, b = cnt;  // invariant: pre[a] <= e < pre[b]
-                while (b - a > 1) {
-                    int mid = (a + b) >> 1;
-                    if (ts.pre[mid] <= e)
-                        a = mid;
-                    else
-                        b = mid;
+            constexpr int U = 4;  // postings in flight per thread
+            for (int32_t e0 = tid; e0 < total; e0 += U * kTileThreads) {
+                int32_t dd[U];
+                float vv[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int32_t e = e0 + u * kTileThreads;
+                    dd[u] = -1;
+                    if (e < total) {
+                        int a = 0, b = cnt;  // pre[a] <= e < pre[b]
+                        while (b - a > 1) {
+                            int mid = (a + b) >> 1;
+                            if (ts.pre[mid] <= e)
+                                a = mid;
+                            else
+                                b = mid;
+                        }
+                        const int32_t j = ts.lo[a] + (e - ts.pre[a]);
+                        dd[u] = __ldg(indices + j) - (int32_t)d0;
+                        vv[u] = __ldg(data + j);
+                    }
                 }
-                const int32_t j = ts.lo[a] + (e - ts.pre[a]);
-                const int32_t d = indices[j] - (int32_t)d0;
-                const float v = data[j];
-                if ((uint32_t)d < (uint32_t)wd) {  // holds for any well-formed index
-                    atomicAdd(&acc[d], v);
-                    atomicOr(&mask[d >> 5], 1u << (d & 31));
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int32_t d = dd[u];
+                    if ((uint32_t)d < (uint32_t)wd) {  // holds for any well-formed index
+                        atomicAdd(&acc[d], vv[u]);
+                        atomicOr(&mask[d >> 5], 1u << (d & 31));
+                    }
                 }
             }
             __syncthreads();
         }
+        if (m0 == m1)
+            BM25_PREFETCH(item + gridDim.x);
 
-        // add the lowest-id untouched documents of the tile (score 0) until
-        // k' documents are flagged or none is left
+        // ---- selection ------------------------------------------------------
+        // tau = the query's running threshold: some tile already holds k'
+        // documents scoring at least tau, so a document below tau cannot be
+        // in the top k' (documents AT tau can, through the doc-id tie rule).
+        if (tid == 0) {
+            st.tau = my_tau;
+            st.ctr = 0;
+            st.minkey = ~0ull;
+            ts.n_surv = 0;
+            ts.n_pos = 0;
+        }
+        __syncthreads();
+        const uint32_t tau = st.tau;
         const uint32_t kp = (uint32_t)min(kprime, wd);
         {
+            uint32_t pos = 0;
+            for (int w = tid; w < nwords; w += kTileThreads) {
+                uint32_t bits = mask[w];
+                while (bits) {
+                    const int bpos = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const int d = (w << 5) + bpos;
+                    const float a = acc[d];
+                    pos += (a > 0.0f);
+                    if (order_f32(a) >= tau) {
+                        uint32_t slot = atomicAdd(&ts.n_surv, 1u);
+                        if (slot < kSurvCap)
+                            ts.surv[slot] = (uint16_t)d;
+                    }
+                }
+            }
+            pos = warp_sum(pos);
+            if ((tid & 31) == 0 && pos)
+                atomicAdd(&ts.n_pos, pos);
+        }
+        __syncthreads();
+        // Untouched documents score exactly 0.  They can enter the tile's top
+        // k' only if 0 clears tau and fewer than k' touched documents score
+        // above 0; then the k' lowest-id untouched ones join the candidates.
+        if (tau <= 0x80000000u && ts.n_pos < kp) {
             uint32_t carry = 0;
             for (int w0 = 0; w0 < nwords && carry < kp; w0 += kTileThreads) {
                 const int w = w0 + tid;
@@ -296,39 +455,60 @@ __global__ void __launch_bounds__(kTileThreads)
                         fill = f;
                     }
                     mask[w] |= fill;
+                    while (fill) {
+                        const int bpos = __ffs(fill) - 1;
+                        fill &= fill - 1;
+                        uint32_t slot = atomicAdd(&ts.n_surv, 1u);
+                        if (slot < kSurvCap)
+                            ts.surv[slot] = (uint16_t)((w << 5) + bpos);
+                    }
                 }
                 carry += tot;
             }
+            __syncthreads();
         }
-        // candidates = flagged documents
-        uint32_t c = 0;
-        for (int w = tid; w < nwords; w += kTileThreads)
-            c += __popc(mask[w]);
-        uint32_t n_cand;
-        block_exclusive_sum(c, ts.scan, &n_cand);
+        const uint32_t n_cand = ts.n_surv;
+        const uint32_t n_emit = n_cand < kp ? n_cand : kp;
         if (tid == 0)
-            st.ctr = 0;
+            st.base = n_emit ? atomicAdd(&ccount[q], n_emit) : 0u;
         __syncthreads();
-
-        u64* out = cand + item * kprime;
-        auto for_each = [&](auto f) {
-            for (int w = tid; w < nwords; w += kTileThreads) {
-                uint32_t bits = mask[w];
-                while (bits) {
-                    int bpos = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    int d = (w << 5) + bpos;
-                    f(make_key(acc[d], (uint32_t)(d0 + d)));
+        if (n_emit > 0) {
+            u64* out = cand + q * cand_cap + st.base;
+            auto emit = [&](u64 key) {
+                uint32_t slot = atomicAdd(&st.ctr, 1u);
+                if (slot < n_emit) {
+                    out[slot] = key;
+                    atomicMin(&st.minkey, key);
                 }
+            };
+            if (n_cand <= kSurvCap) {
+                block_select_idx(st, n_cand, kp,
+                                 [&](uint32_t i) {
+                                     const int d = ts.surv[i];
+                                     return make_key(acc[d], (uint32_t)(d0 + d));
+                                 },
+                                 emit);
+            } else {  // more survivors than the buffer holds: walk the bitmask
+                auto for_each = [&](auto f) {
+                    for (int w = tid; w < nwords; w += kTileThreads) {
+                        uint32_t bits = mask[w];
+                        while (bits) {
+                            const int bpos = __ffs(bits) - 1;
+                            bits &= bits - 1;
+                            const int d = (w << 5) + bpos;
+                            const float a = acc[d];
+                            if (order_f32(a) >= tau)
+                                f(make_key(a, (uint32_t)(d0 + d)));
+                        }
+                    }
+                };
+                block_select(st, n_cand, kp, for_each, emit);
             }
-        };
-        block_select(st, n_cand, kp, for_each, [&](u64 key) {
-            uint32_t slot = atomicAdd(&st.ctr, 1u);
-            if (slot < kp)
-                out[slot] = key;
-        });
-        for (int r = kp + tid; r < kprime; r += kTileThreads)
-            out[r] = 0ull;  // empty slot
+            // a full set of k' candidates raises the query's threshold to the
+            // score of the weakest of them
+            if (tid == 0 && n_emit == kp)
+                atomicMax(&thresh[q], (uint32_t)(st.minkey >> 32));
+        }
 
         // reset the touched accumulators and the bitmask for the next item
         for (int w = tid; w < nwords; w += kTileThreads) {
@@ -344,45 +524,49 @@ __global__ void __launch_bounds__(kTileThreads)
     }
 }
 
+#undef BM25_PREFETCH
+
 // ---- R3 -----------------------------------------------------------------------
+// Per query: the k' best of the tiles' candidates, re-keyed on the final FP32
+// score (shift added) so that equal returned scores list the lower doc id
+// first, then sorted.
 __global__ void __launch_bounds__(kMergeThreads)
-    k_merge(const u64* __restrict__ cand, int32_t n_tiles, int32_t kprime, int32_t k,
-            const double* __restrict__ shift, int32_t* __restrict__ out_ids,
-            float* __restrict__ out_scores)
+    k_merge(const u64* __restrict__ cand, int64_t cand_cap, const uint32_t* __restrict__ ccount,
+            int32_t kprime, int32_t k, const double* __restrict__ shift,
+            int32_t* __restrict__ out_ids, float* __restrict__ out_scores)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SelectState st;
     u64* sel = reinterpret_cast<u64*>(smem);
     const int q = blockIdx.x;
     const int tid = threadIdx.x;
-    const int64_t n = (int64_t)n_tiles * kprime;
-    const u64* c = cand + (int64_t)q * n;
+    const int64_t n = min((int64_t)ccount[q], cand_cap);
+    const u64* c = cand + (int64_t)q * cand_cap;
 
     int sz = 1;
     while (sz < kprime)
         sz <<= 1;
     for (int i = tid; i < sz; i += kMergeThreads)
         sel[i] = 0ull;
-    uint32_t cnt = 0;
-    for (int64_t i = tid; i < n; i += kMergeThreads)
-        cnt += (c[i] != 0ull);
-    uint32_t n_cand;
-    block_exclusive_sum(cnt, st.red, &n_cand);
     if (tid == 0)
         st.ctr = 0;
     __syncthreads();
     auto for_each = [&](auto f) {
-        for (int64_t i = tid; i < n; i += kMergeThreads) {
-            u64 key = c[i];
-            if (key != 0ull)
-                f(key);
-        }
+        for (int64_t i = tid; i < n; i += kMergeThreads)
+            f(c[i]);
     };
-    block_select(st, n_cand, (uint32_t)kprime, for_each, [&](u64 key) {
+    block_select(st, (uint32_t)n, (uint32_t)kprime, for_each, [&](u64 key) {
         uint32_t slot = atomicAdd(&st.ctr, 1u);
         if (slot < (uint32_t)kprime)
             sel[slot] = key;
     });
+    const double sh = shift[q];
+    for (int i = tid; i < kprime; i += kMergeThreads) {
+        u64 key = sel[i];
+        if (key != 0ull)
+            sel[i] = make_key((float)((double)key_score(key) + sh), key_doc(key));
+    }
+    __syncthreads();
     // bitonic sort, descending
     for (int size = 2; size <= sz; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -399,13 +583,12 @@ __global__ void __launch_bounds__(kMergeThreads)
             __syncthreads();
         }
     }
-    const double sh = shift[q];
     for (int r = tid; r < k; r += kMergeThreads) {
         int64_t o = (int64_t)q * k + r;
         if (r < kprime) {
             u64 key = sel[r];
             out_ids[o] = (int32_t)key_doc(key);
-            out_scores[o] = (float)((double)key_score(key) + sh);
+            out_scores[o] = key_score(key);
         } else {
             out_ids[o] = -1;
             out_scores[o] = -__int_as_float(0x7f800000);
@@ -441,11 +624,17 @@ int workspace_reserve(const bm25_index* ix, bm25_workspace* ws, int32_t nq, int6
     (void)ix;
     size_t shift_cap = (size_t)ws->max_queries;
     if ((size_t)nq > shift_cap || !ws->shift) {
-        if (ws->shift)
-            cudaFree(ws->shift);
+        for (void* p : {(void*)ws->shift, (void*)ws->thresh, (void*)ws->ccount})
+            if (p)
+                cudaFree(p);
         ws->shift = nullptr;
-        BM25_CUDA_TRY(cudaMalloc((void**)&ws->shift, sizeof(double) * (size_t)std::max(nq, 1)));
-        ws->max_queries = std::max(nq, 1);
+        ws->thresh = nullptr;
+        ws->ccount = nullptr;
+        const size_t m = (size_t)std::max(nq, 1);
+        BM25_CUDA_TRY(cudaMalloc((void**)&ws->shift, sizeof(double) * m));
+        BM25_CUDA_TRY(cudaMalloc((void**)&ws->thresh, sizeof(uint32_t) * m));
+        BM25_CUDA_TRY(cudaMalloc((void**)&ws->ccount, sizeof(uint32_t) * m));
+        ws->max_queries = (int32_t)m;
     }
     BM25_TRY(grow(&ws->seg, &ws->seg_cap, (size_t)n_tok * (size_t)(n_tiles + 1)));
     BM25_TRY(grow(&ws->cand, &ws->cand_cap, (size_t)nq * (size_t)n_tiles * (size_t)kprime));
@@ -454,7 +643,7 @@ int workspace_reserve(const bm25_index* ix, bm25_workspace* ws, int32_t nq, int6
 
 void workspace_release(bm25_workspace* ws)
 {
-    void* ps[] = {ws->shift, ws->seg, ws->cand};
+    void* ps[] = {ws->shift, ws->thresh, ws->ccount, ws->seg, ws->cand};
     for (void* p : ps)
         if (p)
             cudaFree(p);
@@ -465,6 +654,8 @@ void workspace_release(bm25_workspace* ws)
                 cudaFree(p);
     }
     ws->shift = nullptr;
+    ws->thresh = nullptr;
+    ws->ccount = nullptr;
     ws->seg = nullptr;
     ws->cand = nullptr;
 }
@@ -493,7 +684,8 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
     {
         ProfileScope ps_("k_query_prep", s);
         k_query_prep<<<std::max(g0, 1), 256, 0, s>>>(q_tokens, n_tok, q_off, nq, ix->s0, ix->vocab,
-                                                      ws->shift, ix->status);
+                                                      ws->shift, ws->thresh, ws->ccount,
+                                                      ix->status);
     }
     count_launch();
     BM25_LAUNCH_CHECK();
@@ -521,7 +713,9 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
     {
         ProfileScope ps_("k_tile_topk", s);
         k_tile_topk<<<g2, kTileThreads, smem, s>>>(q_tokens, n_tok, q_off, nq, N, ix->indices,
-                                                   ix->data, ws->seg, W, n_tiles, kprime, ws->cand);
+                                                   ix->data, ws->seg, W, n_tiles, kprime,
+                                                   ws->thresh, ws->ccount, ws->cand,
+                                                   (int64_t)n_tiles * kprime);
     }
     count_launch();
     BM25_LAUNCH_CHECK();
@@ -533,8 +727,8 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
                                        (int)msmem));
     {
         ProfileScope ps_("k_merge", s);
-        k_merge<<<nq, kMergeThreads, msmem, s>>>(ws->cand, n_tiles, kprime, k, ws->shift, out_ids,
-                                                 out_scores);
+        k_merge<<<nq, kMergeThreads, msmem, s>>>(ws->cand, (int64_t)n_tiles * kprime, ws->ccount,
+                                                 kprime, k, ws->shift, out_ids, out_scores);
     }
     count_launch();
     BM25_LAUNCH_CHECK();

@@ -236,15 +236,20 @@ def test_host_entry_points_and_checkpoint(torch_dev):
     a, b_ = ix.export(), ih.export()
     for key in ("indptr", "indices", "tf", "df", "doc_len", "idf", "s0", "data"):
         assert np.array_equal(a[key], b_[key]), key
+    # FP32 atomic accumulation order varies between runs, so each path is
+    # held to the oracle rather than to the other bit for bit
+    orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.BM25L)
+    im = bm25.Index.load_arrays(a)  # export -> import (checkpoint resume)
     ids_d, sc_d = ix.retrieve(_to(torch_dev, q.tokens), _to(torch_dev, q.offsets), 10)
     ids_h, sc_h = ih.retrieve_host(q.tokens, q.offsets, 10)
-    assert np.array_equal(ids_d.cpu().numpy(), ids_h)
-    assert np.array_equal(sc_d.cpu().numpy(), sc_h)
-    # export -> import -> the same answers
-    im = bm25.Index.load_arrays(a)
     ids_i, sc_i = im.retrieve(_to(torch_dev, q.tokens), _to(torch_dev, q.offsets), 10)
-    assert np.array_equal(ids_d.cpu().numpy(), ids_i.cpu().numpy())
-    assert np.array_equal(sc_d.cpu().numpy(), sc_i.cpu().numpy())
+    im.sync_status()
+    results = [(ids_d.cpu().numpy(), sc_d.cpu().numpy()), (ids_h, sc_h),
+               (ids_i.cpu().numpy(), sc_i.cpu().numpy())]
+    for i in range(q.n_queries):
+        full, ab = oracle.score_all(orc, q.query(i), with_abs=True)
+        for name, (ids, sc) in zip(("device", "host", "imported"), results):
+            check_topk(ids[i], sc[i], full, ab, 10, where=f"{name} q{i}")
     for x in (ix, ih, im):
         x.close()
 
