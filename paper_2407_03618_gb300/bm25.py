@@ -248,9 +248,9 @@ class Index:
         qt = _dev_tensor(q_tokens, torch.int32)
         qo = _dev_tensor(q_offsets, torch.int64)
         nq = qo.numel() - 1
-        if out is None:
-            ids = torch.empty((nq, k), dtype=torch.int32, device=qo.device)
-            sc = torch.empty((nq, k), dtype=torch.float32, device=qo.device)
+        if out is None:  # k < 1 reaches the library, which rejects it
+            ids = torch.empty((nq, max(k, 0)), dtype=torch.int32, device=qo.device)
+            sc = torch.empty((nq, max(k, 0)), dtype=torch.float32, device=qo.device)
         else:
             ids, sc = out
         if workspace is None and accumulator == ACC_AUTO and tile_docs == 0:
@@ -277,8 +277,8 @@ class Index:
         qo = _host_array(q_offsets, np.int64)
         nq = _hlen(qo) - 1
         if out is None:
-            ids = np.zeros((nq, k), np.int32)
-            sc = np.zeros((nq, k), np.float32)
+            ids = np.zeros((nq, max(k, 0)), np.int32)
+            sc = np.zeros((nq, max(k, 0)), np.float32)
         else:
             ids, sc = out
         _check(load().bm25_retrieve_host(self.handle, _hptr(qt), _hptr(qo), nq, k, _hptr(ids),

@@ -104,11 +104,10 @@ struct bm25_workspace {
     float* out_scores = nullptr;     // staging for the _host entry point
     double* shift = nullptr;         // [max_queries]  sum_i S0(q_i)
     uint32_t* thresh = nullptr;      // [max_queries]  running k'-th best score key
-    uint32_t* ccount = nullptr;      // [max_queries]  candidates appended so far
+    uint32_t* tcount = nullptr;      // [n_queries * n_tiles]  candidates per (tile, query) item
     int32_t* seg = nullptr;          // [max_query_tokens * (max_tiles + 1)]
-    unsigned long long* cand = nullptr;  // [max_queries * max_tiles * max_k], per query a
-                                         // compact list of at most n_tiles * k' keys
-    size_t seg_cap = 0, cand_cap = 0;    // element capacities
+    unsigned long long* cand = nullptr;  // [n_queries * n_tiles * k'], k' slots per item
+    size_t seg_cap = 0, cand_cap = 0, tcount_cap = 0;  // element capacities
     size_t staging_cap[4] = {0, 0, 0, 0};  // byte capacities of the staging buffers
     bool owns_staging = false;
 };

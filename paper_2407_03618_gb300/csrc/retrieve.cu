@@ -3,17 +3,20 @@
 // shift added back to every returned score).
 //
 // Doc-tiled shared-memory path, four launches per call:
-//   R0 k_query_prep   sum_i S0(q_i) per query in FP64; token / offset checks
+//   R0 k_query_prep   sum_i S0(q_i) per query in FP64; token / offset checks;
+//                     resets the per-query running threshold
 //   R1 k_seg_bounds   for every query token and every doc-tile boundary, the
 //                     first posting of the token's column at or past the
 //                     boundary (binary search: doc ids ascend in a column)
-//   R2 k_tile_topk    persistent CTAs over (query, doc tile) items: each item
+//   R2 k_tile_topk    persistent CTAs over (doc tile, query) items: each item
 //                     scatter-adds its postings into FP32 accumulators in
 //                     shared memory, marks touched documents in a bitmask,
-//                     and radix-selects the tile's best k' candidates,
-//                     including the lowest-id untouched documents (score 0)
-//   R3 k_merge        per query: radix-select k' of the tiles' candidates,
-//                     sort them and write (id, score + shift)
+//                     keeps the documents that clear the query's running
+//                     threshold, and radix-selects the tile's best k' of them
+//                     (including the lowest-id untouched documents, score 0,
+//                     when they can matter)
+//   R3 k_merge        per query: the k' best of the tiles' candidates,
+//                     re-keyed on the final score, sorted, written out
 #include <algorithm>
 #include <cstdio>
 
@@ -26,15 +29,18 @@ namespace {
 typedef unsigned long long u64;
 
 constexpr int kTileThreads = 512;
-constexpr int kTokChunk = 64;     // query tokens staged in shared memory at a time
-constexpr int kMergeThreads = 512;
+constexpr int kTokChunk = 64;          // query tokens staged in shared memory at a time
+constexpr uint32_t kSurvCap = 1024;    // candidates kept in shared memory per item
+constexpr int kMergeThreads = 256;
+constexpr int kMergeBufCap = 4096;     // candidates a merge gathers into shared memory
+constexpr uint32_t kZeroKey = 0x80000000u;  // order_f32(0.0f)
 
 // ---- R0 ---------------------------------------------------------------------
 __global__ void k_query_prep(const int32_t* __restrict__ q_tokens, int64_t n_tok,
                              const int64_t* __restrict__ q_off, int32_t nq,
                              const double* __restrict__ s0, int32_t vocab,
                              double* __restrict__ shift, uint32_t* __restrict__ thresh,
-                             uint32_t* __restrict__ ccount, int* status)
+                             int* status)
 {
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
          q += (int64_t)gridDim.x * blockDim.x) {
@@ -55,7 +61,6 @@ __global__ void k_query_prep(const int32_t* __restrict__ q_tokens, int64_t n_tok
         }
         shift[q] = sum;
         thresh[q] = 0u;  // below every real score key
-        ccount[q] = 0u;
     }
 }
 
@@ -107,7 +112,7 @@ __global__ void k_seg_bounds(const int32_t* __restrict__ q_tokens, int64_t n_tok
 struct SelectState {
     uint32_t hist[256];
     u64 prefix, pmask, minkey;
-    uint32_t need, bucket, ctr, cnt, tau, base;
+    uint32_t need, bucket, ctr, tau;
     uint32_t red[33];
 };
 
@@ -140,9 +145,10 @@ __device__ __forceinline__ void select_bucket(SelectState& st, int shift)
     }
 }
 
-// for_each(f) must call f(key) for every candidate owned by this thread.
-// emit(key) is called for each of the min(k, n) selected keys (any order).
-// n = number of candidates.  All threads of the block must call this.
+// Selection over candidates given by for_each(f), which must call f(key) for
+// every candidate owned by this thread (any loop shape).  emit(key) runs for
+// each of the min(k, n) selected keys.  All threads of the block call this;
+// it ends with __syncthreads().
 template <class ForEach, class Emit>
 __device__ void block_select(SelectState& st, uint32_t n, uint32_t k, ForEach for_each,
                              Emit emit)
@@ -182,12 +188,16 @@ __device__ void block_select(SelectState& st, uint32_t n, uint32_t k, ForEach fo
     __syncthreads();
 }
 
-// Same selection over an indexable candidate set: get(i) returns the key of
-// candidate i < n.  The loops are warp-uniform, so histogram updates are
-// aggregated per warp with __match_any_sync (candidates that share a score
-// prefix would otherwise serialise on one counter).
-template <class Get, class Emit>
-__device__ void block_select_idx(SelectState& st, uint32_t n, uint32_t k, Get get, Emit emit)
+// Selection over an indexable candidate set: get(i) is the key of candidate
+// i < n, and every key starts with the `skip` bytes of `common` (the bytes
+// all candidates share, so their passes are skipped).  The loops are
+// warp-uniform, so histogram updates are aggregated per warp with
+// __match_any_sync (keys sharing a prefix would otherwise serialise on one
+// counter).  With TRAIL_SYNC false the block is not synchronised after the
+// emit loop.
+template <bool TRAIL_SYNC, class Get, class Emit>
+__device__ void block_select_idx(SelectState& st, uint32_t n, uint32_t k, int skip, u64 common,
+                                 Get get, Emit emit)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t stride = blockDim.x;
@@ -195,15 +205,17 @@ __device__ void block_select_idx(SelectState& st, uint32_t n, uint32_t k, Get ge
     if (n <= k) {
         for (uint32_t i = threadIdx.x; i < n; i += stride)
             emit(get(i));
-        __syncthreads();
+        if (TRAIL_SYNC)
+            __syncthreads();
         return;
     }
     if (threadIdx.x == 0) {
-        st.prefix = 0;
-        st.pmask = 0;
+        const u64 pm = skip >= 8 ? ~0ull : (skip <= 0 ? 0ull : ~0ull << (64 - 8 * skip));
+        st.prefix = common & pm;
+        st.pmask = pm;
         st.need = k;
     }
-    for (int pass = 0; pass < 8; pass++) {
+    for (int pass = skip; pass < 8; pass++) {
         const int shift = 56 - 8 * pass;
         for (int i = threadIdx.x; i < 256; i += blockDim.x)
             st.hist[i] = 0;
@@ -234,19 +246,27 @@ __device__ void block_select_idx(SelectState& st, uint32_t n, uint32_t k, Get ge
         if ((key & pm) >= pf)
             emit(key);
     }
-    __syncthreads();
+    if (TRAIL_SYNC)
+        __syncthreads();
+}
+
+// Number of leading bytes shared by every key whose high word lies in
+// [kmin, kmax] (the low word, a doc id, is assumed to vary).
+__device__ __forceinline__ int common_bytes(uint32_t kmin, uint32_t kmax)
+{
+    uint32_t x = kmin ^ kmax;
+    return x ? (__clz(x) >> 3) : 4;
 }
 
 // ---- R2 -----------------------------------------------------------------------
-// Dynamic shared memory: acc[W] FP32 | mask[W/32] | SelectState | token stage.
-constexpr uint32_t kSurvCap = 2048;  // survivors kept in shared memory per item
-
+// Dynamic shared memory: acc[W] FP32 | mask[W/32] | SelectState | TileStage.
 struct TileStage {
     int32_t lo[kTokChunk];
     int32_t pre[kTokChunk + 1];
     uint32_t scan[33];
-    uint32_t n_surv, n_pos;
-    uint16_t surv[kSurvCap];  // local doc ids of the item's candidates
+    uint32_t n_surv, n_pos, kmin, kmax;
+    uint32_t surv_key[kSurvCap];  // order_f32 of the candidate's score
+    uint16_t surv_doc[kSurvCap];  // its doc id within the tile
 };
 
 __global__ void __launch_bounds__(kTileThreads, 3)
@@ -254,8 +274,8 @@ __global__ void __launch_bounds__(kTileThreads, 3)
                 const int64_t* __restrict__ q_off, int32_t nq, int64_t n_docs,
                 const int32_t* __restrict__ indices, const float* __restrict__ data,
                 const int32_t* __restrict__ seg, int32_t W, int32_t n_tiles, int32_t kprime,
-                uint32_t* __restrict__ thresh, uint32_t* __restrict__ ccount,
-                u64* __restrict__ cand, int64_t cand_cap)
+                uint32_t* __restrict__ thresh, uint32_t* __restrict__ tcount,
+                u64* __restrict__ cand)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     float* acc = reinterpret_cast<float*>(smem);
@@ -264,32 +284,27 @@ __global__ void __launch_bounds__(kTileThreads, 3)
     TileStage& ts = *reinterpret_cast<TileStage*>(&st + 1);
 
     const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < W; i += kTileThreads)
         acc[i] = 0.0f;
     for (int i = tid; i < W / 32; i += kTileThreads)
         mask[i] = 0u;
-    __syncthreads();
 
     const int64_t n_items = (int64_t)nq * n_tiles;
     const int64_t per = (int64_t)n_tiles + 1;
-    // tile-major order: tile 0 of every query first, so that the running
-    // per-query threshold is usually known when a query's later tiles run,
-    // and the segments in flight at once all belong to one doc tile
-    auto item_qt = [&](int64_t item, int64_t& q, int32_t& tile) {
-        tile = (int32_t)(item / nq);
-        q = item - (int64_t)tile * nq;
-    };
-    // warp 0 prefetches the first token chunk's segment bounds of its next
-    // item (lane l: tokens 2l, 2l+1) and thread 0 the query's threshold
+    // Tile-major order: tile 0 of every query first, so the running
+    // threshold of a query is usually known when its later tiles run, and
+    // the segments in flight at once all belong to one doc tile.
+    // Warp 0 prefetches the first token chunk's segment bounds of the CTA's
+    // next item (lane l: tokens 2l and 2l+1), thread 0 that query's threshold.
     int32_t pf_lo0 = 0, pf_lo1 = 0, pf_hi0 = 0, pf_hi1 = 0;
     uint32_t pf_tau = 0;
 #define BM25_PREFETCH(ITEM)                                                          \
     do {                                                                             \
         const int64_t it_ = (ITEM);                                                  \
         if (tid < 32 && it_ < n_items) {                                             \
-            int64_t q_;                                                              \
-            int32_t t_;                                                              \
-            item_qt(it_, q_, t_);                                                    \
+            const int32_t t_ = (int32_t)(it_ / nq);                                  \
+            const int64_t q_ = it_ - (int64_t)t_ * nq;                               \
             int64_t a_ = q_off[q_], b_ = q_off[q_ + 1];                              \
             a_ = a_ < 0 ? 0 : (a_ > n_tok ? n_tok : a_);                             \
             b_ = b_ < a_ ? a_ : (b_ > n_tok ? n_tok : b_);                           \
@@ -308,20 +323,28 @@ __global__ void __launch_bounds__(kTileThreads, 3)
         }                                                                            \
     } while (0)
     BM25_PREFETCH(blockIdx.x);
+    __syncthreads();
 
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-        int64_t q;
-        int32_t tile;
-        item_qt(item, q, tile);
+        const int32_t tile = (int32_t)(item / nq);
+        const int64_t q = item - (int64_t)tile * nq;
         const int64_t d0 = (int64_t)tile * W;
         const int32_t wd = (int32_t)min((int64_t)W, n_docs - d0);
         const int32_t nwords = (wd + 31) >> 5;
         int64_t m0 = q_off[q], m1 = q_off[q + 1];
         m0 = m0 < 0 ? 0 : (m0 > n_tok ? n_tok : m0);
         m1 = m1 < m0 ? m0 : (m1 > n_tok ? n_tok : m1);
-        const uint32_t my_tau = pf_tau;  // thread 0's copy is the one used
+        if (tid == 0) {
+            st.tau = pf_tau;
+            st.ctr = 0;
+            st.minkey = ~0ull;
+            ts.n_surv = 0;
+            ts.n_pos = 0;
+            ts.kmin = 0xffffffffu;
+            ts.kmax = 0u;
+        }
 
-        // scatter-add the item's postings, a chunk of query tokens at a time
+        // ---- scatter-add the item's postings, a chunk of tokens at a time ----
         for (int64_t mb = m0; mb < m1; mb += kTokChunk) {
             const int cnt = (int)min((int64_t)kTokChunk, m1 - mb);
             if (tid < 32) {
@@ -330,7 +353,7 @@ __global__ void __launch_bounds__(kTileThreads, 3)
                 for (int h = 0; h < 2; h++) {
                     const int i = 2 * tid + h;
                     int32_t l = 0, hh = 0;
-                    if (mb == m0) {  // prefetched
+                    if (mb == m0) {  // prefetched during the previous item
                         l = h ? pf_lo1 : pf_lo0;
                         hh = h ? pf_hi1 : pf_hi0;
                     } else if (i < cnt) {
@@ -354,26 +377,34 @@ __global__ void __launch_bounds__(kTileThreads, 3)
                 BM25_PREFETCH(item + gridDim.x);  // overlaps with this item's work
             __syncthreads();
             const int32_t total = ts.pre[kTokChunk];
-            constexpr int U = 4;  // postings in flight per thread
-            for (int32_t e0 = tid; e0 < total; e0 += U * kTileThreads) {
+            // Warp w takes runs of 32 consecutive postings; the run's token is
+            // found once per warp, each lane then steps forward over empty or
+            // finished segments.
+            constexpr int U = 4;  // runs in flight per warp
+            for (int32_t r0 = warp * 32; r0 < total; r0 += U * kTileThreads) {
                 int32_t dd[U];
                 float vv[U];
 #pragma unroll
                 for (int u = 0; u < U; u++) {
-                    const int32_t e = e0 + u * kTileThreads;
+                    const int32_t eb = r0 + u * kTileThreads;
                     dd[u] = -1;
-                    if (e < total) {
-                        int a = 0, b = cnt;  // pre[a] <= e < pre[b]
+                    if (eb < total) {
+                        int a = 0, b = cnt;  // pre[a] <= eb < pre[b]
                         while (b - a > 1) {
                             int mid = (a + b) >> 1;
-                            if (ts.pre[mid] <= e)
+                            if (ts.pre[mid] <= eb)
                                 a = mid;
                             else
                                 b = mid;
                         }
-                        const int32_t j = ts.lo[a] + (e - ts.pre[a]);
-                        dd[u] = __ldg(indices + j) - (int32_t)d0;
-                        vv[u] = __ldg(data + j);
+                        const int32_t e = eb + lane;
+                        if (e < total) {
+                            while (ts.pre[a + 1] <= e)
+                                a++;
+                            const int32_t j = ts.lo[a] + (e - ts.pre[a]);
+                            dd[u] = __ldg(indices + j) - (int32_t)d0;
+                            vv[u] = __ldg(data + j);
+                        }
                     }
                 }
 #pragma unroll
@@ -387,49 +418,68 @@ __global__ void __launch_bounds__(kTileThreads, 3)
             }
             __syncthreads();
         }
-        if (m0 == m1)
+        if (m0 == m1) {
             BM25_PREFETCH(item + gridDim.x);
+            __syncthreads();
+        }
 
-        // ---- selection ------------------------------------------------------
+        // ---- candidates ------------------------------------------------------
         // tau = the query's running threshold: some tile already holds k'
         // documents scoring at least tau, so a document below tau cannot be
         // in the top k' (documents AT tau can, through the doc-id tie rule).
-        if (tid == 0) {
-            st.tau = my_tau;
-            st.ctr = 0;
-            st.minkey = ~0ull;
-            ts.n_surv = 0;
-            ts.n_pos = 0;
-        }
-        __syncthreads();
         const uint32_t tau = st.tau;
         const uint32_t kp = (uint32_t)min(kprime, wd);
         {
-            uint32_t pos = 0;
-            for (int w = tid; w < nwords; w += kTileThreads) {
-                uint32_t bits = mask[w];
-                while (bits) {
-                    const int bpos = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const int d = (w << 5) + bpos;
-                    const float a = acc[d];
-                    pos += (a > 0.0f);
-                    if (order_f32(a) >= tau) {
-                        uint32_t slot = atomicAdd(&ts.n_surv, 1u);
-                        if (slot < kSurvCap)
-                            ts.surv[slot] = (uint16_t)d;
+            uint32_t pos = 0, kmin = 0xffffffffu, kmax = 0u;
+            for (int w0 = warp * 32; w0 < nwords; w0 += kTileThreads) {
+                const int w = w0 + lane;
+                uint32_t bits = (w < nwords) ? mask[w] : 0u;
+                const int rounds = __reduce_max_sync(0xffffffffu, __popc(bits));
+                for (int r = 0; r < rounds; r++) {  // warp-uniform
+                    bool keep = false;
+                    int d = 0;
+                    uint32_t o = 0;
+                    if (bits) {
+                        d = (w << 5) + __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        const float a = acc[d];
+                        o = order_f32(a);
+                        pos += (a > 0.0f);
+                        keep = o >= tau;
+                    }
+                    const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+                    if (bal) {
+                        uint32_t base = 0;
+                        if (lane == __ffs(bal) - 1)
+                            base = atomicAdd(&ts.n_surv, (uint32_t)__popc(bal));
+                        base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
+                        if (keep) {
+                            const uint32_t slot = base + __popc(bal & lanemask_lt());
+                            if (slot < kSurvCap) {
+                                ts.surv_key[slot] = o;
+                                ts.surv_doc[slot] = (uint16_t)d;
+                            }
+                            kmin = min(kmin, o);
+                            kmax = max(kmax, o);
+                        }
                     }
                 }
             }
             pos = warp_sum(pos);
-            if ((tid & 31) == 0 && pos)
-                atomicAdd(&ts.n_pos, pos);
+            kmin = __reduce_min_sync(0xffffffffu, kmin);
+            kmax = __reduce_max_sync(0xffffffffu, kmax);
+            if (lane == 0) {
+                if (pos)
+                    atomicAdd(&ts.n_pos, pos);
+                atomicMin(&ts.kmin, kmin);
+                atomicMax(&ts.kmax, kmax);
+            }
         }
         __syncthreads();
         // Untouched documents score exactly 0.  They can enter the tile's top
         // k' only if 0 clears tau and fewer than k' touched documents score
         // above 0; then the k' lowest-id untouched ones join the candidates.
-        if (tau <= 0x80000000u && ts.n_pos < kp) {
+        if (tau <= kZeroKey && ts.n_pos < kp) {
             uint32_t carry = 0;
             for (int w0 = 0; w0 < nwords && carry < kp; w0 += kTileThreads) {
                 const int w = w0 + tid;
@@ -455,62 +505,64 @@ __global__ void __launch_bounds__(kTileThreads, 3)
                         fill = f;
                     }
                     mask[w] |= fill;
+                    if (fill) {
+                        atomicMin(&ts.kmin, kZeroKey);
+                        atomicMax(&ts.kmax, kZeroKey);
+                    }
                     while (fill) {
                         const int bpos = __ffs(fill) - 1;
                         fill &= fill - 1;
-                        uint32_t slot = atomicAdd(&ts.n_surv, 1u);
-                        if (slot < kSurvCap)
-                            ts.surv[slot] = (uint16_t)((w << 5) + bpos);
+                        const uint32_t slot = atomicAdd(&ts.n_surv, 1u);
+                        if (slot < kSurvCap) {
+                            ts.surv_key[slot] = kZeroKey;
+                            ts.surv_doc[slot] = (uint16_t)((w << 5) + bpos);
+                        }
                     }
                 }
                 carry += tot;
             }
             __syncthreads();
         }
+
+        // ---- select and emit -------------------------------------------------
         const uint32_t n_cand = ts.n_surv;
         const uint32_t n_emit = n_cand < kp ? n_cand : kp;
-        if (tid == 0)
-            st.base = n_emit ? atomicAdd(&ccount[q], n_emit) : 0u;
-        __syncthreads();
-        if (n_emit > 0) {
-            u64* out = cand + q * cand_cap + st.base;
-            auto emit = [&](u64 key) {
-                uint32_t slot = atomicAdd(&st.ctr, 1u);
-                if (slot < n_emit) {
-                    out[slot] = key;
-                    atomicMin(&st.minkey, key);
+        u64* out = cand + item * (int64_t)kprime;
+        auto emit = [&](u64 key) {
+            const uint32_t slot = atomicAdd(&st.ctr, 1u);
+            if (slot < n_emit) {
+                out[slot] = key;
+                atomicMin(&st.minkey, key);
+            }
+        };
+        const bool in_smem = n_cand <= kSurvCap;
+        if (n_emit > 0 && in_smem) {
+            const uint32_t kmin = ts.kmin, kmax = ts.kmax;
+            const int skip = common_bytes(kmin, kmax);
+            block_select_idx<false>(st, n_cand, kp, skip, (u64)kmax << 32,
+                                    [&](uint32_t i) {
+                                        return ((u64)ts.surv_key[i] << 32) |
+                                               (u64)(~(uint32_t)(d0 + ts.surv_doc[i]));
+                                    },
+                                    emit);
+        } else if (n_emit > 0) {  // too many to buffer: walk the bitmask instead
+            auto for_each = [&](auto f) {
+                for (int w = tid; w < nwords; w += kTileThreads) {
+                    uint32_t bits = mask[w];
+                    while (bits) {
+                        const int bpos = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        const int d = (w << 5) + bpos;
+                        const float a = acc[d];
+                        if (order_f32(a) >= tau)
+                            f(make_key(a, (uint32_t)(d0 + d)));
+                    }
                 }
             };
-            if (n_cand <= kSurvCap) {
-                block_select_idx(st, n_cand, kp,
-                                 [&](uint32_t i) {
-                                     const int d = ts.surv[i];
-                                     return make_key(acc[d], (uint32_t)(d0 + d));
-                                 },
-                                 emit);
-            } else {  // more survivors than the buffer holds: walk the bitmask
-                auto for_each = [&](auto f) {
-                    for (int w = tid; w < nwords; w += kTileThreads) {
-                        uint32_t bits = mask[w];
-                        while (bits) {
-                            const int bpos = __ffs(bits) - 1;
-                            bits &= bits - 1;
-                            const int d = (w << 5) + bpos;
-                            const float a = acc[d];
-                            if (order_f32(a) >= tau)
-                                f(make_key(a, (uint32_t)(d0 + d)));
-                        }
-                    }
-                };
-                block_select(st, n_cand, kp, for_each, emit);
-            }
-            // a full set of k' candidates raises the query's threshold to the
-            // score of the weakest of them
-            if (tid == 0 && n_emit == kp)
-                atomicMax(&thresh[q], (uint32_t)(st.minkey >> 32));
+            block_select(st, n_cand, kp, for_each, emit);
         }
 
-        // reset the touched accumulators and the bitmask for the next item
+        // ---- reset the touched accumulators and the bitmask -------------------
         for (int w = tid; w < nwords; w += kTileThreads) {
             uint32_t bits = mask[w];
             while (bits) {
@@ -521,41 +573,82 @@ __global__ void __launch_bounds__(kTileThreads, 3)
             mask[w] = 0u;
         }
         __syncthreads();
+        if (tid == 0) {
+            tcount[item] = n_emit;
+            // a full set of k' candidates raises the query's threshold to the
+            // score of the weakest of them
+            if (n_emit == kp && kp > 0)
+                atomicMax(&thresh[q], (uint32_t)(st.minkey >> 32));
+        }
     }
+#undef BM25_PREFETCH
 }
 
-#undef BM25_PREFETCH
-
 // ---- R3 -----------------------------------------------------------------------
-// Per query: the k' best of the tiles' candidates, re-keyed on the final FP32
-// score (shift added) so that equal returned scores list the lower doc id
-// first, then sorted.
+// Per query: gather the tiles' candidates (tcount[tile * nq + q] of them in
+// item tile * nq + q's slots), select the k' best, re-key them on the final
+// FP32 score (shift added) so that equal returned scores list the lower doc
+// id first, sort, and write (id, score).  Dynamic shared memory:
+// sel[pow2 >= k'] | buf[buf_cap] keys | pre[n_tiles + 1].
 __global__ void __launch_bounds__(kMergeThreads)
-    k_merge(const u64* __restrict__ cand, int64_t cand_cap, const uint32_t* __restrict__ ccount,
-            int32_t kprime, int32_t k, const double* __restrict__ shift,
-            int32_t* __restrict__ out_ids, float* __restrict__ out_scores)
+    k_merge(const u64* __restrict__ cand, const uint32_t* __restrict__ tcount, int32_t nq,
+            int32_t n_tiles, int32_t kprime, int32_t k, const double* __restrict__ shift,
+            int32_t* __restrict__ out_ids, float* __restrict__ out_scores, int32_t buf_cap)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SelectState st;
-    u64* sel = reinterpret_cast<u64*>(smem);
-    const int q = blockIdx.x;
-    const int tid = threadIdx.x;
-    const int64_t n = min((int64_t)ccount[q], cand_cap);
-    const u64* c = cand + (int64_t)q * cand_cap;
-
     int sz = 1;
     while (sz < kprime)
         sz <<= 1;
+    u64* sel = reinterpret_cast<u64*>(smem);
+    u64* buf = sel + sz;
+    uint32_t* pre = reinterpret_cast<uint32_t*>(buf + buf_cap);
+    const int q = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // exclusive scan of the per-tile counts
+    uint32_t carry = 0;
+    for (int t0 = 0; t0 < n_tiles; t0 += kMergeThreads) {
+        const int t = t0 + tid;
+        const uint32_t c = t < n_tiles ? tcount[(int64_t)t * nq + q] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_sum(c, st.red, &tot);
+        if (t < n_tiles)
+            pre[t] = carry + ex;
+        carry += tot;
+    }
+    if (tid == 0)
+        pre[n_tiles] = carry;
     for (int i = tid; i < sz; i += kMergeThreads)
         sel[i] = 0ull;
     if (tid == 0)
         st.ctr = 0;
     __syncthreads();
-    auto for_each = [&](auto f) {
-        for (int64_t i = tid; i < n; i += kMergeThreads)
-            f(c[i]);
+    const uint32_t total = pre[n_tiles];
+    const bool gathered = total <= (uint32_t)buf_cap;
+    if (gathered) {  // one warp per tile copies its candidates
+        for (int t = warp; t < n_tiles; t += kMergeThreads / 32) {
+            const uint32_t c = pre[t + 1] - pre[t];
+            const u64* src = cand + ((int64_t)t * nq + q) * kprime;
+            for (uint32_t s = lane; s < c; s += 32)
+                buf[pre[t] + s] = src[s];
+        }
+        __syncthreads();
+    }
+    auto get = [&](uint32_t i) -> u64 {
+        if (gathered)
+            return buf[i];
+        int a = 0, b = n_tiles;  // pre[a] <= i < pre[b]
+        while (b - a > 1) {
+            int mid = (a + b) >> 1;
+            if (pre[mid] <= i)
+                a = mid;
+            else
+                b = mid;
+        }
+        return cand[((int64_t)a * nq + q) * kprime + (i - pre[a])];
     };
-    block_select(st, (uint32_t)n, (uint32_t)kprime, for_each, [&](u64 key) {
+    block_select_idx<true>(st, total, (uint32_t)kprime, 0, 0ull, get, [&](u64 key) {
         uint32_t slot = atomicAdd(&st.ctr, 1u);
         if (slot < (uint32_t)kprime)
             sel[slot] = key;
@@ -585,8 +678,8 @@ __global__ void __launch_bounds__(kMergeThreads)
     }
     for (int r = tid; r < k; r += kMergeThreads) {
         int64_t o = (int64_t)q * k + r;
-        if (r < kprime) {
-            u64 key = sel[r];
+        const u64 key = r < kprime ? sel[r] : 0ull;
+        if (key != 0ull) {
             out_ids[o] = (int32_t)key_doc(key);
             out_scores[o] = key_score(key);
         } else {
@@ -622,28 +715,26 @@ int workspace_reserve(const bm25_index* ix, bm25_workspace* ws, int32_t nq, int6
                       int32_t kprime, int64_t n_tiles)
 {
     (void)ix;
-    size_t shift_cap = (size_t)ws->max_queries;
-    if ((size_t)nq > shift_cap || !ws->shift) {
-        for (void* p : {(void*)ws->shift, (void*)ws->thresh, (void*)ws->ccount})
+    if (nq > ws->max_queries || !ws->shift) {
+        for (void* p : {(void*)ws->shift, (void*)ws->thresh})
             if (p)
                 cudaFree(p);
         ws->shift = nullptr;
         ws->thresh = nullptr;
-        ws->ccount = nullptr;
         const size_t m = (size_t)std::max(nq, 1);
         BM25_CUDA_TRY(cudaMalloc((void**)&ws->shift, sizeof(double) * m));
         BM25_CUDA_TRY(cudaMalloc((void**)&ws->thresh, sizeof(uint32_t) * m));
-        BM25_CUDA_TRY(cudaMalloc((void**)&ws->ccount, sizeof(uint32_t) * m));
         ws->max_queries = (int32_t)m;
     }
     BM25_TRY(grow(&ws->seg, &ws->seg_cap, (size_t)n_tok * (size_t)(n_tiles + 1)));
+    BM25_TRY(grow(&ws->tcount, &ws->tcount_cap, (size_t)nq * (size_t)n_tiles));
     BM25_TRY(grow(&ws->cand, &ws->cand_cap, (size_t)nq * (size_t)n_tiles * (size_t)kprime));
     return BM25_OK;
 }
 
 void workspace_release(bm25_workspace* ws)
 {
-    void* ps[] = {ws->shift, ws->thresh, ws->ccount, ws->seg, ws->cand};
+    void* ps[] = {ws->shift, ws->thresh, ws->tcount, ws->seg, ws->cand};
     for (void* p : ps)
         if (p)
             cudaFree(p);
@@ -655,7 +746,7 @@ void workspace_release(bm25_workspace* ws)
     }
     ws->shift = nullptr;
     ws->thresh = nullptr;
-    ws->ccount = nullptr;
+    ws->tcount = nullptr;
     ws->seg = nullptr;
     ws->cand = nullptr;
 }
@@ -676,7 +767,11 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
     int64_t w_need = (N + 127) / 128 * 128;
     if (W > w_need)
         W = (int32_t)w_need;
-    const int32_t n_tiles = (int32_t)((N + W - 1) / W);
+    const int64_t n_tiles64 = (N + W - 1) / W;
+    if (n_tiles64 > 65536)
+        return set_error(BM25_E_INVALID, "%lld doc tiles of %d documents: use wider tiles",
+                         (long long)n_tiles64, W);
+    const int32_t n_tiles = (int32_t)n_tiles64;
     BM25_TRY(workspace_reserve(ix, ws, nq, n_tok, kprime, n_tiles));
 
     const int max_blocks = di.sm_count * 16;
@@ -684,8 +779,7 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
     {
         ProfileScope ps_("k_query_prep", s);
         k_query_prep<<<std::max(g0, 1), 256, 0, s>>>(q_tokens, n_tok, q_off, nq, ix->s0, ix->vocab,
-                                                      ws->shift, ws->thresh, ws->ccount,
-                                                      ix->status);
+                                                      ws->shift, ws->thresh, ix->status);
     }
     count_launch();
     BM25_LAUNCH_CHECK();
@@ -714,21 +808,23 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
         ProfileScope ps_("k_tile_topk", s);
         k_tile_topk<<<g2, kTileThreads, smem, s>>>(q_tokens, n_tok, q_off, nq, N, ix->indices,
                                                    ix->data, ws->seg, W, n_tiles, kprime,
-                                                   ws->thresh, ws->ccount, ws->cand,
-                                                   (int64_t)n_tiles * kprime);
+                                                   ws->thresh, ws->tcount, ws->cand);
     }
     count_launch();
     BM25_LAUNCH_CHECK();
     int sz = 1;
     while (sz < kprime)
         sz <<= 1;
-    const size_t msmem = (size_t)sz * sizeof(u64);
+    const int32_t buf_cap =
+        (int32_t)std::min<int64_t>(kMergeBufCap, (int64_t)n_tiles * kprime);
+    const size_t msmem = (size_t)sz * sizeof(u64) + (size_t)buf_cap * sizeof(u64) +
+                         (size_t)(n_tiles + 1) * sizeof(uint32_t);
     BM25_CUDA_TRY(cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)msmem));
     {
         ProfileScope ps_("k_merge", s);
-        k_merge<<<nq, kMergeThreads, msmem, s>>>(ws->cand, (int64_t)n_tiles * kprime, ws->ccount,
-                                                 kprime, k, ws->shift, out_ids, out_scores);
+        k_merge<<<nq, kMergeThreads, msmem, s>>>(ws->cand, ws->tcount, nq, n_tiles, kprime, k,
+                                                 ws->shift, out_ids, out_scores, buf_cap);
     }
     count_launch();
     BM25_LAUNCH_CHECK();
