@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 
@@ -257,7 +258,14 @@ int bm25_index_import(int64_t n_docs, int64_t n_tokens, int64_t nnz, int32_t voc
     };
     if (rc == BM25_OK) rc = cp(ix->indptr, indptr, sizeof(int64_t) * (vocab + 1));
     if (rc == BM25_OK) rc = cp(ix->indices, indices, sizeof(int32_t) * nnz);
-    if (rc == BM25_OK) rc = cp(ix->data, data, sizeof(float) * nnz);
+    if (rc == BM25_OK && nnz > 0) {
+        // stored scores never hold -0.0 (retrieval marks untouched documents with it)
+        std::vector<float> d(data, data + nnz);
+        for (float& x : d)
+            if (x == 0.0f)
+                x = 0.0f;
+        rc = cp(ix->data, d.data(), sizeof(float) * nnz);
+    }
     if (rc == BM25_OK) {
         if (tf)
             rc = cp(ix->tf, tf, sizeof(int32_t) * nnz);

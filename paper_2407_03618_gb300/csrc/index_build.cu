@@ -342,7 +342,7 @@ __global__ void k_score(const int32_t* __restrict__ run_pos, const int32_t* __re
             s = c * f / (f + a);
         }
         tf_out[j] = tf;
-        data[j] = s;
+        data[j] = (s == 0.0f) ? 0.0f : s;  // never -0.0: retrieval uses -0.0 as "untouched"
     }
 }
 

@@ -259,14 +259,27 @@ __device__ __forceinline__ int common_bytes(uint32_t kmin, uint32_t kmax)
 }
 
 // ---- R2 -----------------------------------------------------------------------
-// Dynamic shared memory: acc[W] FP32 | mask[W/32] | SelectState | TileStage.
+// Dynamic shared memory: acc[W] FP32 | SelectState | TileStage.
+//
+// An accumulator holds -0.0 until its document is first touched: stored
+// scores are never -0.0, and -0.0 + x == x for every other x, so an
+// atomicAdd that returns -0.0 marks the first touch of its document, and a
+// sum never returns to -0.0.  First touches append the document to a list,
+// and the later passes (candidates, reset) walk that list; a tile touched
+// more densely than the list holds is walked in full instead.
+constexpr uint32_t kUntouched = 0x80000000u;  // bits of -0.0f
+constexpr uint32_t kTouchCap = 1536;  // sized so that three 16K-document tiles fit on an SM
+constexpr uint32_t kRunCap = 128;             // runs of 32 postings with a cached token
+
 struct TileStage {
     int32_t lo[kTokChunk];
     int32_t pre[kTokChunk + 1];
+    uint8_t run_tok[kRunCap];      // token of the first posting of run r
     uint32_t scan[33];
-    uint32_t n_surv, n_pos, kmin, kmax;
-    uint32_t surv_key[kSurvCap];  // order_f32 of the candidate's score
-    uint16_t surv_doc[kSurvCap];  // its doc id within the tile
+    uint32_t n_surv, n_pos, n_touch, kmin, kmax;
+    uint32_t surv_key[kSurvCap];   // order_f32 of the candidate's score
+    uint16_t surv_doc[kSurvCap];   // its doc id within the tile
+    uint16_t touched[kTouchCap];   // doc ids (within the tile) in first-touch order
 };
 
 __global__ void __launch_bounds__(kTileThreads, 3)
@@ -279,32 +292,31 @@ __global__ void __launch_bounds__(kTileThreads, 3)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     float* acc = reinterpret_cast<float*>(smem);
-    uint32_t* mask = reinterpret_cast<uint32_t*>(acc + W);
-    SelectState& st = *reinterpret_cast<SelectState*>(mask + W / 32);
+    SelectState& st = *reinterpret_cast<SelectState*>(acc + W);
     TileStage& ts = *reinterpret_cast<TileStage*>(&st + 1);
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
+    const float neg0 = __uint_as_float(kUntouched);
     for (int i = tid; i < W; i += kTileThreads)
-        acc[i] = 0.0f;
-    for (int i = tid; i < W / 32; i += kTileThreads)
-        mask[i] = 0u;
+        acc[i] = neg0;
 
-    const int64_t n_items = (int64_t)nq * n_tiles;
+    const int32_t n_items = nq * n_tiles;  // < 2^31 (checked by the host)
     const int64_t per = (int64_t)n_tiles + 1;
-    // Tile-major order: tile 0 of every query first, so the running
-    // threshold of a query is usually known when its later tiles run, and
-    // the segments in flight at once all belong to one doc tile.
+    // Tile-major order: item = tile * nq + q, tile 0 of every query first, so
+    // the running threshold of a query is usually known when its later tiles
+    // run, and the segments in flight at once all belong to one doc tile.
+    // (tile, q) advance by the grid stride without dividing.
+    const int32_t step_t = (int32_t)(gridDim.x / nq), step_q = (int32_t)(gridDim.x % nq);
     // Warp 0 prefetches the first token chunk's segment bounds of the CTA's
     // next item (lane l: tokens 2l and 2l+1), thread 0 that query's threshold.
     int32_t pf_lo0 = 0, pf_lo1 = 0, pf_hi0 = 0, pf_hi1 = 0;
     uint32_t pf_tau = 0;
-#define BM25_PREFETCH(ITEM)                                                          \
+#define BM25_PREFETCH(ITEM, TILE, Q)                                                 \
     do {                                                                             \
-        const int64_t it_ = (ITEM);                                                  \
-        if (tid < 32 && it_ < n_items) {                                             \
-            const int32_t t_ = (int32_t)(it_ / nq);                                  \
-            const int64_t q_ = it_ - (int64_t)t_ * nq;                               \
+        if (tid < 32 && (ITEM) < n_items) {                                          \
+            const int32_t t_ = (TILE);                                               \
+            const int32_t q_ = (Q);                                                  \
             int64_t a_ = q_off[q_], b_ = q_off[q_ + 1];                              \
             a_ = a_ < 0 ? 0 : (a_ > n_tok ? n_tok : a_);                             \
             b_ = b_ < a_ ? a_ : (b_ > n_tok ? n_tok : b_);                           \
@@ -322,15 +334,19 @@ __global__ void __launch_bounds__(kTileThreads, 3)
                 pf_tau = *(volatile uint32_t*)&thresh[q_];                           \
         }                                                                            \
     } while (0)
-    BM25_PREFETCH(blockIdx.x);
+    int32_t tile = (int32_t)(blockIdx.x / nq), q = (int32_t)(blockIdx.x % nq);
+    BM25_PREFETCH((int32_t)blockIdx.x, tile, q);
     __syncthreads();
 
-    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int32_t tile = (int32_t)(item / nq);
-        const int64_t q = item - (int64_t)tile * nq;
+    for (int32_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        int32_t ntile = tile + step_t, nqq = q + step_q;  // the CTA's next item
+        if (nqq >= nq) {
+            nqq -= nq;
+            ntile++;
+        }
+        const int32_t nitem = item + (int32_t)gridDim.x;
         const int64_t d0 = (int64_t)tile * W;
         const int32_t wd = (int32_t)min((int64_t)W, n_docs - d0);
-        const int32_t nwords = (wd + 31) >> 5;
         int64_t m0 = q_off[q], m1 = q_off[q + 1];
         m0 = m0 < 0 ? 0 : (m0 > n_tok ? n_tok : m0);
         m1 = m1 < m0 ? m0 : (m1 > n_tok ? n_tok : m1);
@@ -340,6 +356,7 @@ __global__ void __launch_bounds__(kTileThreads, 3)
             st.minkey = ~0ull;
             ts.n_surv = 0;
             ts.n_pos = 0;
+            ts.n_touch = 0;
             ts.kmin = 0xffffffffu;
             ts.kmax = 0u;
         }
@@ -366,60 +383,89 @@ __global__ void __launch_bounds__(kTileThreads, 3)
                     len[h] = hh - l;
                     ts.lo[i] = l;
                 }
-                int32_t s2 = len[0] + len[1];
-                int32_t inc = warp_inclusive_sum(s2);
+                const int32_t s2 = len[0] + len[1];
+                const int32_t inc = warp_inclusive_sum(s2);
                 ts.pre[2 * tid] = inc - s2;
                 ts.pre[2 * tid + 1] = inc - s2 + len[0];
                 if (tid == 31)
                     ts.pre[kTokChunk] = inc;
+                __syncwarp();
+                // the token holding the first posting of each run of 32
+                const int32_t total = ts.pre[kTokChunk];
+                for (int r = tid; r < (int)kRunCap && r * 32 < total; r += 32) {
+                    const int32_t e = r * 32;
+                    int a = 0, b = cnt;  // pre[a] <= e < pre[b]
+                    while (b - a > 1) {
+                        const int mid = (a + b) >> 1;
+                        if (ts.pre[mid] <= e)
+                            a = mid;
+                        else
+                            b = mid;
+                    }
+                    ts.run_tok[r] = (uint8_t)a;
+                }
             }
             if (mb == m0)
-                BM25_PREFETCH(item + gridDim.x);  // overlaps with this item's work
+                BM25_PREFETCH(nitem, ntile, nqq);  // overlaps with this item's work
             __syncthreads();
             const int32_t total = ts.pre[kTokChunk];
-            // Warp w takes runs of 32 consecutive postings; the run's token is
-            // found once per warp, each lane then steps forward over empty or
-            // finished segments.
+            // Warp w takes runs of 32 consecutive postings; each lane starts
+            // from its run's first token and steps over finished segments.
             constexpr int U = 4;  // runs in flight per warp
-            for (int32_t r0 = warp * 32; r0 < total; r0 += U * kTileThreads) {
+            for (int32_t r0 = warp; r0 * 32 < total; r0 += U * (kTileThreads / 32)) {
                 int32_t dd[U];
                 float vv[U];
 #pragma unroll
                 for (int u = 0; u < U; u++) {
-                    const int32_t eb = r0 + u * kTileThreads;
+                    const int32_t r = r0 + u * (kTileThreads / 32);
+                    const int32_t e = r * 32 + lane;
                     dd[u] = -1;
-                    if (eb < total) {
-                        int a = 0, b = cnt;  // pre[a] <= eb < pre[b]
-                        while (b - a > 1) {
-                            int mid = (a + b) >> 1;
-                            if (ts.pre[mid] <= eb)
-                                a = mid;
-                            else
-                                b = mid;
+                    if (e < total) {
+                        int a;
+                        if (r < (int32_t)kRunCap) {
+                            a = ts.run_tok[r];
+                        } else {
+                            int lo_ = 0, hi_ = cnt;
+                            while (hi_ - lo_ > 1) {
+                                const int mid = (lo_ + hi_) >> 1;
+                                if (ts.pre[mid] <= e)
+                                    lo_ = mid;
+                                else
+                                    hi_ = mid;
+                            }
+                            a = lo_;
                         }
-                        const int32_t e = eb + lane;
-                        if (e < total) {
-                            while (ts.pre[a + 1] <= e)
-                                a++;
-                            const int32_t j = ts.lo[a] + (e - ts.pre[a]);
-                            dd[u] = __ldg(indices + j) - (int32_t)d0;
-                            vv[u] = __ldg(data + j);
-                        }
+                        while (ts.pre[a + 1] <= e)
+                            a++;
+                        const int32_t j = ts.lo[a] + (e - ts.pre[a]);
+                        dd[u] = __ldg(indices + j) - (int32_t)d0;
+                        vv[u] = __ldg(data + j);
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < U; u++) {
                     const int32_t d = dd[u];
+                    bool first = false;
                     if ((uint32_t)d < (uint32_t)wd) {  // holds for any well-formed index
-                        atomicAdd(&acc[d], vv[u]);
-                        atomicOr(&mask[d >> 5], 1u << (d & 31));
+                        const float old = atomicAdd(&acc[d], vv[u]);
+                        first = __float_as_uint(old) == kUntouched;
+                    }
+                    const uint32_t bal = __ballot_sync(0xffffffffu, first);
+                    if (bal) {
+                        uint32_t base = 0;
+                        if (lane == __ffs(bal) - 1)
+                            base = atomicAdd(&ts.n_touch, (uint32_t)__popc(bal));
+                        base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
+                        const uint32_t slot = base + __popc(bal & lanemask_lt());
+                        if (first && slot < kTouchCap)
+                            ts.touched[slot] = (uint16_t)d;
                     }
                 }
             }
             __syncthreads();
         }
         if (m0 == m1) {
-            BM25_PREFETCH(item + gridDim.x);
+            BM25_PREFETCH(nitem, ntile, nqq);
             __syncthreads();
         }
 
@@ -429,39 +475,39 @@ __global__ void __launch_bounds__(kTileThreads, 3)
         // in the top k' (documents AT tau can, through the doc-id tie rule).
         const uint32_t tau = st.tau;
         const uint32_t kp = (uint32_t)min(kprime, wd);
+        const uint32_t n_touch = ts.n_touch;
+        const bool listed = n_touch <= kTouchCap;  // else walk the whole tile
+        const uint32_t n_walk = listed ? n_touch : (uint32_t)wd;
         {
             uint32_t pos = 0, kmin = 0xffffffffu, kmax = 0u;
-            for (int w0 = warp * 32; w0 < nwords; w0 += kTileThreads) {
-                const int w = w0 + lane;
-                uint32_t bits = (w < nwords) ? mask[w] : 0u;
-                const int rounds = __reduce_max_sync(0xffffffffu, __popc(bits));
-                for (int r = 0; r < rounds; r++) {  // warp-uniform
-                    bool keep = false;
-                    int d = 0;
-                    uint32_t o = 0;
-                    if (bits) {
-                        d = (w << 5) + __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const float a = acc[d];
+            for (uint32_t b = warp * 32; b < n_walk; b += kTileThreads) {  // warp-uniform
+                const uint32_t i = b + lane;
+                bool keep = false;
+                int d = 0;
+                uint32_t o = 0;
+                if (i < n_walk) {
+                    d = listed ? ts.touched[i] : (int)i;
+                    const float a = acc[d];
+                    if (__float_as_uint(a) != kUntouched) {
                         o = order_f32(a);
                         pos += (a > 0.0f);
                         keep = o >= tau;
                     }
-                    const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-                    if (bal) {
-                        uint32_t base = 0;
-                        if (lane == __ffs(bal) - 1)
-                            base = atomicAdd(&ts.n_surv, (uint32_t)__popc(bal));
-                        base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
-                        if (keep) {
-                            const uint32_t slot = base + __popc(bal & lanemask_lt());
-                            if (slot < kSurvCap) {
-                                ts.surv_key[slot] = o;
-                                ts.surv_doc[slot] = (uint16_t)d;
-                            }
-                            kmin = min(kmin, o);
-                            kmax = max(kmax, o);
+                }
+                const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+                if (bal) {
+                    uint32_t base = 0;
+                    if (lane == __ffs(bal) - 1)
+                        base = atomicAdd(&ts.n_surv, (uint32_t)__popc(bal));
+                    base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
+                    if (keep) {
+                        const uint32_t slot = base + __popc(bal & lanemask_lt());
+                        if (slot < kSurvCap) {
+                            ts.surv_key[slot] = o;
+                            ts.surv_doc[slot] = (uint16_t)d;
                         }
+                        kmin = min(kmin, o);
+                        kmax = max(kmax, o);
                     }
                 }
             }
@@ -479,32 +525,34 @@ __global__ void __launch_bounds__(kTileThreads, 3)
         // Untouched documents score exactly 0.  They can enter the tile's top
         // k' only if 0 clears tau and fewer than k' touched documents score
         // above 0; then the k' lowest-id untouched ones join the candidates.
+        // (Rare: the whole tile is scanned, 32 documents per thread-step.)
         if (tau <= kZeroKey && ts.n_pos < kp) {
+            const int32_t nwords = (wd + 31) >> 5;
             uint32_t carry = 0;
             for (int w0 = 0; w0 < nwords && carry < kp; w0 += kTileThreads) {
                 const int w = w0 + tid;
                 uint32_t zeros = 0;
                 if (w < nwords) {
-                    uint32_t valid = (w == nwords - 1 && (wd & 31)) ? ((1u << (wd & 31)) - 1u)
-                                                                    : 0xffffffffu;
-                    zeros = ~mask[w] & valid;
+                    const int dmax = min(32, wd - (w << 5));
+                    for (int b2 = 0; b2 < dmax; b2++)
+                        if (__float_as_uint(acc[(w << 5) + b2]) == kUntouched)
+                            zeros |= 1u << b2;
                 }
-                uint32_t z = __popc(zeros);
+                const uint32_t z = __popc(zeros);
                 uint32_t tot;
-                uint32_t ex = block_exclusive_sum(z, ts.scan, &tot) + carry;
+                const uint32_t ex = block_exclusive_sum(z, ts.scan, &tot) + carry;
                 if (w < nwords && ex < kp) {
-                    uint32_t take = kp - ex;
+                    const uint32_t take = kp - ex;
                     uint32_t fill = zeros;
                     if (take < z) {  // keep only the lowest `take` zero bits
                         uint32_t f = 0;
                         for (uint32_t c = 0; c < take; c++) {
-                            uint32_t low = fill & (0u - fill);
+                            const uint32_t low = fill & (0u - fill);
                             f |= low;
                             fill ^= low;
                         }
                         fill = f;
                     }
-                    mask[w] |= fill;
                     if (fill) {
                         atomicMin(&ts.kmin, kZeroKey);
                         atomicMax(&ts.kmax, kZeroKey);
@@ -527,7 +575,7 @@ __global__ void __launch_bounds__(kTileThreads, 3)
         // ---- select and emit -------------------------------------------------
         const uint32_t n_cand = ts.n_surv;
         const uint32_t n_emit = n_cand < kp ? n_cand : kp;
-        u64* out = cand + item * (int64_t)kprime;
+        u64* out = cand + (int64_t)item * kprime;
         auto emit = [&](u64 key) {
             const uint32_t slot = atomicAdd(&st.ctr, 1u);
             if (slot < n_emit) {
@@ -538,39 +586,37 @@ __global__ void __launch_bounds__(kTileThreads, 3)
         const bool in_smem = n_cand <= kSurvCap;
         if (n_emit > 0 && in_smem) {
             const uint32_t kmin = ts.kmin, kmax = ts.kmax;
-            const int skip = common_bytes(kmin, kmax);
-            block_select_idx<false>(st, n_cand, kp, skip, (u64)kmax << 32,
+            block_select_idx<false>(st, n_cand, kp, common_bytes(kmin, kmax), (u64)kmax << 32,
                                     [&](uint32_t i) {
                                         return ((u64)ts.surv_key[i] << 32) |
                                                (u64)(~(uint32_t)(d0 + ts.surv_doc[i]));
                                     },
                                     emit);
-        } else if (n_emit > 0) {  // too many to buffer: walk the bitmask instead
+        } else if (n_emit > 0) {
+            // more candidates than the buffer holds: select straight from the
+            // accumulators (untouched documents that joined through the fill
+            // score 0 and read as -0.0, which order_f32 folds onto +0.0)
+            const bool fill_on = tau <= kZeroKey && ts.n_pos < kp;
             auto for_each = [&](auto f) {
-                for (int w = tid; w < nwords; w += kTileThreads) {
-                    uint32_t bits = mask[w];
-                    while (bits) {
-                        const int bpos = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const int d = (w << 5) + bpos;
-                        const float a = acc[d];
-                        if (order_f32(a) >= tau)
-                            f(make_key(a, (uint32_t)(d0 + d)));
-                    }
+                for (int d = tid; d < wd; d += kTileThreads) {
+                    const float a = acc[d];
+                    const bool touched = __float_as_uint(a) != kUntouched;
+                    if ((touched || fill_on) && order_f32(a) >= tau)
+                        f(make_key(a, (uint32_t)(d0 + d)));
                 }
             };
-            block_select(st, n_cand, kp, for_each, emit);
+            // with the fill on, every untouched document is offered; the
+            // lowest ids win their ties, exactly as with the buffered fill
+            block_select(st, fill_on ? 0xffffffffu : n_cand, kp, for_each, emit);
         }
 
-        // ---- reset the touched accumulators and the bitmask -------------------
-        for (int w = tid; w < nwords; w += kTileThreads) {
-            uint32_t bits = mask[w];
-            while (bits) {
-                int bpos = __ffs(bits) - 1;
-                bits &= bits - 1;
-                acc[(w << 5) + bpos] = 0.0f;
-            }
-            mask[w] = 0u;
+        // ---- reset the touched accumulators ----------------------------------
+        if (listed) {
+            for (uint32_t i = tid; i < n_touch; i += kTileThreads)
+                acc[ts.touched[i]] = neg0;
+        } else {
+            for (int i = tid; i < wd; i += kTileThreads)
+                acc[i] = neg0;
         }
         __syncthreads();
         if (tid == 0) {
@@ -580,6 +626,8 @@ __global__ void __launch_bounds__(kTileThreads, 3)
             if (n_emit == kp && kp > 0)
                 atomicMax(&thresh[q], (uint32_t)(st.minkey >> 32));
         }
+        tile = ntile;
+        q = nqq;
     }
 #undef BM25_PREFETCH
 }
@@ -691,7 +739,7 @@ __global__ void __launch_bounds__(kMergeThreads)
 
 size_t tile_smem_bytes(int32_t W)
 {
-    return (size_t)W * 4 + (size_t)(W / 32) * 4 + sizeof(SelectState) + sizeof(TileStage);
+    return (size_t)W * 4 + sizeof(SelectState) + sizeof(TileStage);
 }
 
 template <typename T>
@@ -772,6 +820,9 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
         return set_error(BM25_E_INVALID, "%lld doc tiles of %d documents: use wider tiles",
                          (long long)n_tiles64, W);
     const int32_t n_tiles = (int32_t)n_tiles64;
+    if ((int64_t)nq * n_tiles >= INT32_MAX)
+        return set_error(BM25_E_INVALID, "%d queries x %d doc tiles is too many work items for "
+                         "one call", nq, n_tiles);
     BM25_TRY(workspace_reserve(ix, ws, nq, n_tok, kprime, n_tiles));
 
     const int max_blocks = di.sm_count * 16;
