@@ -73,6 +73,16 @@ enum bm25_accumulator {
 /* Upper bound on min(k, n_docs) for one retrieval call. */
 #define BM25_MAX_K 4096
 
+/* How retrieval runs a query batch.  Results do not depend on the plan
+ * (beyond the order of FP32 additions); only speed does.  Zero fields take
+ * the library's defaults. */
+typedef struct bm25_plan {
+    int32_t accumulator;   /* enum bm25_accumulator */
+    int32_t tile_docs;     /* doc-tile width: a multiple of 1024 in [1024, 49152] */
+    int32_t block_threads; /* threads per CTA of the tiled kernel: 128, 256 or 512 */
+    int32_t reserved;      /* must be 0 */
+} bm25_plan;
+
 /* ------------------------------------------------------------------ index */
 
 /* Eager index build (Sec. 2 "Eager index-time scoring", "Efficient Matrix
@@ -187,19 +197,20 @@ int bm25_workspace_create(const bm25_index* index, int32_t max_queries,
                           bm25_workspace** out);
 void bm25_workspace_free(bm25_workspace* ws);
 
-/* bm25_retrieve with an explicit workspace and accumulator strategy
- * (enum bm25_accumulator) and doc-tile width (0 = the index's plan).  Calls
- * with different workspaces may overlap on the device. */
+/* bm25_retrieve with an explicit workspace and plan (HOST pointer; NULL =
+ * the index's plan).  Calls with different workspaces may overlap on the
+ * device. */
 int bm25_retrieve_ws(const bm25_index* index, bm25_workspace* ws,
                      const int32_t* query_tokens, int64_t n_query_tokens,
                      const int64_t* query_offsets, int32_t n_queries, int32_t k,
-                     int32_t* out_ids, float* out_scores, int accumulator,
-                     int32_t tile_docs, void* cuda_stream);
+                     int32_t* out_ids, float* out_scores, const bm25_plan* plan,
+                     void* cuda_stream);
 
-/* Sets the index's default plan: accumulator strategy and doc-tile width in
- * documents (a multiple of 1024 between 1024 and 49152; 0 keeps the current
- * value). */
-int bm25_index_set_plan(bm25_index* index, int accumulator, int32_t tile_docs);
+/* Sets / reads the index's default plan (HOST pointers).  Zero fields of a
+ * plan being set keep the current values; an invalid field fails with
+ * BM25_E_INVALID and changes nothing. */
+int bm25_index_set_plan(bm25_index* index, const bm25_plan* plan);
+int bm25_index_get_plan(const bm25_index* index, bm25_plan* plan);
 
 /* --------------------------------------------------------------- utility */
 

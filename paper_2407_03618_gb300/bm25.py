@@ -23,6 +23,16 @@ STATUS = {0: "BM25_OK", -1: "BM25_E_INVALID", -2: "BM25_E_TOKEN_RANGE", -3: "BM2
 MAX_K = 4096
 
 
+class Plan(ctypes.Structure):
+    """bm25_plan: how retrieval runs (zero fields = library defaults)."""
+    _fields_ = [("accumulator", ctypes.c_int32), ("tile_docs", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"accumulator": self.accumulator, "tile_docs": self.tile_docs,
+                "block_threads": self.block_threads}
+
+
 class BM25Error(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
@@ -66,8 +76,9 @@ def load(path: str | None = None):
         "bm25_retrieve_host": (cint, [P, P, P, i32, i32, P, P, P]),
         "bm25_workspace_create": (cint, [P, i32, i64, i32, PP]),
         "bm25_workspace_free": (None, [P]),
-        "bm25_retrieve_ws": (cint, [P, P, P, i64, P, i32, i32, P, P, cint, i32, P]),
-        "bm25_index_set_plan": (cint, [P, cint, i32]),
+        "bm25_retrieve_ws": (cint, [P, P, P, i64, P, i32, i32, P, P, P, P]),
+        "bm25_index_set_plan": (cint, [P, P]),
+        "bm25_index_get_plan": (cint, [P, P]),
         "bm25_last_error": (ctypes.c_char_p, []),
         "bm25_launch_count": (i64, []),
         "bm25_version": (ctypes.c_char_p, []),
@@ -233,15 +244,20 @@ class Index:
         out.update(inf)
         return out
 
-    def set_plan(self, accumulator: int = ACC_AUTO, tile_docs: int = 0):
-        _check(load().bm25_index_set_plan(self.handle, accumulator, tile_docs))
+    def set_plan(self, accumulator: int = ACC_AUTO, tile_docs: int = 0, block_threads: int = 0):
+        p = Plan(accumulator, tile_docs, block_threads, 0)
+        _check(load().bm25_index_set_plan(self.handle, ctypes.byref(p)))
+
+    def get_plan(self) -> dict:
+        p = Plan()
+        _check(load().bm25_index_get_plan(self.handle, ctypes.byref(p)))
+        return p.as_dict()
 
     def sync_status(self, stream=None):
         _check(load().bm25_sync_status(self.handle, _stream(stream)))
 
     def retrieve(self, q_tokens, q_offsets, k: int, out=None, stream=None,
-                 workspace: Workspace | None = None, accumulator: int = ACC_AUTO,
-                 tile_docs: int = 0):
+                 workspace: Workspace | None = None, plan: dict | None = None):
         """Device path.  q_tokens CUDA int32, q_offsets CUDA int64 [nQ+1].
         Returns (ids int32 [nQ, k], scores float32 [nQ, k]) CUDA tensors."""
         import torch
@@ -253,16 +269,16 @@ class Index:
             sc = torch.empty((nq, max(k, 0)), dtype=torch.float32, device=qo.device)
         else:
             ids, sc = out
-        if workspace is None and accumulator == ACC_AUTO and tile_docs == 0:
+        if workspace is None and plan is None:
             _check(load().bm25_retrieve(self.handle, qt.data_ptr(), qt.numel(), qo.data_ptr(), nq,
                                         k, ids.data_ptr(), sc.data_ptr(), _stream(stream)))
         else:
             if workspace is None:
                 workspace = self._default_workspace(nq, qt.numel(), k)
+            p = Plan(**(plan or {}))
             _check(load().bm25_retrieve_ws(self.handle, workspace.handle, qt.data_ptr(),
                                            qt.numel(), qo.data_ptr(), nq, k, ids.data_ptr(),
-                                           sc.data_ptr(), accumulator, tile_docs,
-                                           _stream(stream)))
+                                           sc.data_ptr(), ctypes.byref(p), _stream(stream)))
         return ids, sc
 
     def _default_workspace(self, nq, ntok, k):

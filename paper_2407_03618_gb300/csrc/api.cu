@@ -97,6 +97,12 @@ int check_retrieve_args(const bm25_index* ix, int64_t n_tok, int32_t nq, int32_t
     return BM25_OK;
 }
 
+Plan plan_of(const bm25_index* ix)
+{
+    std::lock_guard<std::mutex> g(const_cast<bm25_index*>(ix)->mu);
+    return ix->plan;
+}
+
 int default_ws(const bm25_index* ix, bm25_workspace** out)
 {
     bm25_index* m = const_cast<bm25_index*>(ix);
@@ -110,6 +116,35 @@ int default_ws(const bm25_index* ix, bm25_workspace** out)
 }
 
 }  // namespace
+
+int merge_plan(const bm25_plan* in, const Plan& base, Plan* out)
+{
+    Plan p = base;
+    if (in) {
+        if (in->reserved != 0)
+            return set_error(BM25_E_INVALID, "bm25_plan.reserved must be 0");
+        if (in->accumulator < BM25_ACC_AUTO || in->accumulator > BM25_ACC_L2_DENSE)
+            return set_error(BM25_E_INVALID, "unknown accumulator %d", in->accumulator);
+        if (in->tile_docs != 0 &&
+            (in->tile_docs < 1024 || in->tile_docs > 49152 || in->tile_docs % 1024))
+            return set_error(BM25_E_INVALID,
+                             "tile_docs %d must be a multiple of 1024 in [1024, 49152]",
+                             in->tile_docs);
+        if (in->block_threads != 0 && in->block_threads != 128 && in->block_threads != 256 &&
+            in->block_threads != 512)
+            return set_error(BM25_E_INVALID, "block_threads %d must be 128, 256 or 512",
+                             in->block_threads);
+        if (in->accumulator)
+            p.accumulator = in->accumulator;
+        if (in->tile_docs)
+            p.tile_docs = in->tile_docs;
+        if (in->block_threads)
+            p.threads = in->block_threads;
+    }
+    *out = p;
+    return BM25_OK;
+}
+
 }  // namespace bm25
 
 using namespace bm25;
@@ -360,27 +395,22 @@ int bm25_retrieve(const bm25_index* ix, const int32_t* query_tokens, int64_t n_q
     bm25_workspace* ws = nullptr;
     BM25_TRY(default_ws(ix, &ws));
     return retrieve_device(ix, ws, query_tokens, query_offsets, n_queries, n_query_tokens, k,
-                           out_ids, out_scores, ix->plan.accumulator, ix->plan.tile_docs,
-                           (cudaStream_t)cuda_stream);
+                           out_ids, out_scores, plan_of(ix), (cudaStream_t)cuda_stream);
 }
 
 int bm25_retrieve_ws(const bm25_index* ix, bm25_workspace* ws, const int32_t* query_tokens,
                      int64_t n_query_tokens, const int64_t* query_offsets, int32_t n_queries,
-                     int32_t k, int32_t* out_ids, float* out_scores, int accumulator,
-                     int32_t tile_docs, void* cuda_stream)
+                     int32_t k, int32_t* out_ids, float* out_scores, const bm25_plan* plan,
+                     void* cuda_stream)
 {
     clear_error();
     BM25_TRY(check_retrieve_args(ix, n_query_tokens, n_queries, k));
     if (!ws)
         return set_error(BM25_E_INVALID, "workspace is NULL");
-    if (accumulator < BM25_ACC_AUTO || accumulator > BM25_ACC_L2_DENSE)
-        return set_error(BM25_E_INVALID, "unknown accumulator %d", accumulator);
-    if (tile_docs != 0 && (tile_docs < 1024 || tile_docs > 49152 || tile_docs % 1024))
-        return set_error(BM25_E_INVALID, "tile_docs %d must be a multiple of 1024 in [1024, 49152]",
-                         tile_docs);
+    Plan p;
+    BM25_TRY(merge_plan(plan, plan_of(ix), &p));
     return retrieve_device(ix, ws, query_tokens, query_offsets, n_queries, n_query_tokens, k,
-                           out_ids, out_scores, accumulator ? accumulator : ix->plan.accumulator,
-                           tile_docs ? tile_docs : ix->plan.tile_docs, (cudaStream_t)cuda_stream);
+                           out_ids, out_scores, p, (cudaStream_t)cuda_stream);
 }
 
 int bm25_retrieve_host(const bm25_index* ix, const int32_t* query_tokens,
@@ -428,8 +458,7 @@ int bm25_retrieve_host(const bm25_index* ix, const int32_t* query_tokens,
     BM25_CUDA_TRY(cudaMemcpyAsync(ws->q_offsets, query_offsets,
                                   sizeof(int64_t) * (n_queries + 1), cudaMemcpyHostToDevice, s));
     BM25_TRY(retrieve_device(ix, ws, ws->q_tokens, ws->q_offsets, n_queries, n_tok, k,
-                             ws->out_ids, ws->out_scores, ix->plan.accumulator,
-                             ix->plan.tile_docs, s));
+                             ws->out_ids, ws->out_scores, plan_of(ix), s));
     BM25_CUDA_TRY(cudaMemcpyAsync(out_ids, ws->out_ids, sizeof(int32_t) * (size_t)n_queries * k,
                                   cudaMemcpyDeviceToHost, s));
     BM25_CUDA_TRY(cudaMemcpyAsync(out_scores, ws->out_scores,
@@ -439,20 +468,28 @@ int bm25_retrieve_host(const bm25_index* ix, const int32_t* query_tokens,
     return BM25_OK;
 }
 
-int bm25_index_set_plan(bm25_index* ix, int accumulator, int32_t tile_docs)
+int bm25_index_set_plan(bm25_index* ix, const bm25_plan* plan)
 {
     clear_error();
-    if (!ix)
-        return set_error(BM25_E_INVALID, "index is NULL");
-    if (accumulator < BM25_ACC_AUTO || accumulator > BM25_ACC_L2_DENSE)
-        return set_error(BM25_E_INVALID, "unknown accumulator %d", accumulator);
-    if (tile_docs != 0 && (tile_docs < 1024 || tile_docs > 49152 || tile_docs % 1024))
-        return set_error(BM25_E_INVALID, "tile_docs %d must be a multiple of 1024 in [1024, 49152]",
-                         tile_docs);
+    if (!ix || !plan)
+        return set_error(BM25_E_INVALID, "NULL argument");
+    Plan p;
+    BM25_TRY(merge_plan(plan, plan_of(ix), &p));
     std::lock_guard<std::mutex> g(ix->mu);
-    ix->plan.accumulator = accumulator;
-    if (tile_docs)
-        ix->plan.tile_docs = tile_docs;
+    ix->plan = p;
+    return BM25_OK;
+}
+
+int bm25_index_get_plan(const bm25_index* ix, bm25_plan* plan)
+{
+    clear_error();
+    if (!ix || !plan)
+        return set_error(BM25_E_INVALID, "NULL argument");
+    Plan p = plan_of(ix);
+    plan->accumulator = p.accumulator;
+    plan->tile_docs = p.tile_docs;
+    plan->block_threads = p.threads;
+    plan->reserved = 0;
     return BM25_OK;
 }
 

@@ -66,7 +66,11 @@ int device_info(DeviceInfo* out);
 struct Plan {
     int accumulator = BM25_ACC_AUTO;
     int32_t tile_docs = 16384;
+    int32_t threads = 512;
 };
+// Fills zero fields of `in` from `base`; BM25_E_INVALID (nothing changed) if
+// a field is out of range.
+int merge_plan(const bm25_plan* in, const Plan& base, Plan* out);
 
 }  // namespace bm25
 
@@ -127,8 +131,8 @@ int pool_for_current_device(cudaMemPool_t* out);
 // ---- retrieval (retrieve.cu) -------------------------------------------
 int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_tokens,
                     const int64_t* q_offsets, int32_t n_queries, int64_t n_query_tokens,
-                    int32_t k, int32_t* out_ids, float* out_scores, int accumulator,
-                    int32_t tile_docs, cudaStream_t stream);
+                    int32_t k, int32_t* out_ids, float* out_scores, const Plan& plan,
+                    cudaStream_t stream);
 int workspace_reserve(const bm25_index* ix, bm25_workspace* ws, int32_t n_queries,
                       int64_t n_query_tokens, int32_t kprime, int64_t n_tiles);
 void workspace_release(bm25_workspace* ws);

@@ -267,22 +267,41 @@ __device__ __forceinline__ int common_bytes(uint32_t kmin, uint32_t kmax)
 // sum never returns to -0.0.  First touches append the document to a list,
 // and the later passes (candidates, reset) walk that list; a tile touched
 // more densely than the list holds is walked in full instead.
+#ifdef BM25_PHASE_TIMING
+// Diagnostic build only: per-phase cycle totals of k_tile_topk, summed over
+// CTAs (thread 0's view), and item statistics.
+__device__ unsigned long long g_phase[16];
+#define BM25_PHASE(I)                                                                \
+    do {                                                                             \
+        if (tid == 0) {                                                              \
+            const long long now_ = clock64();                                        \
+            ph_acc[I] += (unsigned long long)(now_ - ph_t);                          \
+            ph_t = now_;                                                             \
+        }                                                                            \
+    } while (0)
+#else
+#define BM25_PHASE(I) \
+    do {              \
+    } while (0)
+#endif
 constexpr uint32_t kUntouched = 0x80000000u;  // bits of -0.0f
 constexpr uint32_t kTouchCap = 1536;  // sized so that three 16K-document tiles fit on an SM
-constexpr uint32_t kRunCap = 128;             // runs of 32 postings with a cached token
+constexpr uint32_t kRunCap = 128;     // runs of 32 postings with a cached token
 
 struct TileStage {
     int32_t lo[kTokChunk];
     int32_t pre[kTokChunk + 1];
     uint8_t run_tok[kRunCap];      // token of the first posting of run r
     uint32_t scan[33];
+    int32_t qoff[2][2];            // token range of the current / next item, by parity
     uint32_t n_surv, n_pos, n_touch, kmin, kmax;
     uint32_t surv_key[kSurvCap];   // order_f32 of the candidate's score
     uint16_t surv_doc[kSurvCap];   // its doc id within the tile
     uint16_t touched[kTouchCap];   // doc ids (within the tile) in first-touch order
 };
 
-__global__ void __launch_bounds__(kTileThreads, 3)
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1536 / THREADS)
     k_tile_topk(const int32_t* __restrict__ q_tokens, int64_t n_tok,
                 const int64_t* __restrict__ q_off, int32_t nq, int64_t n_docs,
                 const int32_t* __restrict__ indices, const float* __restrict__ data,
@@ -290,6 +309,7 @@ __global__ void __launch_bounds__(kTileThreads, 3)
                 uint32_t* __restrict__ thresh, uint32_t* __restrict__ tcount,
                 u64* __restrict__ cand)
 {
+    constexpr int WARPS = THREADS / 32;
     extern __shared__ __align__(16) unsigned char smem[];
     float* acc = reinterpret_cast<float*>(smem);
     SelectState& st = *reinterpret_cast<SelectState*>(acc + W);
@@ -298,7 +318,7 @@ __global__ void __launch_bounds__(kTileThreads, 3)
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const float neg0 = __uint_as_float(kUntouched);
-    for (int i = tid; i < W; i += kTileThreads)
+    for (int i = tid; i < W; i += THREADS)
         acc[i] = neg0;
 
     const int32_t n_items = nq * n_tiles;  // < 2^31 (checked by the host)
@@ -308,50 +328,103 @@ __global__ void __launch_bounds__(kTileThreads, 3)
     // run, and the segments in flight at once all belong to one doc tile.
     // (tile, q) advance by the grid stride without dividing.
     const int32_t step_t = (int32_t)(gridDim.x / nq), step_q = (int32_t)(gridDim.x % nq);
-    // Warp 0 prefetches the first token chunk's segment bounds of the CTA's
-    // next item (lane l: tokens 2l and 2l+1), thread 0 that query's threshold.
+    auto advance = [&](int32_t& t, int32_t& qq) {
+        t += step_t;
+        qq += step_q;
+        if (qq >= nq) {
+            qq -= nq;
+            t++;
+        }
+    };
+    const int32_t ntok32 = (int32_t)n_tok;  // < 2^31 (checked by the host)
+    auto clamp_off = [&](int64_t v) -> int32_t {
+        return v < 0 ? 0 : (v > n_tok ? ntok32 : (int32_t)v);
+    };
+    // Warp 0 runs a two-stage pipeline over the CTA's items: while item i is
+    // processed it loads the segment bounds of item i+1 (lane l: tokens 2l
+    // and 2l+1 of the first chunk) from token ranges it loaded during item
+    // i-1, and the token range of item i+2.  Thread 0 also loads item i+1's
+    // threshold.  No load of the pipeline is consumed in the item it is
+    // issued in.
+    int32_t tile = (int32_t)(blockIdx.x / nq), q = (int32_t)(blockIdx.x % nq);
+    int32_t t1 = tile, q1 = q;
+    advance(t1, q1);
+    int32_t t2 = t1, q2 = q1;
+    advance(t2, q2);
+    int32_t a1 = 0, b1 = 0, a2 = 0, b2 = 0;  // token ranges of items i+1, i+2 (warp 0)
     int32_t pf_lo0 = 0, pf_lo1 = 0, pf_hi0 = 0, pf_hi1 = 0;
     uint32_t pf_tau = 0;
-#define BM25_PREFETCH(ITEM, TILE, Q)                                                 \
-    do {                                                                             \
-        if (tid < 32 && (ITEM) < n_items) {                                          \
-            const int32_t t_ = (TILE);                                               \
-            const int32_t q_ = (Q);                                                  \
-            int64_t a_ = q_off[q_], b_ = q_off[q_ + 1];                              \
-            a_ = a_ < 0 ? 0 : (a_ > n_tok ? n_tok : a_);                             \
-            b_ = b_ < a_ ? a_ : (b_ > n_tok ? n_tok : b_);                           \
-            const int64_t m_ = a_ + 2 * tid;                                         \
-            pf_lo0 = pf_hi0 = pf_lo1 = pf_hi1 = 0;                                   \
-            if (m_ < b_) {                                                           \
-                pf_lo0 = seg[m_ * per + t_];                                         \
-                pf_hi0 = seg[m_ * per + t_ + 1];                                     \
-            }                                                                        \
-            if (m_ + 1 < b_) {                                                       \
-                pf_lo1 = seg[(m_ + 1) * per + t_];                                   \
-                pf_hi1 = seg[(m_ + 1) * per + t_ + 1];                               \
-            }                                                                        \
-            if (tid == 0)                                                            \
-                pf_tau = *(volatile uint32_t*)&thresh[q_];                           \
-        }                                                                            \
-    } while (0)
-    int32_t tile = (int32_t)(blockIdx.x / nq), q = (int32_t)(blockIdx.x % nq);
-    BM25_PREFETCH((int32_t)blockIdx.x, tile, q);
-    __syncthreads();
-
-    for (int32_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-        int32_t ntile = tile + step_t, nqq = q + step_q;  // the CTA's next item
-        if (nqq >= nq) {
-            nqq -= nq;
-            ntile++;
+    auto load_seg = [&](int32_t t_, int32_t a_, int32_t b_) {
+        const int32_t m_ = a_ + 2 * tid;
+        pf_lo0 = pf_hi0 = pf_lo1 = pf_hi1 = 0;
+        if (m_ < b_) {
+            pf_lo0 = seg[(int64_t)m_ * per + t_];
+            pf_hi0 = seg[(int64_t)m_ * per + t_ + 1];
         }
-        const int32_t nitem = item + (int32_t)gridDim.x;
+        if (m_ + 1 < b_) {
+            pf_lo1 = seg[(int64_t)(m_ + 1) * per + t_];
+            pf_hi1 = seg[(int64_t)(m_ + 1) * per + t_ + 1];
+        }
+    };
+    if (tid < 32) {
+        const int32_t a0 = clamp_off(q_off[q]);
+        const int32_t b0 = max(a0, clamp_off(q_off[q + 1]));
+        load_seg(tile, a0, b0);
+        if (tid == 0) {
+            ts.qoff[0][0] = a0;
+            ts.qoff[0][1] = b0;
+            pf_tau = *(volatile uint32_t*)&thresh[q];
+        }
+        if ((int64_t)blockIdx.x + gridDim.x < n_items) {
+            a1 = clamp_off(q_off[q1]);
+            b1 = max(a1, clamp_off(q_off[q1 + 1]));
+        }
+        if ((int64_t)blockIdx.x + 2 * (int64_t)gridDim.x < n_items) {
+            a2 = clamp_off(q_off[q2]);
+            b2 = max(a2, clamp_off(q_off[q2 + 1]));
+        }
+    }
+    __syncthreads();
+#ifdef BM25_PHASE_TIMING
+    unsigned long long ph_acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long ph_t = clock64();
+#endif
+
+    int parity = 0;
+    for (int32_t item = blockIdx.x; item < n_items; item += gridDim.x, parity ^= 1) {
         const int64_t d0 = (int64_t)tile * W;
         const int32_t wd = (int32_t)min((int64_t)W, n_docs - d0);
-        int64_t m0 = q_off[q], m1 = q_off[q + 1];
-        m0 = m0 < 0 ? 0 : (m0 > n_tok ? n_tok : m0);
-        m1 = m1 < m0 ? m0 : (m1 > n_tok ? n_tok : m1);
+        const int32_t m0 = ts.qoff[parity][0], m1 = ts.qoff[parity][1];
+        const uint32_t my_tau = pf_tau;
+        // warp 0: advance the pipeline (segment bounds of the next item, token
+        // range of the one after), once this item's prefetched values are used
+        auto pipeline = [&]() {
+            if (tid < 32) {
+                const int32_t nitem = item + (int32_t)gridDim.x;
+                if (nitem < n_items) {
+                    load_seg(t1, a1, b1);
+                    if (tid == 0) {
+                        ts.qoff[parity ^ 1][0] = a1;
+                        ts.qoff[parity ^ 1][1] = b1;
+                        pf_tau = *(volatile uint32_t*)&thresh[q1];
+                    }
+                }
+                a1 = a2;
+                b1 = b2;
+                int32_t t3 = t2, q3 = q2;
+                advance(t3, q3);
+                if ((int64_t)nitem + 2 * (int64_t)gridDim.x < n_items) {
+                    a2 = clamp_off(q_off[q3]);
+                    b2 = max(a2, clamp_off(q_off[q3 + 1]));
+                }
+                t1 = t2;
+                q1 = q2;
+                t2 = t3;
+                q2 = q3;
+            }
+        };
         if (tid == 0) {
-            st.tau = pf_tau;
+            st.tau = my_tau;
             st.ctr = 0;
             st.minkey = ~0ull;
             ts.n_surv = 0;
@@ -362,8 +435,8 @@ __global__ void __launch_bounds__(kTileThreads, 3)
         }
 
         // ---- scatter-add the item's postings, a chunk of tokens at a time ----
-        for (int64_t mb = m0; mb < m1; mb += kTokChunk) {
-            const int cnt = (int)min((int64_t)kTokChunk, m1 - mb);
+        for (int32_t mb = m0; mb < m1; mb += kTokChunk) {
+            const int cnt = min(kTokChunk, m1 - mb);
             if (tid < 32) {
                 int32_t len[2];
 #pragma unroll
@@ -374,7 +447,7 @@ __global__ void __launch_bounds__(kTileThreads, 3)
                         l = h ? pf_lo1 : pf_lo0;
                         hh = h ? pf_hi1 : pf_hi0;
                     } else if (i < cnt) {
-                        const int32_t* sg = seg + (mb + i) * per + tile;
+                        const int32_t* sg = seg + (int64_t)(mb + i) * per + tile;
                         l = sg[0];
                         hh = sg[1];
                     }
@@ -404,20 +477,21 @@ __global__ void __launch_bounds__(kTileThreads, 3)
                     }
                     ts.run_tok[r] = (uint8_t)a;
                 }
+                if (mb == m0)
+                    pipeline();
             }
-            if (mb == m0)
-                BM25_PREFETCH(nitem, ntile, nqq);  // overlaps with this item's work
             __syncthreads();
+            BM25_PHASE(0);
             const int32_t total = ts.pre[kTokChunk];
             // Warp w takes runs of 32 consecutive postings; each lane starts
             // from its run's first token and steps over finished segments.
             constexpr int U = 4;  // runs in flight per warp
-            for (int32_t r0 = warp; r0 * 32 < total; r0 += U * (kTileThreads / 32)) {
+            for (int32_t r0 = warp; r0 * 32 < total; r0 += U * WARPS) {
                 int32_t dd[U];
                 float vv[U];
 #pragma unroll
                 for (int u = 0; u < U; u++) {
-                    const int32_t r = r0 + u * (kTileThreads / 32);
+                    const int32_t r = r0 + u * WARPS;
                     const int32_t e = r * 32 + lane;
                     dd[u] = -1;
                     if (e < total) {
@@ -463,9 +537,10 @@ __global__ void __launch_bounds__(kTileThreads, 3)
                 }
             }
             __syncthreads();
+            BM25_PHASE(1);
         }
         if (m0 == m1) {
-            BM25_PREFETCH(nitem, ntile, nqq);
+            pipeline();
             __syncthreads();
         }
 
@@ -480,7 +555,7 @@ __global__ void __launch_bounds__(kTileThreads, 3)
         const uint32_t n_walk = listed ? n_touch : (uint32_t)wd;
         {
             uint32_t pos = 0, kmin = 0xffffffffu, kmax = 0u;
-            for (uint32_t b = warp * 32; b < n_walk; b += kTileThreads) {  // warp-uniform
+            for (uint32_t b = warp * 32; b < n_walk; b += THREADS) {  // warp-uniform
                 const uint32_t i = b + lane;
                 bool keep = false;
                 int d = 0;
@@ -511,25 +586,29 @@ __global__ void __launch_bounds__(kTileThreads, 3)
                     }
                 }
             }
-            pos = warp_sum(pos);
+            pos = __reduce_add_sync(0xffffffffu, pos);
             kmin = __reduce_min_sync(0xffffffffu, kmin);
             kmax = __reduce_max_sync(0xffffffffu, kmax);
             if (lane == 0) {
                 if (pos)
                     atomicAdd(&ts.n_pos, pos);
-                atomicMin(&ts.kmin, kmin);
-                atomicMax(&ts.kmax, kmax);
+                if (kmin <= kmax) {
+                    atomicMin(&ts.kmin, kmin);
+                    atomicMax(&ts.kmax, kmax);
+                }
             }
         }
         __syncthreads();
+        BM25_PHASE(2);
         // Untouched documents score exactly 0.  They can enter the tile's top
         // k' only if 0 clears tau and fewer than k' touched documents score
         // above 0; then the k' lowest-id untouched ones join the candidates.
         // (Rare: the whole tile is scanned, 32 documents per thread-step.)
-        if (tau <= kZeroKey && ts.n_pos < kp) {
+        const bool fill_on = tau <= kZeroKey && ts.n_pos < kp;
+        if (fill_on) {
             const int32_t nwords = (wd + 31) >> 5;
             uint32_t carry = 0;
-            for (int w0 = 0; w0 < nwords && carry < kp; w0 += kTileThreads) {
+            for (int w0 = 0; w0 < nwords && carry < kp; w0 += THREADS) {
                 const int w = w0 + tid;
                 uint32_t zeros = 0;
                 if (w < nwords) {
@@ -571,6 +650,7 @@ __global__ void __launch_bounds__(kTileThreads, 3)
             }
             __syncthreads();
         }
+        BM25_PHASE(3);
 
         // ---- select and emit -------------------------------------------------
         const uint32_t n_cand = ts.n_surv;
@@ -583,8 +663,7 @@ __global__ void __launch_bounds__(kTileThreads, 3)
                 atomicMin(&st.minkey, key);
             }
         };
-        const bool in_smem = n_cand <= kSurvCap;
-        if (n_emit > 0 && in_smem) {
+        if (n_emit > 0 && n_cand <= kSurvCap) {
             const uint32_t kmin = ts.kmin, kmax = ts.kmax;
             block_select_idx<false>(st, n_cand, kp, common_bytes(kmin, kmax), (u64)kmax << 32,
                                     [&](uint32_t i) {
@@ -594,31 +673,37 @@ __global__ void __launch_bounds__(kTileThreads, 3)
                                     emit);
         } else if (n_emit > 0) {
             // more candidates than the buffer holds: select straight from the
-            // accumulators (untouched documents that joined through the fill
-            // score 0 and read as -0.0, which order_f32 folds onto +0.0)
-            const bool fill_on = tau <= kZeroKey && ts.n_pos < kp;
+            // accumulators.  With the fill on every untouched document is
+            // offered (score 0; -0.0 folds onto +0.0 in the key), and the
+            // lowest ids win their ties exactly as with the buffered fill.
             auto for_each = [&](auto f) {
-                for (int d = tid; d < wd; d += kTileThreads) {
+                for (int d = tid; d < wd; d += THREADS) {
                     const float a = acc[d];
                     const bool touched = __float_as_uint(a) != kUntouched;
                     if ((touched || fill_on) && order_f32(a) >= tau)
                         f(make_key(a, (uint32_t)(d0 + d)));
                 }
             };
-            // with the fill on, every untouched document is offered; the
-            // lowest ids win their ties, exactly as with the buffered fill
             block_select(st, fill_on ? 0xffffffffu : n_cand, kp, for_each, emit);
         }
+        BM25_PHASE(4);
 
         // ---- reset the touched accumulators ----------------------------------
         if (listed) {
-            for (uint32_t i = tid; i < n_touch; i += kTileThreads)
+            for (uint32_t i = tid; i < n_touch; i += THREADS)
                 acc[ts.touched[i]] = neg0;
         } else {
-            for (int i = tid; i < wd; i += kTileThreads)
+            for (int i = tid; i < wd; i += THREADS)
                 acc[i] = neg0;
         }
         __syncthreads();
+        BM25_PHASE(5);
+#ifdef BM25_PHASE_TIMING
+        if (tid == 0) {
+            ph_acc[6] += n_touch;
+            ph_acc[7] += n_cand > kp ? 1 : 0;
+        }
+#endif
         if (tid == 0) {
             tcount[item] = n_emit;
             // a full set of k' candidates raises the query's threshold to the
@@ -626,10 +711,13 @@ __global__ void __launch_bounds__(kTileThreads, 3)
             if (n_emit == kp && kp > 0)
                 atomicMax(&thresh[q], (uint32_t)(st.minkey >> 32));
         }
-        tile = ntile;
-        q = nqq;
+        advance(tile, q);
     }
-#undef BM25_PREFETCH
+#ifdef BM25_PHASE_TIMING
+    if (tid == 0)
+        for (int i = 0; i < 8; i++)
+            atomicAdd(&g_phase[i], ph_acc[i]);
+#endif
 }
 
 // ---- R3 -----------------------------------------------------------------------
@@ -759,6 +847,19 @@ int grow(T** p, size_t* cap, size_t need)
 
 }  // namespace
 
+#ifdef BM25_PHASE_TIMING
+extern "C" int bm25_debug_phase_read(unsigned long long* out, int reset)
+{
+    if (cudaMemcpyFromSymbol(out, g_phase, sizeof(unsigned long long) * 8) != cudaSuccess)
+        return -4;
+    if (reset) {
+        unsigned long long z[16] = {0};
+        cudaMemcpyToSymbol(g_phase, z, sizeof(z));
+    }
+    return 0;
+}
+#endif
+
 int workspace_reserve(const bm25_index* ix, bm25_workspace* ws, int32_t nq, int64_t n_tok,
                       int32_t kprime, int64_t n_tiles)
 {
@@ -801,16 +902,16 @@ void workspace_release(bm25_workspace* ws)
 
 int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_tokens,
                     const int64_t* q_off, int32_t nq, int64_t n_tok, int32_t k, int32_t* out_ids,
-                    float* out_scores, int accumulator, int32_t tile_docs, cudaStream_t s)
+                    float* out_scores, const Plan& plan, cudaStream_t s)
 {
-    (void)accumulator;
+    const int32_t tile_docs = plan.tile_docs;
     if (nq == 0)
         return BM25_OK;
     DeviceInfo di;
     BM25_TRY(device_info(&di));
     const int64_t N = ix->n_docs;
     const int32_t kprime = (int32_t)std::min<int64_t>(k, N);
-    int32_t W = tile_docs > 0 ? tile_docs : ix->plan.tile_docs;
+    int32_t W = tile_docs > 0 ? tile_docs : 16384;
     // multiples of 128 keep the shared-memory carve-up 16-byte aligned
     int64_t w_need = (N + 127) / 128 * 128;
     if (W > w_need)
@@ -846,23 +947,32 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
         BM25_LAUNCH_CHECK();
     }
     const size_t smem = tile_smem_bytes(W);
-    BM25_CUDA_TRY(cudaFuncSetAttribute(k_tile_topk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
-    int per_sm = 0;
-    BM25_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_topk,
-                                                                kTileThreads, smem));
-    if (per_sm < 1)
-        return set_error(BM25_E_INVALID, "doc tile of %d documents does not fit on an SM", W);
     const int64_t n_items = (int64_t)nq * n_tiles;
-    int g2 = (int)std::min<int64_t>(n_items, (int64_t)di.sm_count * per_sm);
-    {
-        ProfileScope ps_("k_tile_topk", s);
-        k_tile_topk<<<g2, kTileThreads, smem, s>>>(q_tokens, n_tok, q_off, nq, N, ix->indices,
-                                                   ix->data, ws->seg, W, n_tiles, kprime,
-                                                   ws->thresh, ws->tcount, ws->cand);
-    }
-    count_launch();
-    BM25_LAUNCH_CHECK();
+    auto launch_tile = [&](auto kernel, int threads) -> int {
+        BM25_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+        int per_sm = 0;
+        BM25_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads,
+                                                                    smem));
+        if (per_sm < 1)
+            return set_error(BM25_E_INVALID, "doc tile of %d documents does not fit on an SM", W);
+        const int g2 = (int)std::min<int64_t>(n_items, (int64_t)di.sm_count * per_sm);
+        {
+            ProfileScope ps_("k_tile_topk", s);
+            kernel<<<g2, threads, smem, s>>>(q_tokens, n_tok, q_off, nq, N, ix->indices, ix->data,
+                                             ws->seg, W, n_tiles, kprime, ws->thresh, ws->tcount,
+                                             ws->cand);
+        }
+        count_launch();
+        BM25_LAUNCH_CHECK();
+        return BM25_OK;
+    };
+    if (plan.threads == 128)
+        BM25_TRY(launch_tile(k_tile_topk<128>, 128));
+    else if (plan.threads == 256)
+        BM25_TRY(launch_tile(k_tile_topk<256>, 256));
+    else
+        BM25_TRY(launch_tile(k_tile_topk<512>, 512));
     int sz = 1;
     while (sz < kprime)
         sz <<= 1;

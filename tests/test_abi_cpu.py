@@ -52,4 +52,5 @@ def test_null_handles_are_rejected(lib):
     assert lib.bm25_sync_status(None, None) == -1
     lib.bm25_index_free(None)
     lib.bm25_workspace_free(None)
-    assert lib.bm25_index_set_plan(None, 0, 0) == -1
+    assert lib.bm25_index_set_plan(None, None) == -1
+    assert lib.bm25_index_get_plan(None, None) == -1

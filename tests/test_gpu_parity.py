@@ -135,13 +135,15 @@ def test_sort_spans_many_tiles_and_passes(torch_dev):
 
 # --------------------------------------------------------- retrieval -----
 
-@pytest.mark.parametrize("tile_docs", [1024, 2048, 16384])
-def test_retrieval_across_tiles(torch_dev, tile_docs):
+@pytest.mark.parametrize("tile_docs,threads", [(1024, 128), (2048, 256), (16384, 512),
+                                               (4096, 512), (49152, 256)])
+def test_retrieval_across_tiles(torch_dev, tile_docs, threads):
     """Small doc tiles force many (query, tile) items and a ragged last tile."""
     c = synth.make_corpus(9_999, 3_000, 1.1, ("poisson", 30), seed=2)
     q = synth.make_queries(64, 3_000, 1.1, ("uniform", 0, 12), seed=3)
     ix = _build(torch_dev, c, "bm25+")
-    ix.set_plan(0, tile_docs)
+    ix.set_plan(0, tile_docs, threads)
+    assert ix.get_plan() == {"accumulator": 0, "tile_docs": tile_docs, "block_threads": threads}
     orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.BM25PLUS)
     for k in (1, 7, 100, 1000):
         _check_retrieval(torch_dev, ix, orc, q, k, where=f"W={tile_docs} k={k}")
@@ -262,7 +264,8 @@ def test_workspace_and_bad_retrieve_args(torch_dev):
     orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, 0)
     ws = bm25.Workspace(ix, q.n_queries, q.tokens.shape[0], 10)
     ids, sc = ix.retrieve(_to(torch_dev, q.tokens), _to(torch_dev, q.offsets), 10, workspace=ws,
-                          accumulator=bm25.ACC_SMEM_TILED, tile_docs=1024)
+                          plan={"accumulator": bm25.ACC_SMEM_TILED, "tile_docs": 1024,
+                                "block_threads": 128})
     ix.sync_status()
     ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
     for i in range(q.n_queries):
@@ -273,5 +276,7 @@ def test_workspace_and_bad_retrieve_args(torch_dev):
             ix.retrieve(_to(torch_dev, q.tokens), _to(torch_dev, q.offsets), k)
     with pytest.raises(bm25.BM25Error):
         ix.set_plan(0, 1000)
+    with pytest.raises(bm25.BM25Error):
+        ix.set_plan(0, 0, 96)
     ws.close()
     ix.close()
