@@ -28,7 +28,6 @@ namespace {
 
 typedef unsigned long long u64;
 
-constexpr int kTileThreads = 512;
 constexpr int kTokChunk = 64;          // query tokens staged in shared memory at a time
 constexpr uint32_t kSurvCap = 1024;    // candidates kept in shared memory per item
 constexpr int kMergeThreads = 256;
@@ -190,10 +189,12 @@ __device__ void block_select(SelectState& st, uint32_t n, uint32_t k, ForEach fo
 
 // Selection over an indexable candidate set: get(i) is the key of candidate
 // i < n, and every key starts with the `skip` bytes of `common` (the bytes
-// all candidates share, so their passes are skipped).  The loops are
-// warp-uniform, so histogram updates are aggregated per warp with
-// __match_any_sync (keys sharing a prefix would otherwise serialise on one
-// counter).  With TRAIL_SYNC false the block is not synchronised after the
+// all candidates share, so their passes are skipped).  emit(key, slot) runs
+// once per selected key with distinct slots 0 .. min(k, n) - 1.  The loops
+// are warp-uniform, so histogram updates and output slots are aggregated
+// per warp (__match_any_sync / __ballot_sync): keys sharing a prefix would
+// otherwise serialise on one shared-memory counter.  st.ctr must be 0 on
+// entry.  With TRAIL_SYNC false the block is not synchronised after the
 // emit loop.
 template <bool TRAIL_SYNC, class Get, class Emit>
 __device__ void block_select_idx(SelectState& st, uint32_t n, uint32_t k, int skip, u64 common,
@@ -204,7 +205,7 @@ __device__ void block_select_idx(SelectState& st, uint32_t n, uint32_t k, int sk
     const uint32_t base0 = threadIdx.x & ~31u;
     if (n <= k) {
         for (uint32_t i = threadIdx.x; i < n; i += stride)
-            emit(get(i));
+            emit(get(i), i);
         if (TRAIL_SYNC)
             __syncthreads();
         return;
@@ -241,10 +242,23 @@ __device__ void block_select_idx(SelectState& st, uint32_t n, uint32_t k, int sk
             break;
     }
     const u64 pm = st.pmask, pf = st.prefix;
-    for (uint32_t i = threadIdx.x; i < n; i += stride) {
-        u64 key = get(i);
-        if ((key & pm) >= pf)
-            emit(key);
+    for (uint32_t b = base0; b < n; b += stride) {
+        const uint32_t i = b + lane;
+        u64 key = 0;
+        bool take = false;
+        if (i < n) {
+            key = get(i);
+            take = (key & pm) >= pf;
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, take);
+        if (bal) {
+            uint32_t base = 0;
+            if (lane == __ffs(bal) - 1)
+                base = atomicAdd(&st.ctr, (uint32_t)__popc(bal));
+            base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
+            if (take)
+                emit(key, base + __popc(bal & lanemask_lt()));
+        }
     }
     if (TRAIL_SYNC)
         __syncthreads();
@@ -264,9 +278,11 @@ __device__ __forceinline__ int common_bytes(uint32_t kmin, uint32_t kmax)
 // An accumulator holds -0.0 until its document is first touched: stored
 // scores are never -0.0, and -0.0 + x == x for every other x, so an
 // atomicAdd that returns -0.0 marks the first touch of its document, and a
-// sum never returns to -0.0.  First touches append the document to a list,
-// and the later passes (candidates, reset) walk that list; a tile touched
-// more densely than the list holds is walked in full instead.
+// sum never returns to -0.0.  Each warp lists the documents it touched first
+// and, later, those of them that clear the query's threshold, in lists of its
+// own with counts held in registers: no counter is shared between warps, so
+// no shared-memory atomic serialises them.  A list that overflows sends the
+// item down a path that walks the whole tile instead.
 #ifdef BM25_PHASE_TIMING
 // Diagnostic build only: per-phase cycle totals of k_tile_topk, summed over
 // CTAs (thread 0's view), and item statistics.
@@ -285,19 +301,24 @@ __device__ unsigned long long g_phase[16];
     } while (0)
 #endif
 constexpr uint32_t kUntouched = 0x80000000u;  // bits of -0.0f
-constexpr uint32_t kTouchCap = 1536;  // sized so that three 16K-document tiles fit on an SM
+constexpr uint32_t kTouchCap = 1536;  // all warps' touched lists (three 16K tiles per SM)
 constexpr uint32_t kRunCap = 128;     // runs of 32 postings with a cached token
+constexpr int kMaxWarps = 16;
 
 struct TileStage {
     int32_t lo[kTokChunk];
     int32_t pre[kTokChunk + 1];
-    uint8_t run_tok[kRunCap];      // token of the first posting of run r
+    uint8_t run_tok[kRunCap];             // token of the first posting of run r
     uint32_t scan[33];
-    int32_t qoff[2][2];            // token range of the current / next item, by parity
-    uint32_t n_surv, n_pos, n_touch, kmin, kmax;
-    uint32_t surv_key[kSurvCap];   // order_f32 of the candidate's score
-    uint16_t surv_doc[kSurvCap];   // its doc id within the tile
-    uint16_t touched[kTouchCap];   // doc ids (within the tile) in first-touch order
+    int32_t qoff[2][2];                   // token range of the current / next item
+    uint32_t w_touch[kMaxWarps];          // per warp: documents it touched first
+    uint32_t w_surv[kMaxWarps];           // per warp: its candidates
+    uint32_t w_pos[kMaxWarps];            // per warp: touched documents scoring > 0
+    uint32_t w_kmin[kMaxWarps], w_kmax[kMaxWarps];  // per warp: candidate score keys
+    uint32_t surv_pre[kMaxWarps + 1];     // exclusive prefix of w_surv (select path)
+    uint32_t surv_key[kSurvCap];          // per-warp slices: order_f32 of the score
+    uint16_t surv_doc[kSurvCap];          //   and the doc id within the tile
+    uint16_t touched[kTouchCap];          // per-warp slices: doc ids within the tile
 };
 
 template <int THREADS>
@@ -310,6 +331,9 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
                 u64* __restrict__ cand)
 {
     constexpr int WARPS = THREADS / 32;
+    constexpr uint32_t TPW = kTouchCap / WARPS;  // touched-list slots per warp
+    constexpr uint32_t SPW = kSurvCap / WARPS;   // candidate slots per warp
+    static_assert(WARPS <= kMaxWarps, "too many warps");
     extern __shared__ __align__(16) unsigned char smem[];
     float* acc = reinterpret_cast<float*>(smem);
     SelectState& st = *reinterpret_cast<SelectState*>(acc + W);
@@ -317,7 +341,11 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
+    const uint32_t ltmask = lanemask_lt();
     const float neg0 = __uint_as_float(kUntouched);
+    uint16_t* my_touch = ts.touched + warp * TPW;
+    uint32_t* my_skey = ts.surv_key + warp * SPW;
+    uint16_t* my_sdoc = ts.surv_doc + warp * SPW;
     for (int i = tid; i < W; i += THREADS)
         acc[i] = neg0;
 
@@ -342,16 +370,17 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
     };
     // Warp 0 runs a two-stage pipeline over the CTA's items: while item i is
     // processed it loads the segment bounds of item i+1 (lane l: tokens 2l
-    // and 2l+1 of the first chunk) from token ranges it loaded during item
-    // i-1, and the token range of item i+2.  Thread 0 also loads item i+1's
-    // threshold.  No load of the pipeline is consumed in the item it is
-    // issued in.
+    // and 2l+1 of the first chunk) from the token range it loaded during item
+    // i-1, and the (raw, unclamped) token range of item i+2.  Thread 0 also
+    // loads item i+1's threshold.  No load of the pipeline is consumed in the
+    // item it is issued in.
     int32_t tile = (int32_t)(blockIdx.x / nq), q = (int32_t)(blockIdx.x % nq);
     int32_t t1 = tile, q1 = q;
     advance(t1, q1);
     int32_t t2 = t1, q2 = q1;
     advance(t2, q2);
-    int32_t a1 = 0, b1 = 0, a2 = 0, b2 = 0;  // token ranges of items i+1, i+2 (warp 0)
+    int32_t a1 = 0, b1 = 0;                 // clamped token range of item i+1
+    int64_t ra2 = 0, rb2 = 0;               // raw token range of item i+2
     int32_t pf_lo0 = 0, pf_lo1 = 0, pf_hi0 = 0, pf_hi1 = 0;
     uint32_t pf_tau = 0;
     auto load_seg = [&](int32_t t_, int32_t a_, int32_t b_) {
@@ -380,8 +409,8 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
             b1 = max(a1, clamp_off(q_off[q1 + 1]));
         }
         if ((int64_t)blockIdx.x + 2 * (int64_t)gridDim.x < n_items) {
-            a2 = clamp_off(q_off[q2]);
-            b2 = max(a2, clamp_off(q_off[q2 + 1]));
+            ra2 = q_off[q2];
+            rb2 = q_off[q2 + 1];
         }
     }
     __syncthreads();
@@ -395,9 +424,9 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
         const int64_t d0 = (int64_t)tile * W;
         const int32_t wd = (int32_t)min((int64_t)W, n_docs - d0);
         const int32_t m0 = ts.qoff[parity][0], m1 = ts.qoff[parity][1];
-        const uint32_t my_tau = pf_tau;
-        // warp 0: advance the pipeline (segment bounds of the next item, token
-        // range of the one after), once this item's prefetched values are used
+        if (tid == 0)
+            st.tau = pf_tau;  // thread 0 holds the threshold; the others read st.tau
+        // warp 0: advance the pipeline once this item's prefetched values are used
         auto pipeline = [&]() {
             if (tid < 32) {
                 const int32_t nitem = item + (int32_t)gridDim.x;
@@ -409,13 +438,13 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
                         pf_tau = *(volatile uint32_t*)&thresh[q1];
                     }
                 }
-                a1 = a2;
-                b1 = b2;
+                a1 = clamp_off(ra2);
+                b1 = max(a1, clamp_off(rb2));
                 int32_t t3 = t2, q3 = q2;
                 advance(t3, q3);
                 if ((int64_t)nitem + 2 * (int64_t)gridDim.x < n_items) {
-                    a2 = clamp_off(q_off[q3]);
-                    b2 = max(a2, clamp_off(q_off[q3 + 1]));
+                    ra2 = q_off[q3];
+                    rb2 = q_off[q3 + 1];
                 }
                 t1 = t2;
                 q1 = q2;
@@ -423,16 +452,7 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
                 q2 = q3;
             }
         };
-        if (tid == 0) {
-            st.tau = my_tau;
-            st.ctr = 0;
-            st.minkey = ~0ull;
-            ts.n_surv = 0;
-            ts.n_pos = 0;
-            ts.n_touch = 0;
-            ts.kmin = 0xffffffffu;
-            ts.kmax = 0u;
-        }
+        uint32_t n_first = 0;  // documents this warp touched first (warp-uniform)
 
         // ---- scatter-add the item's postings, a chunk of tokens at a time ----
         for (int32_t mb = m0; mb < m1; mb += kTokChunk) {
@@ -525,15 +545,10 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
                         first = __float_as_uint(old) == kUntouched;
                     }
                     const uint32_t bal = __ballot_sync(0xffffffffu, first);
-                    if (bal) {
-                        uint32_t base = 0;
-                        if (lane == __ffs(bal) - 1)
-                            base = atomicAdd(&ts.n_touch, (uint32_t)__popc(bal));
-                        base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
-                        const uint32_t slot = base + __popc(bal & lanemask_lt());
-                        if (first && slot < kTouchCap)
-                            ts.touched[slot] = (uint16_t)d;
-                    }
+                    const uint32_t slot = n_first + __popc(bal & ltmask);
+                    if (first && slot < TPW)
+                        my_touch[slot] = (uint16_t)d;
+                    n_first += __popc(bal);
                 }
             }
             __syncthreads();
@@ -544,173 +559,213 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
             __syncthreads();
         }
 
-        // ---- candidates ------------------------------------------------------
+        // ---- candidates: each warp walks its own touched list ------------------
         // tau = the query's running threshold: some tile already holds k'
         // documents scoring at least tau, so a document below tau cannot be
         // in the top k' (documents AT tau can, through the doc-id tie rule).
         const uint32_t tau = st.tau;
         const uint32_t kp = (uint32_t)min(kprime, wd);
-        const uint32_t n_touch = ts.n_touch;
-        const bool listed = n_touch <= kTouchCap;  // else walk the whole tile
-        const uint32_t n_walk = listed ? n_touch : (uint32_t)wd;
         {
-            uint32_t pos = 0, kmin = 0xffffffffu, kmax = 0u;
-            for (uint32_t b = warp * 32; b < n_walk; b += THREADS) {  // warp-uniform
-                const uint32_t i = b + lane;
-                bool keep = false;
-                int d = 0;
-                uint32_t o = 0;
-                if (i < n_walk) {
-                    d = listed ? ts.touched[i] : (int)i;
-                    const float a = acc[d];
-                    if (__float_as_uint(a) != kUntouched) {
+            uint32_t pos = 0, kmin = 0xffffffffu, kmax = 0u, n_keep = 0;
+            const bool ok = n_first <= TPW;
+            if (lane == 0)
+                ts.w_touch[warp] = n_first;
+            if (ok) {
+                for (uint32_t b = 0; b < n_first; b += 32) {  // warp-uniform
+                    const uint32_t i = b + lane;
+                    bool keep = false;
+                    uint32_t o = 0;
+                    int d = 0;
+                    if (i < n_first) {
+                        d = my_touch[i];
+                        const float a = acc[d];
                         o = order_f32(a);
                         pos += (a > 0.0f);
                         keep = o >= tau;
                     }
-                }
-                const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-                if (bal) {
-                    uint32_t base = 0;
-                    if (lane == __ffs(bal) - 1)
-                        base = atomicAdd(&ts.n_surv, (uint32_t)__popc(bal));
-                    base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
+                    const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+                    const uint32_t slot = n_keep + __popc(bal & ltmask);
                     if (keep) {
-                        const uint32_t slot = base + __popc(bal & lanemask_lt());
-                        if (slot < kSurvCap) {
-                            ts.surv_key[slot] = o;
-                            ts.surv_doc[slot] = (uint16_t)d;
+                        if (slot < SPW) {
+                            my_skey[slot] = o;
+                            my_sdoc[slot] = (uint16_t)d;
                         }
                         kmin = min(kmin, o);
                         kmax = max(kmax, o);
                     }
+                    n_keep += __popc(bal);
                 }
             }
             pos = __reduce_add_sync(0xffffffffu, pos);
             kmin = __reduce_min_sync(0xffffffffu, kmin);
             kmax = __reduce_max_sync(0xffffffffu, kmax);
             if (lane == 0) {
-                if (pos)
-                    atomicAdd(&ts.n_pos, pos);
-                if (kmin <= kmax) {
-                    atomicMin(&ts.kmin, kmin);
-                    atomicMax(&ts.kmax, kmax);
-                }
+                ts.w_surv[warp] = n_keep;
+                ts.w_pos[warp] = pos;
+                ts.w_kmin[warp] = kmin;
+                ts.w_kmax[warp] = kmax;
             }
         }
         __syncthreads();
         BM25_PHASE(2);
+        // every warp reduces the per-warp figures itself (lane w reads warp w's)
+        uint32_t n_cand, n_pos, kmin, kmax, my_base;
+        bool listed;
+        {
+            const bool has = lane < WARPS;
+            const uint32_t t = has ? ts.w_touch[lane] : 0u;
+            const uint32_t sv = has ? ts.w_surv[lane] : 0u;
+            const uint32_t ps = has ? ts.w_pos[lane] : 0u;
+            listed = __all_sync(0xffffffffu, t <= TPW && sv <= SPW);
+            const uint32_t inc = warp_inclusive_sum(sv);
+            n_cand = __shfl_sync(0xffffffffu, inc, 31);
+            my_base = __shfl_sync(0xffffffffu, inc - sv, warp);
+            n_pos = __reduce_add_sync(0xffffffffu, ps);
+            kmin = __reduce_min_sync(0xffffffffu, has ? ts.w_kmin[lane] : 0xffffffffu);
+            kmax = __reduce_max_sync(0xffffffffu, has ? ts.w_kmax[lane] : 0u);
+        }
+        if (!listed) {  // some list overflowed: count over the whole tile
+            uint32_t c = 0, p = 0;
+            for (int d = tid; d < wd; d += THREADS) {
+                const float a = acc[d];
+                if (__float_as_uint(a) != kUntouched) {
+                    c += order_f32(a) >= tau;
+                    p += a > 0.0f;
+                }
+            }
+            uint32_t tot;
+            block_exclusive_sum(c, ts.scan, &tot);
+            n_cand = tot;
+            block_exclusive_sum(p, ts.scan, &tot);
+            n_pos = tot;
+        }
         // Untouched documents score exactly 0.  They can enter the tile's top
         // k' only if 0 clears tau and fewer than k' touched documents score
-        // above 0; then the k' lowest-id untouched ones join the candidates.
-        // (Rare: the whole tile is scanned, 32 documents per thread-step.)
-        const bool fill_on = tau <= kZeroKey && ts.n_pos < kp;
-        if (fill_on) {
-            const int32_t nwords = (wd + 31) >> 5;
-            uint32_t carry = 0;
-            for (int w0 = 0; w0 < nwords && carry < kp; w0 += THREADS) {
-                const int w = w0 + tid;
-                uint32_t zeros = 0;
-                if (w < nwords) {
-                    const int dmax = min(32, wd - (w << 5));
-                    for (int b2 = 0; b2 < dmax; b2++)
-                        if (__float_as_uint(acc[(w << 5) + b2]) == kUntouched)
-                            zeros |= 1u << b2;
-                }
-                const uint32_t z = __popc(zeros);
-                uint32_t tot;
-                const uint32_t ex = block_exclusive_sum(z, ts.scan, &tot) + carry;
-                if (w < nwords && ex < kp) {
-                    const uint32_t take = kp - ex;
-                    uint32_t fill = zeros;
-                    if (take < z) {  // keep only the lowest `take` zero bits
-                        uint32_t f = 0;
-                        for (uint32_t c = 0; c < take; c++) {
-                            const uint32_t low = fill & (0u - fill);
-                            f |= low;
-                            fill ^= low;
-                        }
-                        fill = f;
-                    }
-                    if (fill) {
-                        atomicMin(&ts.kmin, kZeroKey);
-                        atomicMax(&ts.kmax, kZeroKey);
-                    }
-                    while (fill) {
-                        const int bpos = __ffs(fill) - 1;
-                        fill &= fill - 1;
-                        const uint32_t slot = atomicAdd(&ts.n_surv, 1u);
-                        if (slot < kSurvCap) {
-                            ts.surv_key[slot] = kZeroKey;
-                            ts.surv_doc[slot] = (uint16_t)((w << 5) + bpos);
-                        }
-                    }
-                }
-                carry += tot;
-            }
-            __syncthreads();
-        }
-        BM25_PHASE(3);
+        // above 0; then the lowest-id untouched ones join the candidates.
+        const bool fill_on = tau <= kZeroKey && n_pos < kp;
 
         // ---- select and emit -------------------------------------------------
-        const uint32_t n_cand = ts.n_surv;
-        const uint32_t n_emit = n_cand < kp ? n_cand : kp;
         u64* out = cand + (int64_t)item * kprime;
-        auto emit = [&](u64 key) {
-            const uint32_t slot = atomicAdd(&st.ctr, 1u);
-            if (slot < n_emit) {
-                out[slot] = key;
-                atomicMin(&st.minkey, key);
+        uint32_t n_emit;
+        uint32_t new_tau = 0;  // thread 0: score key of the weakest emitted candidate
+        if (listed && !fill_on) {
+            n_emit = n_cand < kp ? n_cand : kp;
+            if (n_cand <= kp) {
+                // every candidate is kept: warp w writes its own at its offset
+                const uint32_t nw = ts.w_surv[warp];
+                for (uint32_t i = lane; i < nw; i += 32)
+                    out[my_base + i] = ((u64)my_skey[i] << 32) |
+                                       (u64)(~(uint32_t)(d0 + my_sdoc[i]));
+                new_tau = kmin;
+            } else {
+                if (tid < WARPS + 1) {  // candidate i lives in warp w's slice
+                    uint32_t x = 0;
+                    for (int w = 0; w < tid; w++)
+                        x += ts.w_surv[w];
+                    ts.surv_pre[tid] = x;
+                }
+                if (tid == 0)
+                    st.ctr = 0;
+                __syncthreads();
+                auto get = [&](uint32_t i) -> u64 {
+                    int a = 0, b = WARPS;  // surv_pre[a] <= i < surv_pre[b]
+                    while (b - a > 1) {
+                        const int mid = (a + b) >> 1;
+                        if (ts.surv_pre[mid] <= i)
+                            a = mid;
+                        else
+                            b = mid;
+                    }
+                    const uint32_t s = a * SPW + (i - ts.surv_pre[a]);
+                    return ((u64)ts.surv_key[s] << 32) |
+                           (u64)(~(uint32_t)(d0 + ts.surv_doc[s]));
+                };
+                block_select_idx<true>(st, n_cand, kp, common_bytes(kmin, kmax),
+                                       (u64)kmax << 32, get,
+                                       [&](u64 key, uint32_t slot) { out[slot] = key; });
+                // the selected keys are those at or above the final prefix, so
+                // its score word is a lower bound on the weakest of them
+                new_tau = (uint32_t)(st.prefix >> 32);
             }
-        };
-        if (n_emit > 0 && n_cand <= kSurvCap) {
-            const uint32_t kmin = ts.kmin, kmax = ts.kmax;
-            block_select_idx<false>(st, n_cand, kp, common_bytes(kmin, kmax), (u64)kmax << 32,
-                                    [&](uint32_t i) {
-                                        return ((u64)ts.surv_key[i] << 32) |
-                                               (u64)(~(uint32_t)(d0 + ts.surv_doc[i]));
-                                    },
-                                    emit);
-        } else if (n_emit > 0) {
-            // more candidates than the buffer holds: select straight from the
-            // accumulators.  With the fill on every untouched document is
-            // offered (score 0; -0.0 folds onto +0.0 in the key), and the
-            // lowest ids win their ties exactly as with the buffered fill.
+        } else {
+            // rare paths (a list overflowed, or untouched documents may
+            // compete): select straight from the accumulators.  With the fill
+            // on every untouched document is offered (score 0; -0.0 folds onto
+            // +0.0 in the key) and the lowest ids win their ties.
+            uint32_t n_all = n_cand;
+            if (fill_on) {
+                uint32_t c = 0;
+                for (int d = tid; d < wd; d += THREADS)
+                    c += __float_as_uint(acc[d]) == kUntouched;
+                uint32_t tot;
+                block_exclusive_sum(c, ts.scan, &tot);
+                n_all += tot;
+            }
+            n_emit = n_all < kp ? n_all : kp;
+            if (tid == 0)
+                st.ctr = 0;
+            __syncthreads();
             auto for_each = [&](auto f) {
                 for (int d = tid; d < wd; d += THREADS) {
                     const float a = acc[d];
                     const bool touched = __float_as_uint(a) != kUntouched;
-                    if ((touched || fill_on) && order_f32(a) >= tau)
+                    if (touched ? order_f32(a) >= tau : fill_on)
                         f(make_key(a, (uint32_t)(d0 + d)));
                 }
             };
-            block_select(st, fill_on ? 0xffffffffu : n_cand, kp, for_each, emit);
+            block_select(st, n_all, kp, for_each, [&](u64 key) {
+                const uint32_t slot = atomicAdd(&st.ctr, 1u);
+                if (slot < n_emit)
+                    out[slot] = key;
+            });
+            new_tau = n_all > kp ? (uint32_t)(st.prefix >> 32) : kZeroKey;
+            if (n_all <= kp) {  // everything was taken: the weakest is the minimum
+                uint32_t mn = 0xffffffffu;
+                for (int d = tid; d < wd; d += THREADS) {
+                    const float a = acc[d];
+                    const bool touched = __float_as_uint(a) != kUntouched;
+                    if (touched ? order_f32(a) >= tau : fill_on)
+                        mn = min(mn, order_f32(a));
+                }
+                mn = __reduce_min_sync(0xffffffffu, mn);
+                if (lane == 0)
+                    ts.w_kmin[warp] = mn;
+                __syncthreads();
+                if (tid == 0) {
+                    for (int w = 0; w < WARPS; w++)
+                        mn = min(mn, ts.w_kmin[w]);
+                    new_tau = mn;
+                }
+            }
+            // the accumulators are reset from the whole tile below
         }
-        BM25_PHASE(4);
+        BM25_PHASE(3);
 
         // ---- reset the touched accumulators ----------------------------------
         if (listed) {
-            for (uint32_t i = tid; i < n_touch; i += THREADS)
-                acc[ts.touched[i]] = neg0;
+            const uint32_t nt = min(n_first, TPW);
+            for (uint32_t i = lane; i < nt; i += 32)
+                acc[my_touch[i]] = neg0;
         } else {
+            __syncthreads();  // the walks above read the accumulators
             for (int i = tid; i < wd; i += THREADS)
                 acc[i] = neg0;
         }
+        if (tid == 0) {
+            tcount[item] = n_emit;
+            // a full set of k' candidates raises the query's threshold to (a
+            // lower bound on) the score of the weakest of them
+            if (n_emit == kp && kp > 0)
+                atomicMax(&thresh[q], new_tau);
+        }
         __syncthreads();
-        BM25_PHASE(5);
+        BM25_PHASE(4);
 #ifdef BM25_PHASE_TIMING
         if (tid == 0) {
-            ph_acc[6] += n_touch;
+            ph_acc[6] += n_first;
             ph_acc[7] += n_cand > kp ? 1 : 0;
         }
 #endif
-        if (tid == 0) {
-            tcount[item] = n_emit;
-            // a full set of k' candidates raises the query's threshold to the
-            // score of the weakest of them
-            if (n_emit == kp && kp > 0)
-                atomicMax(&thresh[q], (uint32_t)(st.minkey >> 32));
-        }
         advance(tile, q);
     }
 #ifdef BM25_PHASE_TIMING
@@ -784,8 +839,7 @@ __global__ void __launch_bounds__(kMergeThreads)
         }
         return cand[((int64_t)a * nq + q) * kprime + (i - pre[a])];
     };
-    block_select_idx<true>(st, total, (uint32_t)kprime, 0, 0ull, get, [&](u64 key) {
-        uint32_t slot = atomicAdd(&st.ctr, 1u);
+    block_select_idx<true>(st, total, (uint32_t)kprime, 0, 0ull, get, [&](u64 key, uint32_t slot) {
         if (slot < (uint32_t)kprime)
             sel[slot] = key;
     });
