@@ -29,7 +29,7 @@ namespace {
 typedef unsigned long long u64;
 
 constexpr int kTokChunk = 64;          // query tokens staged in shared memory at a time
-constexpr uint32_t kSurvCap = 1024;    // candidates kept in shared memory per item
+constexpr uint32_t kSurvCap = 2048;    // candidates kept in shared memory per item
 constexpr int kMergeThreads = 256;
 constexpr int kMergeBufCap = 4096;     // candidates a merge gathers into shared memory
 constexpr uint32_t kZeroKey = 0x80000000u;  // order_f32(0.0f)
@@ -144,111 +144,66 @@ __device__ __forceinline__ void select_bucket(SelectState& st, int shift)
     }
 }
 
-// Selection over candidates given by for_each(f), which must call f(key) for
-// every candidate owned by this thread (any loop shape).  emit(key) runs for
-// each of the min(k, n) selected keys.  All threads of the block call this;
-// it ends with __syncthreads().
-template <class ForEach, class Emit>
-__device__ void block_select(SelectState& st, uint32_t n, uint32_t k, ForEach for_each,
-                             Emit emit)
-{
-    if (n <= k) {
-        for_each([&](u64 key) { emit(key); });
-        __syncthreads();
-        return;
-    }
-    if (threadIdx.x == 0) {
-        st.prefix = 0;
-        st.pmask = 0;
-        st.need = k;
-    }
-    for (int pass = 0; pass < 8; pass++) {
-        const int shift = 56 - 8 * pass;
-        for (int i = threadIdx.x; i < 256; i += blockDim.x)
-            st.hist[i] = 0;
-        __syncthreads();
-        const u64 pm = st.pmask, pf = st.prefix;
-        for_each([&](u64 key) {
-            if ((key & pm) == pf)
-                atomicAdd(&st.hist[(key >> shift) & 0xff], 1u);
-        });
-        __syncthreads();
-        if (threadIdx.x < 32)
-            select_bucket(st, shift);
-        __syncthreads();
-        if (st.bucket == st.need)
-            break;
-    }
-    const u64 pm = st.pmask, pf = st.prefix;
-    for_each([&](u64 key) {
-        if ((key & pm) >= pf)
-            emit(key);
-    });
-    __syncthreads();
-}
-
-// Selection over an indexable candidate set: get(i) is the key of candidate
-// i < n, and every key starts with the `skip` bytes of `common` (the bytes
-// all candidates share, so their passes are skipped).  emit(key, slot) runs
-// once per selected key with distinct slots 0 .. min(k, n) - 1.  The loops
-// are warp-uniform, so histogram updates and output slots are aggregated
-// per warp (__match_any_sync / __ballot_sync): keys sharing a prefix would
-// otherwise serialise on one shared-memory counter.  st.ctr must be 0 on
-// entry.  With TRAIL_SYNC false the block is not synchronised after the
-// emit loop.
+// Selection over an indexable candidate set: get(i) for i < n_index is the
+// key of candidate i, or 0 where index i holds no candidate; n_real is the
+// number of non-zero keys.  Every key starts with the `skip` bytes of
+// `common` (bytes all candidates share, so their passes are skipped).
+// emit(key, slot) runs once per selected key with distinct slots
+// 0 .. min(k, n_real) - 1.  The loops are warp-uniform, so histogram updates
+// and output slots are aggregated per warp (__match_any_sync /
+// __ballot_sync): keys sharing a prefix would otherwise serialise on one
+// shared-memory counter.  st.ctr must be 0 on entry.  With TRAIL_SYNC false
+// the block is not synchronised after the emit loop.
 template <bool TRAIL_SYNC, class Get, class Emit>
-__device__ void block_select_idx(SelectState& st, uint32_t n, uint32_t k, int skip, u64 common,
-                                 Get get, Emit emit)
+__device__ void block_select_idx(SelectState& st, uint32_t n_index, uint32_t n_real, uint32_t k,
+                                 int skip, u64 common, Get get, Emit emit)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t stride = blockDim.x;
     const uint32_t base0 = threadIdx.x & ~31u;
-    if (n <= k) {
-        for (uint32_t i = threadIdx.x; i < n; i += stride)
-            emit(get(i), i);
-        if (TRAIL_SYNC)
-            __syncthreads();
-        return;
-    }
-    if (threadIdx.x == 0) {
-        const u64 pm = skip >= 8 ? ~0ull : (skip <= 0 ? 0ull : ~0ull << (64 - 8 * skip));
-        st.prefix = common & pm;
-        st.pmask = pm;
-        st.need = k;
-    }
-    for (int pass = skip; pass < 8; pass++) {
-        const int shift = 56 - 8 * pass;
-        for (int i = threadIdx.x; i < 256; i += blockDim.x)
-            st.hist[i] = 0;
-        __syncthreads();
-        const u64 pm = st.pmask, pf = st.prefix;
-        for (uint32_t b = base0; b < n; b += stride) {
-            const uint32_t i = b + lane;
-            uint32_t dg = 0xffffffffu;
-            if (i < n) {
-                u64 key = get(i);
-                if ((key & pm) == pf)
-                    dg = (uint32_t)(key >> shift) & 0xffu;
-            }
-            uint32_t peers = __match_any_sync(0xffffffffu, dg);
-            if (dg != 0xffffffffu && (peers & lanemask_lt()) == 0)
-                atomicAdd(&st.hist[dg], (uint32_t)__popc(peers));
+    u64 pm = 0, pf = 0;
+    if (n_real > k) {
+        if (threadIdx.x == 0) {
+            const u64 m0 = skip >= 8 ? ~0ull : (skip <= 0 ? 0ull : ~0ull << (64 - 8 * skip));
+            st.prefix = common & m0;
+            st.pmask = m0;
+            st.need = k;
         }
-        __syncthreads();
-        if (threadIdx.x < 32)
-            select_bucket(st, shift);
-        __syncthreads();
-        if (st.bucket == st.need)
-            break;
+        for (int pass = skip; pass < 8; pass++) {
+            const int shift = 56 - 8 * pass;
+            for (int i = threadIdx.x; i < 256; i += blockDim.x)
+                st.hist[i] = 0;
+            __syncthreads();
+            const u64 cpm = st.pmask, cpf = st.prefix;
+            for (uint32_t b = base0; b < n_index; b += stride) {
+                const uint32_t i = b + lane;
+                uint32_t dg = 0xffffffffu;
+                if (i < n_index) {
+                    const u64 key = get(i);
+                    if (key != 0ull && (key & cpm) == cpf)
+                        dg = (uint32_t)(key >> shift) & 0xffu;
+                }
+                const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+                if (dg != 0xffffffffu && (peers & lanemask_lt()) == 0)
+                    atomicAdd(&st.hist[dg], (uint32_t)__popc(peers));
+            }
+            __syncthreads();
+            if (threadIdx.x < 32)
+                select_bucket(st, shift);
+            __syncthreads();
+            if (st.bucket == st.need)
+                break;
+        }
+        pm = st.pmask;
+        pf = st.prefix;
     }
-    const u64 pm = st.pmask, pf = st.prefix;
-    for (uint32_t b = base0; b < n; b += stride) {
+    for (uint32_t b = base0; b < n_index; b += stride) {
         const uint32_t i = b + lane;
         u64 key = 0;
         bool take = false;
-        if (i < n) {
+        if (i < n_index) {
             key = get(i);
-            take = (key & pm) >= pf;
+            take = key != 0ull && (key & pm) >= pf;
         }
         const uint32_t bal = __ballot_sync(0xffffffffu, take);
         if (bal) {
@@ -316,8 +271,7 @@ struct TileStage {
     uint32_t w_pos[kMaxWarps];            // per warp: touched documents scoring > 0
     uint32_t w_kmin[kMaxWarps], w_kmax[kMaxWarps];  // per warp: candidate score keys
     uint32_t surv_pre[kMaxWarps + 1];     // exclusive prefix of w_surv (select path)
-    uint32_t surv_key[kSurvCap];          // per-warp slices: order_f32 of the score
-    uint16_t surv_doc[kSurvCap];          //   and the doc id within the tile
+    uint16_t surv_doc[kSurvCap];          // per-warp slices: candidates' doc ids in the tile
     uint16_t touched[kTouchCap];          // per-warp slices: doc ids within the tile
 };
 
@@ -344,7 +298,6 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
     const uint32_t ltmask = lanemask_lt();
     const float neg0 = __uint_as_float(kUntouched);
     uint16_t* my_touch = ts.touched + warp * TPW;
-    uint32_t* my_skey = ts.surv_key + warp * SPW;
     uint16_t* my_sdoc = ts.surv_doc + warp * SPW;
     for (int i = tid; i < W; i += THREADS)
         acc[i] = neg0;
@@ -586,10 +539,8 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
                     const uint32_t bal = __ballot_sync(0xffffffffu, keep);
                     const uint32_t slot = n_keep + __popc(bal & ltmask);
                     if (keep) {
-                        if (slot < SPW) {
-                            my_skey[slot] = o;
+                        if (slot < SPW)
                             my_sdoc[slot] = (uint16_t)d;
-                        }
                         kmin = min(kmin, o);
                         kmax = max(kmax, o);
                     }
@@ -653,9 +604,10 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
             if (n_cand <= kp) {
                 // every candidate is kept: warp w writes its own at its offset
                 const uint32_t nw = ts.w_surv[warp];
-                for (uint32_t i = lane; i < nw; i += 32)
-                    out[my_base + i] = ((u64)my_skey[i] << 32) |
-                                       (u64)(~(uint32_t)(d0 + my_sdoc[i]));
+                for (uint32_t i = lane; i < nw; i += 32) {
+                    const int d = my_sdoc[i];
+                    out[my_base + i] = make_key(acc[d], (uint32_t)(d0 + d));
+                }
                 new_tau = kmin;
             } else {
                 if (tid < WARPS + 1) {  // candidate i lives in warp w's slice
@@ -676,11 +628,10 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
                         else
                             b = mid;
                     }
-                    const uint32_t s = a * SPW + (i - ts.surv_pre[a]);
-                    return ((u64)ts.surv_key[s] << 32) |
-                           (u64)(~(uint32_t)(d0 + ts.surv_doc[s]));
+                    const int d = ts.surv_doc[a * SPW + (i - ts.surv_pre[a])];
+                    return make_key(acc[d], (uint32_t)(d0 + d));
                 };
-                block_select_idx<true>(st, n_cand, kp, common_bytes(kmin, kmax),
+                block_select_idx<true>(st, n_cand, n_cand, kp, common_bytes(kmin, kmax),
                                        (u64)kmax << 32, get,
                                        [&](u64 key, uint32_t slot) { out[slot] = key; });
                 // the selected keys are those at or above the final prefix, so
@@ -705,27 +656,22 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
             if (tid == 0)
                 st.ctr = 0;
             __syncthreads();
-            auto for_each = [&](auto f) {
-                for (int d = tid; d < wd; d += THREADS) {
-                    const float a = acc[d];
-                    const bool touched = __float_as_uint(a) != kUntouched;
-                    if (touched ? order_f32(a) >= tau : fill_on)
-                        f(make_key(a, (uint32_t)(d0 + d)));
-                }
+            auto get = [&](uint32_t d) -> u64 {
+                const float a = acc[d];
+                const bool touched = __float_as_uint(a) != kUntouched;
+                return (touched ? order_f32(a) >= tau : fill_on)
+                           ? make_key(a, (uint32_t)(d0 + d))
+                           : 0ull;
             };
-            block_select(st, n_all, kp, for_each, [&](u64 key) {
-                const uint32_t slot = atomicAdd(&st.ctr, 1u);
-                if (slot < n_emit)
-                    out[slot] = key;
-            });
+            block_select_idx<true>(st, (uint32_t)wd, n_all, kp, 0, 0ull, get,
+                                   [&](u64 key, uint32_t slot) { out[slot] = key; });
             new_tau = n_all > kp ? (uint32_t)(st.prefix >> 32) : kZeroKey;
             if (n_all <= kp) {  // everything was taken: the weakest is the minimum
                 uint32_t mn = 0xffffffffu;
                 for (int d = tid; d < wd; d += THREADS) {
-                    const float a = acc[d];
-                    const bool touched = __float_as_uint(a) != kUntouched;
-                    if (touched ? order_f32(a) >= tau : fill_on)
-                        mn = min(mn, order_f32(a));
+                    const u64 key = get(d);
+                    if (key != 0ull)
+                        mn = min(mn, (uint32_t)(key >> 32));
                 }
                 mn = __reduce_min_sync(0xffffffffu, mn);
                 if (lane == 0)
@@ -815,7 +761,7 @@ __global__ void __launch_bounds__(kMergeThreads)
     if (tid == 0)
         st.ctr = 0;
     __syncthreads();
-    const uint32_t total = pre[n_tiles];
+    const uint32_t total = pre[n_tiles];  // > 0: the tiles hold at least k' candidates
     const bool gathered = total <= (uint32_t)buf_cap;
     if (gathered) {  // one warp per tile copies its candidates
         for (int t = warp; t < n_tiles; t += kMergeThreads / 32) {
@@ -839,7 +785,8 @@ __global__ void __launch_bounds__(kMergeThreads)
         }
         return cand[((int64_t)a * nq + q) * kprime + (i - pre[a])];
     };
-    block_select_idx<true>(st, total, (uint32_t)kprime, 0, 0ull, get, [&](u64 key, uint32_t slot) {
+    block_select_idx<true>(st, total, total, (uint32_t)kprime, 0, 0ull, get,
+                           [&](u64 key, uint32_t slot) {
         if (slot < (uint32_t)kprime)
             sel[slot] = key;
     });
