@@ -29,7 +29,6 @@ namespace {
 typedef unsigned long long u64;
 
 constexpr int kTokChunk = 64;          // query tokens staged in shared memory at a time
-constexpr uint32_t kSurvCap = 2048;    // candidates kept in shared memory per item
 constexpr int kMergeThreads = 256;
 constexpr int kMergeBufCap = 4096;     // candidates a merge gathers into shared memory
 constexpr uint32_t kZeroKey = 0x80000000u;  // order_f32(0.0f)
@@ -234,10 +233,13 @@ __device__ __forceinline__ int common_bytes(uint32_t kmin, uint32_t kmax)
 // scores are never -0.0, and -0.0 + x == x for every other x, so an
 // atomicAdd that returns -0.0 marks the first touch of its document, and a
 // sum never returns to -0.0.  Each warp lists the documents it touched first
-// and, later, those of them that clear the query's threshold, in lists of its
-// own with counts held in registers: no counter is shared between warps, so
-// no shared-memory atomic serialises them.  A list that overflows sends the
-// item down a path that walks the whole tile instead.
+// in a list of its own, with the count held in a register: no counter is
+// shared between warps, so no shared-memory atomic serialises them.  When the
+// query's threshold is above 0 the warp then compacts, in place, the entries
+// that clear it (the candidates) and resets the others at once; otherwise the
+// list stays whole and the candidates are read through a mask.  A list that
+// overflows, or a tile whose untouched documents may compete, sends the item
+// down a path that walks the whole tile instead.
 #ifdef BM25_PHASE_TIMING
 // Diagnostic build only: per-phase cycle totals of k_tile_topk, summed over
 // CTAs (thread 0's view), and item statistics.
@@ -256,7 +258,7 @@ __device__ unsigned long long g_phase[16];
     } while (0)
 #endif
 constexpr uint32_t kUntouched = 0x80000000u;  // bits of -0.0f
-constexpr uint32_t kTouchCap = 1536;  // all warps' touched lists (three 16K tiles per SM)
+constexpr uint32_t kTouchCap = 4096;  // all warps' touched lists (three 16K tiles per SM)
 constexpr uint32_t kRunCap = 128;     // runs of 32 postings with a cached token
 constexpr int kMaxWarps = 16;
 
@@ -270,8 +272,7 @@ struct TileStage {
     uint32_t w_surv[kMaxWarps];           // per warp: its candidates
     uint32_t w_pos[kMaxWarps];            // per warp: touched documents scoring > 0
     uint32_t w_kmin[kMaxWarps], w_kmax[kMaxWarps];  // per warp: candidate score keys
-    uint32_t surv_pre[kMaxWarps + 1];     // exclusive prefix of w_surv (select path)
-    uint16_t surv_doc[kSurvCap];          // per-warp slices: candidates' doc ids in the tile
+    uint32_t list_pre[kMaxWarps + 1];     // exclusive prefix of the lists read by a select
     uint16_t touched[kTouchCap];          // per-warp slices: doc ids within the tile
 };
 
@@ -286,7 +287,6 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
 {
     constexpr int WARPS = THREADS / 32;
     constexpr uint32_t TPW = kTouchCap / WARPS;  // touched-list slots per warp
-    constexpr uint32_t SPW = kSurvCap / WARPS;   // candidate slots per warp
     static_assert(WARPS <= kMaxWarps, "too many warps");
     extern __shared__ __align__(16) unsigned char smem[];
     float* acc = reinterpret_cast<float*>(smem);
@@ -298,7 +298,6 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
     const uint32_t ltmask = lanemask_lt();
     const float neg0 = __uint_as_float(kUntouched);
     uint16_t* my_touch = ts.touched + warp * TPW;
-    uint16_t* my_sdoc = ts.surv_doc + warp * SPW;
     for (int i = tid; i < W; i += THREADS)
         acc[i] = neg0;
 
@@ -518,12 +517,12 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
         // in the top k' (documents AT tau can, through the doc-id tie rule).
         const uint32_t tau = st.tau;
         const uint32_t kp = (uint32_t)min(kprime, wd);
+        const bool compact = tau > kZeroKey;  // then no untouched document can compete
         {
             uint32_t pos = 0, kmin = 0xffffffffu, kmax = 0u, n_keep = 0;
-            const bool ok = n_first <= TPW;
             if (lane == 0)
                 ts.w_touch[warp] = n_first;
-            if (ok) {
+            if (n_first <= TPW) {
                 for (uint32_t b = 0; b < n_first; b += 32) {  // warp-uniform
                     const uint32_t i = b + lane;
                     bool keep = false;
@@ -535,12 +534,14 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
                         o = order_f32(a);
                         pos += (a > 0.0f);
                         keep = o >= tau;
+                        if (compact && !keep)
+                            acc[d] = neg0;  // below the threshold: done with it
                     }
                     const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-                    const uint32_t slot = n_keep + __popc(bal & ltmask);
                     if (keep) {
-                        if (slot < SPW)
-                            my_sdoc[slot] = (uint16_t)d;
+                        // slot <= i: the entry being overwritten was already read
+                        if (compact)
+                            my_touch[n_keep + __popc(bal & ltmask)] = (uint16_t)d;
                         kmin = min(kmin, o);
                         kmax = max(kmax, o);
                     }
@@ -556,24 +557,31 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
                 ts.w_kmin[warp] = kmin;
                 ts.w_kmax[warp] = kmax;
             }
+            if (compact)
+                n_first = n_keep;  // the list now holds the candidates only
         }
         __syncthreads();
         BM25_PHASE(2);
         // every warp reduces the per-warp figures itself (lane w reads warp w's)
-        uint32_t n_cand, n_pos, kmin, kmax, my_base;
+        uint32_t n_cand, n_pos, kmin, kmax, my_base, n_list;
         bool listed;
         {
             const bool has = lane < WARPS;
             const uint32_t t = has ? ts.w_touch[lane] : 0u;
             const uint32_t sv = has ? ts.w_surv[lane] : 0u;
             const uint32_t ps = has ? ts.w_pos[lane] : 0u;
-            listed = __all_sync(0xffffffffu, t <= TPW && sv <= SPW);
-            const uint32_t inc = warp_inclusive_sum(sv);
-            n_cand = __shfl_sync(0xffffffffu, inc, 31);
-            my_base = __shfl_sync(0xffffffffu, inc - sv, warp);
+            listed = __all_sync(0xffffffffu, t <= TPW);
+            const uint32_t len = compact ? sv : t;  // entries each list now holds
+            const uint32_t inc = warp_inclusive_sum(len);
+            n_list = __shfl_sync(0xffffffffu, inc, 31);
+            my_base = __shfl_sync(0xffffffffu, inc - len, warp);
+            n_cand = __reduce_add_sync(0xffffffffu, sv);
             n_pos = __reduce_add_sync(0xffffffffu, ps);
             kmin = __reduce_min_sync(0xffffffffu, has ? ts.w_kmin[lane] : 0xffffffffu);
             kmax = __reduce_max_sync(0xffffffffu, has ? ts.w_kmax[lane] : 0u);
+            const uint32_t pre_l = inc - len;  // lane w: exclusive prefix up to warp w
+            if (warp == 0 && lane <= WARPS)
+                ts.list_pre[lane] = pre_l;
         }
         if (!listed) {  // some list overflowed: count over the whole tile
             uint32_t c = 0, p = 0;
@@ -593,50 +601,45 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
         // Untouched documents score exactly 0.  They can enter the tile's top
         // k' only if 0 clears tau and fewer than k' touched documents score
         // above 0; then the lowest-id untouched ones join the candidates.
-        const bool fill_on = tau <= kZeroKey && n_pos < kp;
+        const bool fill_on = !compact && n_pos < kp;
 
         // ---- select and emit -------------------------------------------------
         u64* out = cand + (int64_t)item * kprime;
         uint32_t n_emit;
-        uint32_t new_tau = 0;  // thread 0: score key of the weakest emitted candidate
+        uint32_t new_tau = 0;  // score key of (a lower bound on) the weakest emitted
         if (listed && !fill_on) {
             n_emit = n_cand < kp ? n_cand : kp;
-            if (n_cand <= kp) {
+            if (n_cand <= kp && compact) {
                 // every candidate is kept: warp w writes its own at its offset
-                const uint32_t nw = ts.w_surv[warp];
-                for (uint32_t i = lane; i < nw; i += 32) {
-                    const int d = my_sdoc[i];
+                for (uint32_t i = lane; i < n_first; i += 32) {
+                    const int d = my_touch[i];
                     out[my_base + i] = make_key(acc[d], (uint32_t)(d0 + d));
                 }
                 new_tau = kmin;
             } else {
-                if (tid < WARPS + 1) {  // candidate i lives in warp w's slice
-                    uint32_t x = 0;
-                    for (int w = 0; w < tid; w++)
-                        x += ts.w_surv[w];
-                    ts.surv_pre[tid] = x;
-                }
                 if (tid == 0)
                     st.ctr = 0;
                 __syncthreads();
+                // index i lives in warp w's list at i - list_pre[w]
                 auto get = [&](uint32_t i) -> u64 {
-                    int a = 0, b = WARPS;  // surv_pre[a] <= i < surv_pre[b]
+                    int a = 0, b = WARPS;  // list_pre[a] <= i < list_pre[b]
                     while (b - a > 1) {
                         const int mid = (a + b) >> 1;
-                        if (ts.surv_pre[mid] <= i)
+                        if (ts.list_pre[mid] <= i)
                             a = mid;
                         else
                             b = mid;
                     }
-                    const int d = ts.surv_doc[a * SPW + (i - ts.surv_pre[a])];
-                    return make_key(acc[d], (uint32_t)(d0 + d));
+                    const int d = ts.touched[a * TPW + (i - ts.list_pre[a])];
+                    const float v = acc[d];
+                    return order_f32(v) >= tau ? make_key(v, (uint32_t)(d0 + d)) : 0ull;
                 };
-                block_select_idx<true>(st, n_cand, n_cand, kp, common_bytes(kmin, kmax),
+                block_select_idx<true>(st, n_list, n_cand, kp, common_bytes(kmin, kmax),
                                        (u64)kmax << 32, get,
                                        [&](u64 key, uint32_t slot) { out[slot] = key; });
                 // the selected keys are those at or above the final prefix, so
                 // its score word is a lower bound on the weakest of them
-                new_tau = (uint32_t)(st.prefix >> 32);
+                new_tau = n_cand > kp ? (uint32_t)(st.prefix >> 32) : kmin;
             }
         } else {
             // rare paths (a list overflowed, or untouched documents may
@@ -688,9 +691,8 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
         BM25_PHASE(3);
 
         // ---- reset the touched accumulators ----------------------------------
-        if (listed) {
-            const uint32_t nt = min(n_first, TPW);
-            for (uint32_t i = lane; i < nt; i += 32)
+        if (listed && !fill_on) {
+            for (uint32_t i = lane; i < n_first; i += 32)  // the whole list, or the candidates
                 acc[my_touch[i]] = neg0;
         } else {
             __syncthreads();  // the walks above read the accumulators
