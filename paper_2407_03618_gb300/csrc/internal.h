@@ -66,7 +66,7 @@ int device_info(DeviceInfo* out);
 struct Plan {
     int accumulator = BM25_ACC_AUTO;
     int32_t tile_docs = 16384;
-    int32_t threads = 512;
+    int32_t threads = 256;
 };
 // Fills zero fields of `in` from `base`; BM25_E_INVALID (nothing changed) if
 // a field is out of range.

@@ -19,6 +19,7 @@
 //                     re-keyed on the final score, sorted, written out
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 
 #include "device.cuh"
 #include "internal.h"
@@ -277,7 +278,7 @@ struct TileStage {
 };
 
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, 1536 / THREADS)
+__global__ void __launch_bounds__(THREADS, 3)  // three 16K-document tiles per SM
     k_tile_topk(const int32_t* __restrict__ q_tokens, int64_t n_tok,
                 const int64_t* __restrict__ q_off, int32_t nq, int64_t n_docs,
                 const int32_t* __restrict__ indices, const float* __restrict__ data,
@@ -710,7 +711,8 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS)
         BM25_PHASE(4);
 #ifdef BM25_PHASE_TIMING
         if (tid == 0) {
-            ph_acc[6] += n_first;
+            ph_acc[5] += compact ? 1 : 0;
+            ph_acc[6] += (!listed || fill_on) ? 1 : 0;
             ph_acc[7] += n_cand > kp ? 1 : 0;
         }
 #endif
@@ -959,6 +961,10 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
                                                                     smem));
         if (per_sm < 1)
             return set_error(BM25_E_INVALID, "doc tile of %d documents does not fit on an SM", W);
+#ifdef BM25_PHASE_TIMING
+        if (const char* e = getenv("BM25_CTAS_PER_SM"))
+            per_sm = std::min(per_sm, atoi(e));
+#endif
         const int g2 = (int)std::min<int64_t>(n_items, (int64_t)di.sm_count * per_sm);
         {
             ProfileScope ps_("k_tile_topk", s);
