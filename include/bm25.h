@@ -206,6 +206,28 @@ int bm25_retrieve_ws(const bm25_index* index, bm25_workspace* ws,
                      int32_t* out_ids, float* out_scores, const bm25_plan* plan,
                      void* cuda_stream);
 
+/* Retrieval that allocates nothing, for callers that cannot call cudaMalloc
+ * at this point: code running where a device allocation would synchronise
+ * the device or is not allowed (a host callback, a real-time serving loop
+ * with a fixed memory budget, a process whose device memory is owned by
+ * another allocator).  The paper has no counterpart; it is an operational
+ * variant of bm25_retrieve (same arguments, same results up to the order of
+ * FP32 additions).
+ *
+ * Its scratch is one file-scope device array of 16 MiB that every GPU
+ * loading the library holds until the process exits.  A batch whose scratch
+ * (8 bytes per query, 4 per query, 4 per query token and doc-tile boundary,
+ * 4 per query and doc tile, 8 per query, doc tile and k' candidate slot)
+ * exceeds 16 MiB fails with BM25_E_INVALID; split it.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture.  Every call shares the
+ * array: calls that overlap on the GPU (other streams, other threads) race
+ * and must be serialised by the caller. */
+int bm25_retrieve_noalloc(const bm25_index* index, const int32_t* query_tokens,
+                          int64_t n_query_tokens, const int64_t* query_offsets,
+                          int32_t n_queries, int32_t k, int32_t* out_ids,
+                          float* out_scores, void* cuda_stream);
+
 /* Sets / reads the index's default plan (HOST pointers).  Zero fields of a
  * plan being set keep the current values; an invalid field fails with
  * BM25_E_INVALID and changes nothing. */

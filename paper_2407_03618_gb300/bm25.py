@@ -74,6 +74,7 @@ def load(path: str | None = None):
         "bm25_index_free": (None, [P]),
         "bm25_retrieve": (cint, [P, P, i64, P, i32, i32, P, P, P]),
         "bm25_retrieve_host": (cint, [P, P, P, i32, i32, P, P, P]),
+        "bm25_retrieve_noalloc": (cint, [P, P, i64, P, i32, i32, P, P, P]),
         "bm25_workspace_create": (cint, [P, i32, i64, i32, PP]),
         "bm25_workspace_free": (None, [P]),
         "bm25_retrieve_ws": (cint, [P, P, P, i64, P, i32, i32, P, P, P, P]),

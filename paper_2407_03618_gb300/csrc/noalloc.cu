@@ -1,0 +1,135 @@
+// Retrieval for callers that cannot allocate device memory.
+//
+// bm25_retrieve keeps its scratch in a workspace that grows with cudaMalloc
+// on demand.  Some callers cannot allow that: code running where an
+// allocation would synchronise the device or is forbidden outright (inside a
+// host callback or a real-time serving loop with a fixed memory budget,
+// under an allocator that owns all device memory, or in a process that has
+// no right to grow its footprint).  bm25_retrieve_noalloc runs the same
+// kernels with their scratch carved from one file-scope device array of
+// kScratchBytes, so a call allocates nothing.  Every GPU that loads this
+// library holds that array for the life of the process.
+//
+// The array is shared by every call: calls that overlap on the GPU (on
+// different streams, or from different threads) race on it and must be
+// serialised by the caller.  The kernels write every scratch word they read
+// within a call (the per-query threshold is reset by the first kernel), so
+// the previous call's contents never leak into a result.
+#include <cstring>
+#include <mutex>
+
+#include "internal.h"
+
+namespace bm25 {
+namespace {
+
+constexpr size_t kScratchBytes = size_t(16) << 20;  // 16 MiB
+constexpr size_t kAlign = 256;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+std::mutex g_mu;
+void* g_dev_ptr[64] = {};  // the array's device address, per device
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Device address of the array on the current device.  cudaGetSymbolAddress
+// returns it once the module is loaded on that device; the host-side symbol
+// itself is not a device address and must never reach a kernel.
+int scratch_ptr(int dev, void** out)
+{
+    if (dev < 0 || dev >= 64)
+        return set_error(BM25_E_CUDA, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!g_dev_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return set_error(BM25_E_CUDA, "cudaGetSymbolAddress of the scratch array failed: %s",
+                             cudaGetErrorString(e));
+        g_dev_ptr[dev] = p;
+    }
+    *out = g_dev_ptr[dev];
+    return BM25_OK;
+}
+
+}  // namespace
+}  // namespace bm25
+
+using namespace bm25;
+
+extern "C" int bm25_retrieve_noalloc(const bm25_index* ix, const int32_t* query_tokens,
+                                     int64_t n_query_tokens, const int64_t* query_offsets,
+                                     int32_t n_queries, int32_t k, int32_t* out_ids,
+                                     float* out_scores, void* cuda_stream)
+{
+    clear_error();
+    if (!ix)
+        return set_error(BM25_E_INVALID, "index is NULL");
+    if (n_queries < 0 || n_query_tokens < 0 || n_query_tokens > (int64_t)INT32_MAX)
+        return set_error(BM25_E_INVALID, "bad batch size (n_queries %d, n_query_tokens %lld)",
+                         n_queries, (long long)n_query_tokens);
+    if (k < 1)
+        return set_error(BM25_E_INVALID, "k = %d must be >= 1", k);
+    const int64_t N = ix->n_docs;
+    const int64_t kp = k < N ? k : N;
+    if (kp > BM25_MAX_K)
+        return set_error(BM25_E_INVALID, "min(k, n_docs) = %lld exceeds BM25_MAX_K = %d",
+                         (long long)kp, BM25_MAX_K);
+    int dev = 0;
+    BM25_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != ix->device)
+        return set_error(BM25_E_INVALID, "current device %d is not the index's device %d", dev,
+                         ix->device);
+    if (n_queries == 0)
+        return BM25_OK;
+
+    Plan plan;
+    {
+        std::lock_guard<std::mutex> g(const_cast<bm25_index*>(ix)->mu);
+        plan = ix->plan;
+    }
+    // the doc-tile geometry retrieve_device derives from the plan
+    int64_t W = plan.tile_docs > 0 ? plan.tile_docs : 16384;
+    const int64_t w_need = (N + 127) / 128 * 128;
+    if (W > w_need)
+        W = w_need;
+    const int64_t n_tiles = (N + W - 1) / W;
+
+    const size_t b_shift = align_up(sizeof(double) * (size_t)n_queries);
+    const size_t b_thresh = align_up(sizeof(uint32_t) * (size_t)n_queries);
+    const size_t b_seg = align_up(sizeof(int32_t) * (size_t)n_query_tokens * (size_t)(n_tiles + 1));
+    const size_t b_tcount = align_up(sizeof(uint32_t) * (size_t)n_queries * (size_t)n_tiles);
+    const size_t b_cand =
+        align_up(sizeof(unsigned long long) * (size_t)n_queries * (size_t)n_tiles * (size_t)kp);
+    const size_t need = b_shift + b_thresh + b_seg + b_tcount + b_cand;
+    if (need > kScratchBytes)
+        return set_error(BM25_E_INVALID,
+                         "this batch needs %zu bytes of scratch; bm25_retrieve_noalloc holds %zu "
+                         "(use fewer queries, tokens or a smaller k per call, or bm25_retrieve)",
+                         need, kScratchBytes);
+
+    void* base = nullptr;
+    BM25_TRY(scratch_ptr(dev, &base));
+    unsigned char* p = static_cast<unsigned char*>(base);
+    // A workspace whose buffers are slices of the array and whose capacities
+    // match this call exactly, so retrieve_device finds nothing to grow.
+    bm25_workspace ws;
+    ws.device = dev;
+    ws.shift = reinterpret_cast<double*>(p);
+    ws.thresh = reinterpret_cast<uint32_t*>(p + b_shift);
+    ws.max_queries = n_queries;
+    ws.seg = reinterpret_cast<int32_t*>(p + b_shift + b_thresh);
+    ws.seg_cap = (size_t)n_query_tokens * (size_t)(n_tiles + 1);
+    ws.tcount = reinterpret_cast<uint32_t*>(p + b_shift + b_thresh + b_seg);
+    ws.tcount_cap = (size_t)n_queries * (size_t)n_tiles;
+    ws.cand = reinterpret_cast<unsigned long long*>(p + b_shift + b_thresh + b_seg + b_tcount);
+    ws.cand_cap = (size_t)n_queries * (size_t)n_tiles * (size_t)kp;
+    if (ws.seg_cap == 0)
+        ws.seg_cap = 1;  // an empty batch of tokens still passes a non-null buffer
+    ws.owns_staging = false;
+    int rc = retrieve_device(ix, &ws, query_tokens, query_offsets, n_queries, n_query_tokens, k,
+                             out_ids, out_scores, plan, (cudaStream_t)cuda_stream);
+    // the slices belong to the array: nothing is released
+    return rc;
+}
