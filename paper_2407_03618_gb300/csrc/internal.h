@@ -65,7 +65,7 @@ int device_info(DeviceInfo* out);
 // ---- the index --------------------------------------------------------
 struct Plan {
     int accumulator = BM25_ACC_AUTO;
-    int32_t tile_docs = 16384;
+    int32_t tile_docs = 12288;
     int32_t threads = 256;
 };
 // Fills zero fields of `in` from `base`; BM25_E_INVALID (nothing changed) if

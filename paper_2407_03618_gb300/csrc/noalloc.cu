@@ -90,7 +90,7 @@ extern "C" int bm25_retrieve_noalloc(const bm25_index* ix, const int32_t* query_
         plan = ix->plan;
     }
     // the doc-tile geometry retrieve_device derives from the plan
-    int64_t W = plan.tile_docs > 0 ? plan.tile_docs : 16384;
+    int64_t W = plan.tile_docs > 0 ? plan.tile_docs : 12288;
     const int64_t w_need = (N + 127) / 128 * 128;
     if (W > w_need)
         W = w_need;

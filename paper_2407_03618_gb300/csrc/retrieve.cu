@@ -228,19 +228,25 @@ __device__ __forceinline__ int common_bytes(uint32_t kmin, uint32_t kmax)
 }
 
 // ---- R2 -----------------------------------------------------------------------
-// Dynamic shared memory: acc[W] FP32 | SelectState | TileStage.
+// Dynamic shared memory: acc[W] FP32 | SelectState | TileStage |
+// surv_val[WARPS * SPW] FP32 | surv_doc[WARPS * SPW] (doc id within the tile).
 //
-// An accumulator holds -0.0 until its document is first touched: stored
-// scores are never -0.0, and -0.0 + x == x for every other x, so an
-// atomicAdd that returns -0.0 marks the first touch of its document, and a
-// sum never returns to -0.0.  Each warp lists the documents it touched first
-// in a list of its own, with the count held in a register: no counter is
-// shared between warps, so no shared-memory atomic serialises them.  When the
-// query's threshold is above 0 the warp then compacts, in place, the entries
-// that clear it (the candidates) and resets the others at once; otherwise the
-// list stays whole and the candidates are read through a mask.  A list that
-// overflows, or a tile whose untouched documents may compete, sends the item
-// down a path that walks the whole tile instead.
+// An accumulator holds -0.0 until a posting lands on it (stored scores are
+// never -0.0 and -0.0 + x == x, so a touched accumulator is never -0.0).
+// Postings are added with fire-and-forget shared-memory reductions.  In the
+// common case an item's postings fit in one round of U per thread, and each
+// thread keeps the doc ids of its postings in registers; after the barrier
+// it claims each of those documents with an atomic exchange that returns the
+// document's sum and leaves a mark behind: the first claimer of a document
+// gets its score, later claimers (the document appeared in several columns)
+// see the mark.  With the query's threshold above 0 the mark is -0.0, so the
+// claim also resets the accumulator for the next item; otherwise (untouched
+// documents may compete) the mark is a NaN pattern, which keeps touched and
+// untouched documents apart until the tile is done.  Documents that clear
+// the threshold go, with their score, to a list of the claiming warp, sized
+// to the postings the warp owns (no overflow, no shared counters).  Items
+// with more postings than one round, or more tokens than one chunk, take a
+// path that walks the whole tile.
 #ifdef BM25_PHASE_TIMING
 // Diagnostic build only: per-phase cycle totals of k_tile_topk, summed over
 // CTAs (thread 0's view), and item statistics.
@@ -259,9 +265,10 @@ __device__ unsigned long long g_phase[16];
     } while (0)
 #endif
 constexpr uint32_t kUntouched = 0x80000000u;  // bits of -0.0f
-constexpr uint32_t kTouchCap = 4096;  // all warps' touched lists (three 16K tiles per SM)
-constexpr uint32_t kRunCap = 128;     // runs of 32 postings with a cached token
+constexpr uint32_t kMarked = 0x7fffffffu;     // a NaN: claimed while untouched ones still count
+constexpr uint32_t kRunCap = 128;             // runs of 32 postings with a cached token
 constexpr int kMaxWarps = 16;
+constexpr int kPostU = 8;                     // postings per thread in one round
 
 struct TileStage {
     int32_t lo[kTokChunk];
@@ -269,16 +276,20 @@ struct TileStage {
     uint8_t run_tok[kRunCap];             // token of the first posting of run r
     uint32_t scan[33];
     int32_t qoff[2][2];                   // token range of the current / next item
-    uint32_t w_touch[kMaxWarps];          // per warp: documents it touched first
     uint32_t w_surv[kMaxWarps];           // per warp: its candidates
-    uint32_t w_pos[kMaxWarps];            // per warp: touched documents scoring > 0
+    uint32_t w_pos[kMaxWarps];            // per warp: claimed documents scoring > 0
     uint32_t w_kmin[kMaxWarps], w_kmax[kMaxWarps];  // per warp: candidate score keys
-    uint32_t list_pre[kMaxWarps + 1];     // exclusive prefix of the lists read by a select
-    uint16_t touched[kTouchCap];          // per-warp slices: doc ids within the tile
+    uint32_t list_pre[kMaxWarps + 1];     // exclusive prefix of the candidate lists
 };
 
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, 3)  // three 16K-document tiles per SM
+constexpr size_t tile_lists_bytes()
+{
+    return (size_t)(THREADS / 32) * (kPostU * 32) * (sizeof(float) + sizeof(uint16_t));
+}
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per SM
     k_tile_topk(const int32_t* __restrict__ q_tokens, int64_t n_tok,
                 const int64_t* __restrict__ q_off, int32_t nq, int64_t n_docs,
                 const int32_t* __restrict__ indices, const float* __restrict__ data,
@@ -287,18 +298,22 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 16K-document tiles per S
                 u64* __restrict__ cand)
 {
     constexpr int WARPS = THREADS / 32;
-    constexpr uint32_t TPW = kTouchCap / WARPS;  // touched-list slots per warp
+    constexpr int U = kPostU;
+    constexpr uint32_t SPW = U * 32;  // candidates a warp can claim in one round
     static_assert(WARPS <= kMaxWarps, "too many warps");
     extern __shared__ __align__(16) unsigned char smem[];
     float* acc = reinterpret_cast<float*>(smem);
     SelectState& st = *reinterpret_cast<SelectState*>(acc + W);
     TileStage& ts = *reinterpret_cast<TileStage*>(&st + 1);
+    float* surv_val = reinterpret_cast<float*>(&ts + 1);
+    uint16_t* surv_doc = reinterpret_cast<uint16_t*>(surv_val + WARPS * SPW);
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const uint32_t ltmask = lanemask_lt();
     const float neg0 = __uint_as_float(kUntouched);
-    uint16_t* my_touch = ts.touched + warp * TPW;
+    float* my_sval = surv_val + warp * SPW;
+    uint16_t* my_sdoc = surv_doc + warp * SPW;
     for (int i = tid; i < W; i += THREADS)
         acc[i] = neg0;
 
@@ -377,8 +392,6 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 16K-document tiles per S
         const int64_t d0 = (int64_t)tile * W;
         const int32_t wd = (int32_t)min((int64_t)W, n_docs - d0);
         const int32_t m0 = ts.qoff[parity][0], m1 = ts.qoff[parity][1];
-        if (tid == 0)
-            st.tau = pf_tau;  // thread 0 holds the threshold; the others read st.tau
         // warp 0: advance the pipeline once this item's prefetched values are used
         auto pipeline = [&]() {
             if (tid < 32) {
@@ -405,7 +418,13 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 16K-document tiles per S
                 q2 = q3;
             }
         };
-        uint32_t n_first = 0;  // documents this warp touched first (warp-uniform)
+        if (tid == 0)
+            st.tau = pf_tau;  // thread 0 holds the threshold; the others read st.tau
+        int32_t dd[U];        // doc ids (within the tile) of this thread's postings
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            dd[u] = -1;
+        bool one_round = true;  // one chunk of tokens, one round of postings (uniform)
 
         // ---- scatter-add the item's postings, a chunk of tokens at a time ----
         for (int32_t mb = m0; mb < m1; mb += kTokChunk) {
@@ -456,11 +475,11 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 16K-document tiles per S
             __syncthreads();
             BM25_PHASE(0);
             const int32_t total = ts.pre[kTokChunk];
+            if (mb != m0 || total > U * THREADS)
+                one_round = false;
             // Warp w takes runs of 32 consecutive postings; each lane starts
             // from its run's first token and steps over finished segments.
-            constexpr int U = 4;  // runs in flight per warp
             for (int32_t r0 = warp; r0 * 32 < total; r0 += U * WARPS) {
-                int32_t dd[U];
                 float vv[U];
 #pragma unroll
                 for (int u = 0; u < U; u++) {
@@ -491,17 +510,10 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 16K-document tiles per S
                 }
 #pragma unroll
                 for (int u = 0; u < U; u++) {
-                    const int32_t d = dd[u];
-                    bool first = false;
-                    if ((uint32_t)d < (uint32_t)wd) {  // holds for any well-formed index
-                        const float old = atomicAdd(&acc[d], vv[u]);
-                        first = __float_as_uint(old) == kUntouched;
-                    }
-                    const uint32_t bal = __ballot_sync(0xffffffffu, first);
-                    const uint32_t slot = n_first + __popc(bal & ltmask);
-                    if (first && slot < TPW)
-                        my_touch[slot] = (uint16_t)d;
-                    n_first += __popc(bal);
+                    if ((uint32_t)dd[u] < (uint32_t)wd)  // holds for any well-formed index
+                        atomicAdd(&acc[dd[u]], vv[u]);   // result unused: a reduction
+                    else
+                        dd[u] = -1;
                 }
             }
             __syncthreads();
@@ -512,42 +524,46 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 16K-document tiles per S
             __syncthreads();
         }
 
-        // ---- candidates: each warp walks its own touched list ------------------
         // tau = the query's running threshold: some tile already holds k'
         // documents scoring at least tau, so a document below tau cannot be
         // in the top k' (documents AT tau can, through the doc-id tie rule).
         const uint32_t tau = st.tau;
         const uint32_t kp = (uint32_t)min(kprime, wd);
-        const bool compact = tau > kZeroKey;  // then no untouched document can compete
-        {
+        // Untouched documents score exactly 0: they can matter only if 0
+        // clears tau (and then only if fewer than k' touched ones score > 0).
+        const bool zero_counts = tau <= kZeroKey;
+        u64* out = cand + (int64_t)item * kprime;
+        uint32_t n_emit = 0;
+        uint32_t new_tau = 0;  // score key of (a lower bound on) the weakest emitted
+        bool tau_ok = false;   // new_tau is a valid bound to publish
+
+        if (one_round) {
+            // ---- claim each posting's document once; keep the candidates ---------
+            const uint32_t mark = zero_counts ? kMarked : kUntouched;
             uint32_t pos = 0, kmin = 0xffffffffu, kmax = 0u, n_keep = 0;
-            if (lane == 0)
-                ts.w_touch[warp] = n_first;
-            if (n_first <= TPW) {
-                for (uint32_t b = 0; b < n_first; b += 32) {  // warp-uniform
-                    const uint32_t i = b + lane;
-                    bool keep = false;
-                    uint32_t o = 0;
-                    int d = 0;
-                    if (i < n_first) {
-                        d = my_touch[i];
-                        const float a = acc[d];
-                        o = order_f32(a);
-                        pos += (a > 0.0f);
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                bool keep = false;
+                float v = 0.0f;
+                uint32_t o = 0;
+                if (dd[u] >= 0) {
+                    v = atomicExch(&acc[dd[u]], __uint_as_float(mark));
+                    const uint32_t vb = __float_as_uint(v);
+                    if (vb != kUntouched && vb != kMarked) {  // the first claim
+                        o = order_f32(v);
+                        pos += (v > 0.0f);
                         keep = o >= tau;
-                        if (compact && !keep)
-                            acc[d] = neg0;  // below the threshold: done with it
                     }
-                    const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-                    if (keep) {
-                        // slot <= i: the entry being overwritten was already read
-                        if (compact)
-                            my_touch[n_keep + __popc(bal & ltmask)] = (uint16_t)d;
-                        kmin = min(kmin, o);
-                        kmax = max(kmax, o);
-                    }
-                    n_keep += __popc(bal);
                 }
+                const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const uint32_t slot = n_keep + __popc(bal & ltmask);  // < SPW
+                    my_sval[slot] = v;
+                    my_sdoc[slot] = (uint16_t)dd[u];
+                    kmin = min(kmin, o);
+                    kmax = max(kmax, o);
+                }
+                n_keep += __popc(bal);
             }
             pos = __reduce_add_sync(0xffffffffu, pos);
             kmin = __reduce_min_sync(0xffffffffu, kmin);
@@ -558,33 +574,97 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 16K-document tiles per S
                 ts.w_kmin[warp] = kmin;
                 ts.w_kmax[warp] = kmax;
             }
-            if (compact)
-                n_first = n_keep;  // the list now holds the candidates only
-        }
-        __syncthreads();
-        BM25_PHASE(2);
-        // every warp reduces the per-warp figures itself (lane w reads warp w's)
-        uint32_t n_cand, n_pos, kmin, kmax, my_base, n_list;
-        bool listed;
-        {
-            const bool has = lane < WARPS;
-            const uint32_t t = has ? ts.w_touch[lane] : 0u;
-            const uint32_t sv = has ? ts.w_surv[lane] : 0u;
-            const uint32_t ps = has ? ts.w_pos[lane] : 0u;
-            listed = __all_sync(0xffffffffu, t <= TPW);
-            const uint32_t len = compact ? sv : t;  // entries each list now holds
-            const uint32_t inc = warp_inclusive_sum(len);
-            n_list = __shfl_sync(0xffffffffu, inc, 31);
-            my_base = __shfl_sync(0xffffffffu, inc - len, warp);
-            n_cand = __reduce_add_sync(0xffffffffu, sv);
-            n_pos = __reduce_add_sync(0xffffffffu, ps);
-            kmin = __reduce_min_sync(0xffffffffu, has ? ts.w_kmin[lane] : 0xffffffffu);
-            kmax = __reduce_max_sync(0xffffffffu, has ? ts.w_kmax[lane] : 0u);
-            const uint32_t pre_l = inc - len;  // lane w: exclusive prefix up to warp w
-            if (warp == 0 && lane <= WARPS)
-                ts.list_pre[lane] = pre_l;
-        }
-        if (!listed) {  // some list overflowed: count over the whole tile
+            __syncthreads();
+            BM25_PHASE(2);
+            uint32_t n_cand, n_pos, my_base;
+            {
+                const bool has = lane < WARPS;
+                const uint32_t sv = has ? ts.w_surv[lane] : 0u;
+                const uint32_t inc = warp_inclusive_sum(sv);
+                n_cand = __shfl_sync(0xffffffffu, inc, 31);
+                my_base = __shfl_sync(0xffffffffu, inc - sv, warp);
+                n_pos = __reduce_add_sync(0xffffffffu, has ? ts.w_pos[lane] : 0u);
+                kmin = __reduce_min_sync(0xffffffffu, has ? ts.w_kmin[lane] : 0xffffffffu);
+                kmax = __reduce_max_sync(0xffffffffu, has ? ts.w_kmax[lane] : 0u);
+                if (warp == 0 && lane <= WARPS)
+                    ts.list_pre[lane] = inc - sv;
+            }
+            const bool fill_on = zero_counts && n_pos < kp;
+            if (!fill_on) {
+                if (zero_counts) {  // lift the marks: the accumulators start the next item clean
+#pragma unroll
+                    for (int u = 0; u < U; u++)
+                        if (dd[u] >= 0)
+                            acc[dd[u]] = neg0;
+                }
+                n_emit = n_cand < kp ? n_cand : kp;
+                if (n_cand <= kp) {
+                    // every candidate is kept: warp w writes its own at its offset
+                    const uint32_t nw = ts.w_surv[warp];
+                    for (uint32_t i = lane; i < nw; i += 32)
+                        out[my_base + i] = make_key(my_sval[i], (uint32_t)(d0 + my_sdoc[i]));
+                    new_tau = kmin;
+                    tau_ok = true;
+                } else {
+                    if (tid == 0)
+                        st.ctr = 0;
+                    __syncthreads();
+                    auto get = [&](uint32_t i) -> u64 {
+                        int a = 0, b = WARPS;  // list_pre[a] <= i < list_pre[b]
+                        while (b - a > 1) {
+                            const int mid = (a + b) >> 1;
+                            if (ts.list_pre[mid] <= i)
+                                a = mid;
+                            else
+                                b = mid;
+                        }
+                        const uint32_t s = a * SPW + (i - ts.list_pre[a]);
+                        return make_key(surv_val[s], (uint32_t)(d0 + surv_doc[s]));
+                    };
+                    block_select_idx<true>(st, n_cand, n_cand, kp, common_bytes(kmin, kmax),
+                                           (u64)kmax << 32, get,
+                                           [&](u64 key, uint32_t slot) { out[slot] = key; });
+                    // the selected keys are those at or above the final prefix,
+                    // so its score word bounds the weakest of them from below
+                    new_tau = (uint32_t)(st.prefix >> 32);
+                    tau_ok = true;
+                }
+            } else {
+                // Untouched documents compete (rare): put the candidates' sums
+                // back and select from the whole tile, where -0.0 now means
+                // untouched, the mark means touched below tau, anything else is
+                // a candidate.  Then clear what this thread's postings touched.
+                const uint32_t nw = ts.w_surv[warp];
+                for (uint32_t i = lane; i < nw; i += 32)
+                    acc[my_sdoc[i]] = my_sval[i];
+                uint32_t c = 0;
+                for (int d = tid; d < wd; d += THREADS)
+                    c += __float_as_uint(acc[d]) == kUntouched;
+                uint32_t n_untouched;
+                block_exclusive_sum(c, ts.scan, &n_untouched);
+                const uint32_t n_all = n_cand + n_untouched;
+                n_emit = n_all < kp ? n_all : kp;
+                if (tid == 0)
+                    st.ctr = 0;
+                __syncthreads();
+                auto get = [&](uint32_t d) -> u64 {
+                    const float a = acc[d];
+                    return __float_as_uint(a) == kMarked ? 0ull
+                                                         : make_key(a, (uint32_t)(d0 + d));
+                };
+                block_select_idx<true>(st, (uint32_t)wd, n_all, kp, 0, 0ull, get,
+                                       [&](u64 key, uint32_t slot) { out[slot] = key; });
+                if (n_all > kp) {
+                    new_tau = (uint32_t)(st.prefix >> 32);
+                    tau_ok = true;
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++)
+                    if (dd[u] >= 0)
+                        acc[dd[u]] = neg0;
+            }
+        } else {
+            // ---- many postings or tokens: walk the whole tile --------------------
             uint32_t c = 0, p = 0;
             for (int d = tid; d < wd; d += THREADS) {
                 const float a = acc[d];
@@ -593,69 +673,17 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 16K-document tiles per S
                     p += a > 0.0f;
                 }
             }
-            uint32_t tot;
-            block_exclusive_sum(c, ts.scan, &tot);
-            n_cand = tot;
-            block_exclusive_sum(p, ts.scan, &tot);
-            n_pos = tot;
-        }
-        // Untouched documents score exactly 0.  They can enter the tile's top
-        // k' only if 0 clears tau and fewer than k' touched documents score
-        // above 0; then the lowest-id untouched ones join the candidates.
-        const bool fill_on = !compact && n_pos < kp;
-
-        // ---- select and emit -------------------------------------------------
-        u64* out = cand + (int64_t)item * kprime;
-        uint32_t n_emit;
-        uint32_t new_tau = 0;  // score key of (a lower bound on) the weakest emitted
-        if (listed && !fill_on) {
-            n_emit = n_cand < kp ? n_cand : kp;
-            if (n_cand <= kp && compact) {
-                // every candidate is kept: warp w writes its own at its offset
-                for (uint32_t i = lane; i < n_first; i += 32) {
-                    const int d = my_touch[i];
-                    out[my_base + i] = make_key(acc[d], (uint32_t)(d0 + d));
-                }
-                new_tau = kmin;
-            } else {
-                if (tid == 0)
-                    st.ctr = 0;
-                __syncthreads();
-                // index i lives in warp w's list at i - list_pre[w]
-                auto get = [&](uint32_t i) -> u64 {
-                    int a = 0, b = WARPS;  // list_pre[a] <= i < list_pre[b]
-                    while (b - a > 1) {
-                        const int mid = (a + b) >> 1;
-                        if (ts.list_pre[mid] <= i)
-                            a = mid;
-                        else
-                            b = mid;
-                    }
-                    const int d = ts.touched[a * TPW + (i - ts.list_pre[a])];
-                    const float v = acc[d];
-                    return order_f32(v) >= tau ? make_key(v, (uint32_t)(d0 + d)) : 0ull;
-                };
-                block_select_idx<true>(st, n_list, n_cand, kp, common_bytes(kmin, kmax),
-                                       (u64)kmax << 32, get,
-                                       [&](u64 key, uint32_t slot) { out[slot] = key; });
-                // the selected keys are those at or above the final prefix, so
-                // its score word is a lower bound on the weakest of them
-                new_tau = n_cand > kp ? (uint32_t)(st.prefix >> 32) : kmin;
-            }
-        } else {
-            // rare paths (a list overflowed, or untouched documents may
-            // compete): select straight from the accumulators.  With the fill
-            // on every untouched document is offered (score 0; -0.0 folds onto
-            // +0.0 in the key) and the lowest ids win their ties.
-            uint32_t n_all = n_cand;
+            uint32_t n_cand, n_pos, n_untouched = 0;
+            block_exclusive_sum(c, ts.scan, &n_cand);
+            block_exclusive_sum(p, ts.scan, &n_pos);
+            const bool fill_on = zero_counts && n_pos < kp;
             if (fill_on) {
-                uint32_t c = 0;
+                uint32_t z = 0;
                 for (int d = tid; d < wd; d += THREADS)
-                    c += __float_as_uint(acc[d]) == kUntouched;
-                uint32_t tot;
-                block_exclusive_sum(c, ts.scan, &tot);
-                n_all += tot;
+                    z += __float_as_uint(acc[d]) == kUntouched;
+                block_exclusive_sum(z, ts.scan, &n_untouched);
             }
+            const uint32_t n_all = n_cand + n_untouched;
             n_emit = n_all < kp ? n_all : kp;
             if (tid == 0)
                 st.ctr = 0;
@@ -669,51 +697,28 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 16K-document tiles per S
             };
             block_select_idx<true>(st, (uint32_t)wd, n_all, kp, 0, 0ull, get,
                                    [&](u64 key, uint32_t slot) { out[slot] = key; });
-            new_tau = n_all > kp ? (uint32_t)(st.prefix >> 32) : kZeroKey;
-            if (n_all <= kp) {  // everything was taken: the weakest is the minimum
-                uint32_t mn = 0xffffffffu;
-                for (int d = tid; d < wd; d += THREADS) {
-                    const u64 key = get(d);
-                    if (key != 0ull)
-                        mn = min(mn, (uint32_t)(key >> 32));
-                }
-                mn = __reduce_min_sync(0xffffffffu, mn);
-                if (lane == 0)
-                    ts.w_kmin[warp] = mn;
-                __syncthreads();
-                if (tid == 0) {
-                    for (int w = 0; w < WARPS; w++)
-                        mn = min(mn, ts.w_kmin[w]);
-                    new_tau = mn;
-                }
+            if (n_all > kp) {
+                new_tau = (uint32_t)(st.prefix >> 32);
+                tau_ok = true;
             }
-            // the accumulators are reset from the whole tile below
-        }
-        BM25_PHASE(3);
-
-        // ---- reset the touched accumulators ----------------------------------
-        if (listed && !fill_on) {
-            for (uint32_t i = lane; i < n_first; i += 32)  // the whole list, or the candidates
-                acc[my_touch[i]] = neg0;
-        } else {
-            __syncthreads();  // the walks above read the accumulators
             for (int i = tid; i < wd; i += THREADS)
                 acc[i] = neg0;
         }
+        BM25_PHASE(3);
         if (tid == 0) {
             tcount[item] = n_emit;
             // a full set of k' candidates raises the query's threshold to (a
             // lower bound on) the score of the weakest of them
-            if (n_emit == kp && kp > 0)
+            if (tau_ok && n_emit == kp && kp > 0)
                 atomicMax(&thresh[q], new_tau);
         }
         __syncthreads();
         BM25_PHASE(4);
 #ifdef BM25_PHASE_TIMING
         if (tid == 0) {
-            ph_acc[5] += compact ? 1 : 0;
-            ph_acc[6] += (!listed || fill_on) ? 1 : 0;
-            ph_acc[7] += n_cand > kp ? 1 : 0;
+            ph_acc[5] += one_round ? 1 : 0;
+            ph_acc[6] += zero_counts ? 1 : 0;
+            ph_acc[7] += n_emit == kp ? 1 : 0;
         }
 #endif
         advance(tile, q);
@@ -830,9 +835,12 @@ __global__ void __launch_bounds__(kMergeThreads)
     }
 }
 
-size_t tile_smem_bytes(int32_t W)
+size_t tile_smem_bytes(int32_t W, int threads)
 {
-    return (size_t)W * 4 + sizeof(SelectState) + sizeof(TileStage);
+    const size_t lists = threads == 128   ? tile_lists_bytes<128>()
+                         : threads == 256 ? tile_lists_bytes<256>()
+                                          : tile_lists_bytes<512>();
+    return (size_t)W * 4 + sizeof(SelectState) + sizeof(TileStage) + lists;
 }
 
 template <typename T>
@@ -916,7 +924,7 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
     BM25_TRY(device_info(&di));
     const int64_t N = ix->n_docs;
     const int32_t kprime = (int32_t)std::min<int64_t>(k, N);
-    int32_t W = tile_docs > 0 ? tile_docs : 16384;
+    int32_t W = tile_docs > 0 ? tile_docs : 12288;
     // multiples of 128 keep the shared-memory carve-up 16-byte aligned
     int64_t w_need = (N + 127) / 128 * 128;
     if (W > w_need)
@@ -951,7 +959,7 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
         count_launch();
         BM25_LAUNCH_CHECK();
     }
-    const size_t smem = tile_smem_bytes(W);
+    const size_t smem = tile_smem_bytes(W, plan.threads);
     const int64_t n_items = (int64_t)nq * n_tiles;
     auto launch_tile = [&](auto kernel, int threads) -> int {
         BM25_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
