@@ -216,7 +216,7 @@ int bm25_retrieve_ws(const bm25_index* index, bm25_workspace* ws,
  *
  * Its scratch is one file-scope device array of 16 MiB that every GPU
  * loading the library holds until the process exits.  A batch whose scratch
- * (8 bytes per query, 4 per query, 4 per query token and doc-tile boundary,
+ * (16 bytes per query, 4 per query token and doc-tile boundary,
  * 4 per query and doc tile, 8 per query, doc tile and k' candidate slot)
  * exceeds 16 MiB fails with BM25_E_INVALID; split it.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress), so

@@ -108,6 +108,7 @@ struct bm25_workspace {
     float* out_scores = nullptr;     // staging for the _host entry point
     double* shift = nullptr;         // [max_queries]  sum_i S0(q_i)
     uint32_t* thresh = nullptr;      // [max_queries]  running k'-th best score key
+    uint32_t* qpost = nullptr;       // [max_queries]  postings of the query's columns
     uint32_t* tcount = nullptr;      // [n_queries * n_tiles]  candidates per (tile, query) item
     int32_t* seg = nullptr;          // [max_query_tokens * (max_tiles + 1)]
     unsigned long long* cand = nullptr;  // [n_queries * n_tiles * k'], k' slots per item

@@ -98,11 +98,12 @@ extern "C" int bm25_retrieve_noalloc(const bm25_index* ix, const int32_t* query_
 
     const size_t b_shift = align_up(sizeof(double) * (size_t)n_queries);
     const size_t b_thresh = align_up(sizeof(uint32_t) * (size_t)n_queries);
+    const size_t b_qpost = align_up(sizeof(uint32_t) * (size_t)n_queries);
     const size_t b_seg = align_up(sizeof(int32_t) * (size_t)n_query_tokens * (size_t)(n_tiles + 1));
     const size_t b_tcount = align_up(sizeof(uint32_t) * (size_t)n_queries * (size_t)n_tiles);
     const size_t b_cand =
         align_up(sizeof(unsigned long long) * (size_t)n_queries * (size_t)n_tiles * (size_t)kp);
-    const size_t need = b_shift + b_thresh + b_seg + b_tcount + b_cand;
+    const size_t need = b_shift + b_thresh + b_qpost + b_seg + b_tcount + b_cand;
     if (need > kScratchBytes)
         return set_error(BM25_E_INVALID,
                          "this batch needs %zu bytes of scratch; bm25_retrieve_noalloc holds %zu "
@@ -118,12 +119,14 @@ extern "C" int bm25_retrieve_noalloc(const bm25_index* ix, const int32_t* query_
     ws.device = dev;
     ws.shift = reinterpret_cast<double*>(p);
     ws.thresh = reinterpret_cast<uint32_t*>(p + b_shift);
+    ws.qpost = reinterpret_cast<uint32_t*>(p + b_shift + b_thresh);
     ws.max_queries = n_queries;
-    ws.seg = reinterpret_cast<int32_t*>(p + b_shift + b_thresh);
+    p += b_shift + b_thresh + b_qpost;
+    ws.seg = reinterpret_cast<int32_t*>(p);
     ws.seg_cap = (size_t)n_query_tokens * (size_t)(n_tiles + 1);
-    ws.tcount = reinterpret_cast<uint32_t*>(p + b_shift + b_thresh + b_seg);
+    ws.tcount = reinterpret_cast<uint32_t*>(p + b_seg);
     ws.tcount_cap = (size_t)n_queries * (size_t)n_tiles;
-    ws.cand = reinterpret_cast<unsigned long long*>(p + b_shift + b_thresh + b_seg + b_tcount);
+    ws.cand = reinterpret_cast<unsigned long long*>(p + b_seg + b_tcount);
     ws.cand_cap = (size_t)n_queries * (size_t)n_tiles * (size_t)kp;
     if (ws.seg_cap == 0)
         ws.seg_cap = 1;  // an empty batch of tokens still passes a non-null buffer

@@ -4,7 +4,8 @@
 //
 // Doc-tiled shared-memory path, four launches per call:
 //   R0 k_query_prep   sum_i S0(q_i) per query in FP64; token / offset checks;
-//                     resets the per-query running threshold
+//                     resets the per-query running threshold; counts the
+//                     query's postings (a bound on the documents it touches)
 //   R1 k_seg_bounds   for every query token and every doc-tile boundary, the
 //                     first posting of the token's column at or past the
 //                     boundary (binary search: doc ids ascend in a column)
@@ -37,8 +38,9 @@ constexpr uint32_t kZeroKey = 0x80000000u;  // order_f32(0.0f)
 // ---- R0 ---------------------------------------------------------------------
 __global__ void k_query_prep(const int32_t* __restrict__ q_tokens, int64_t n_tok,
                              const int64_t* __restrict__ q_off, int32_t nq,
-                             const double* __restrict__ s0, int32_t vocab,
-                             double* __restrict__ shift, uint32_t* __restrict__ thresh,
+                             const double* __restrict__ s0, const int64_t* __restrict__ indptr,
+                             int32_t vocab, double* __restrict__ shift,
+                             uint32_t* __restrict__ thresh, uint32_t* __restrict__ qpost,
                              int* status)
 {
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
@@ -50,6 +52,7 @@ __global__ void k_query_prep(const int32_t* __restrict__ q_tokens, int64_t n_tok
         lo = lo < 0 ? 0 : (lo > n_tok ? n_tok : lo);
         hi = hi < lo ? lo : (hi > n_tok ? n_tok : hi);
         double sum = 0.0;
+        int64_t post = 0;
         for (int64_t m = lo; m < hi; m++) {
             int32_t t = q_tokens[m];
             if (t < 0 || t >= vocab) {
@@ -57,9 +60,11 @@ __global__ void k_query_prep(const int32_t* __restrict__ q_tokens, int64_t n_tok
                 continue;
             }
             sum += s0[t];
+            post += indptr[t + 1] - indptr[t];
         }
         shift[q] = sum;
         thresh[q] = 0u;  // below every real score key
+        qpost[q] = post > 0xffffffffll ? 0xffffffffu : (uint32_t)post;
     }
 }
 
@@ -266,21 +271,82 @@ __device__ unsigned long long g_phase[16];
 #endif
 constexpr uint32_t kUntouched = 0x80000000u;  // bits of -0.0f
 constexpr uint32_t kMarked = 0x7fffffffu;     // a NaN: claimed while untouched ones still count
-constexpr uint32_t kRunCap = 128;             // runs of 32 postings with a cached token
 constexpr int kMaxWarps = 16;
 constexpr int kPostU = 8;                     // postings per thread in one round
+constexpr uint32_t kOutCap = 128;             // candidates an item stages for a deferred write
 
 struct TileStage {
     int32_t lo[kTokChunk];
     int32_t pre[kTokChunk + 1];
-    uint8_t run_tok[kRunCap];             // token of the first posting of run r
     uint32_t scan[33];
     int32_t qoff[2][2];                   // token range of the current / next item
     uint32_t w_surv[kMaxWarps];           // per warp: its candidates
     uint32_t w_pos[kMaxWarps];            // per warp: claimed documents scoring > 0
     uint32_t w_kmin[kMaxWarps], w_kmax[kMaxWarps];  // per warp: candidate score keys
     uint32_t list_pre[kMaxWarps + 1];     // exclusive prefix of the candidate lists
+    // The previous item's result, written to global memory by the next item
+    // once its first barrier has passed, so that no barrier waits on those
+    // writes: its candidates (when at most kOutCap), count and threshold.
+    u64 obuf[kOutCap];
+    int32_t o_item, o_q;
+    uint32_t o_count, o_tau, o_staged;  // o_staged = 0: written directly already
+    uint32_t q_post;                    // the current query's postings (all columns)
+    uint32_t cutoff;                    // fill: docs [0, cutoff) hold the k' lowest untouched
 };
+
+// Bitonic sort of one 64-bit key per lane, descending across the warp.
+__device__ __forceinline__ u64 warp_sort_desc(u64 key)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const u64 other = __shfl_xor_sync(0xffffffffu, key, stride);
+            const bool lower = (lane & stride) == 0;  // the lower index of the pair
+            const bool desc = (lane & size) == 0;     // this block sorts descending
+            // the lower index keeps the larger key in a descending block
+            const bool keep_max = (lower == desc);
+            key = keep_max ? (key > other ? key : other) : (key < other ? key : other);
+        }
+    }
+    return key;
+}
+
+// Counts the untouched documents (accumulator -0.0) among the tile's first
+// wd, up to k of them, and stores in *cutoff the smallest c such that docs
+// [0, c) hold min(k, untouched) of them.  All threads call it (block scans
+// over words of 32 documents); ends with __syncthreads().
+__device__ uint32_t first_untouched(const float* acc, int32_t wd, uint32_t k, uint32_t* scan_buf,
+                                    uint32_t* cutoff)
+{
+    const int32_t nwords = (wd + 31) >> 5;
+    uint32_t carry = 0;
+    if (threadIdx.x == 0)
+        *cutoff = (uint32_t)wd;
+    for (int w0 = 0; w0 < nwords && carry < k; w0 += blockDim.x) {
+        const int w = w0 + threadIdx.x;
+        uint32_t zeros = 0;
+        if (w < nwords) {
+            const int dmax = min(32, wd - (w << 5));
+            for (int b = 0; b < dmax; b++)
+                if (__float_as_uint(acc[(w << 5) + b]) == 0x80000000u)
+                    zeros |= 1u << b;
+        }
+        const uint32_t z = __popc(zeros);
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_sum(z, scan_buf, &tot) + carry;
+        if (w < nwords && ex < k && ex + z >= k) {  // the k-th untouched one is here
+            uint32_t f = zeros;
+            for (uint32_t c = ex + 1; c < k; c++)
+                f &= f - 1;
+            *cutoff = (uint32_t)((w << 5) + __ffs(f));  // one past it
+        }
+        carry += tot;
+    }
+    __syncthreads();
+    return carry < k ? carry : k;
+}
 
 template <int THREADS>
 constexpr size_t tile_lists_bytes()
@@ -294,8 +360,8 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
                 const int64_t* __restrict__ q_off, int32_t nq, int64_t n_docs,
                 const int32_t* __restrict__ indices, const float* __restrict__ data,
                 const int32_t* __restrict__ seg, int32_t W, int32_t n_tiles, int32_t kprime,
-                uint32_t* __restrict__ thresh, uint32_t* __restrict__ tcount,
-                u64* __restrict__ cand)
+                uint32_t* __restrict__ thresh, const uint32_t* __restrict__ qpost,
+                uint32_t* __restrict__ tcount, u64* __restrict__ cand)
 {
     constexpr int WARPS = THREADS / 32;
     constexpr int U = kPostU;
@@ -350,7 +416,7 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
     int32_t a1 = 0, b1 = 0;                 // clamped token range of item i+1
     int64_t ra2 = 0, rb2 = 0;               // raw token range of item i+2
     int32_t pf_lo0 = 0, pf_lo1 = 0, pf_hi0 = 0, pf_hi1 = 0;
-    uint32_t pf_tau = 0;
+    uint32_t pf_tau = 0, pf_post = 0;
     auto load_seg = [&](int32_t t_, int32_t a_, int32_t b_) {
         const int32_t m_ = a_ + 2 * tid;
         pf_lo0 = pf_hi0 = pf_lo1 = pf_hi1 = 0;
@@ -363,6 +429,8 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
             pf_hi1 = seg[(int64_t)(m_ + 1) * per + t_ + 1];
         }
     };
+    if (tid == 0)
+        ts.o_item = -1;
     if (tid < 32) {
         const int32_t a0 = clamp_off(q_off[q]);
         const int32_t b0 = max(a0, clamp_off(q_off[q + 1]));
@@ -371,6 +439,7 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
             ts.qoff[0][0] = a0;
             ts.qoff[0][1] = b0;
             pf_tau = *(volatile uint32_t*)&thresh[q];
+            pf_post = qpost[q];
         }
         if ((int64_t)blockIdx.x + gridDim.x < n_items) {
             a1 = clamp_off(q_off[q1]);
@@ -387,6 +456,22 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
     long long ph_t = clock64();
 #endif
 
+    // writes the previous item's staged result (all threads; call between
+    // two barriers)
+    auto flush = [&]() {
+        const int32_t pi = ts.o_item;
+        if (pi < 0)
+            return;
+        const uint32_t pc = ts.o_count;
+        if (ts.o_staged) {
+            for (uint32_t t = tid; t < pc; t += THREADS)
+                cand[(int64_t)pi * kprime + t] = ts.obuf[t];
+            if (tid == 0)
+                tcount[pi] = pc;
+        }
+        if (tid == 0 && ts.o_tau != 0u)
+            atomicMax(&thresh[ts.o_q], ts.o_tau);
+    };
     int parity = 0;
     for (int32_t item = blockIdx.x; item < n_items; item += gridDim.x, parity ^= 1) {
         const int64_t d0 = (int64_t)tile * W;
@@ -402,6 +487,7 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
                         ts.qoff[parity ^ 1][0] = a1;
                         ts.qoff[parity ^ 1][1] = b1;
                         pf_tau = *(volatile uint32_t*)&thresh[q1];
+                        pf_post = qpost[q1];
                     }
                 }
                 a1 = clamp_off(ra2);
@@ -418,8 +504,10 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
                 q2 = q3;
             }
         };
-        if (tid == 0)
+        if (tid == 0) {
             st.tau = pf_tau;  // thread 0 holds the threshold; the others read st.tau
+            ts.q_post = pf_post;
+        }
         int32_t dd[U];        // doc ids (within the tile) of this thread's postings
 #pragma unroll
         for (int u = 0; u < U; u++)
@@ -454,53 +542,40 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
                 ts.pre[2 * tid + 1] = inc - s2 + len[0];
                 if (tid == 31)
                     ts.pre[kTokChunk] = inc;
-                __syncwarp();
-                // the token holding the first posting of each run of 32
-                const int32_t total = ts.pre[kTokChunk];
-                for (int r = tid; r < (int)kRunCap && r * 32 < total; r += 32) {
-                    const int32_t e = r * 32;
-                    int a = 0, b = cnt;  // pre[a] <= e < pre[b]
-                    while (b - a > 1) {
-                        const int mid = (a + b) >> 1;
-                        if (ts.pre[mid] <= e)
-                            a = mid;
-                        else
-                            b = mid;
-                    }
-                    ts.run_tok[r] = (uint8_t)a;
-                }
                 if (mb == m0)
                     pipeline();
             }
             __syncthreads();
             BM25_PHASE(0);
+            if (mb == m0)
+                flush();
             const int32_t total = ts.pre[kTokChunk];
             if (mb != m0 || total > U * THREADS)
                 one_round = false;
-            // Warp w takes runs of 32 consecutive postings; each lane starts
-            // from its run's first token and steps over finished segments.
+            // Warp w takes runs of 32 consecutive postings, r = w, w + WARPS, ...
+            // The token of its first run comes from one warp-uniform binary
+            // search; runs only move forward, so each later one (and each
+            // lane) steps on from there over finished or empty segments.
             for (int32_t r0 = warp; r0 * 32 < total; r0 += U * WARPS) {
                 float vv[U];
+                int a = 0;
+                {
+                    const int32_t eb = r0 * 32;
+                    int b = cnt;  // pre[a] <= eb < pre[b]
+                    while (b - a > 1) {
+                        const int mid = (a + b) >> 1;
+                        if (ts.pre[mid] <= eb)
+                            a = mid;
+                        else
+                            b = mid;
+                    }
+                }
 #pragma unroll
                 for (int u = 0; u < U; u++) {
                     const int32_t r = r0 + u * WARPS;
                     const int32_t e = r * 32 + lane;
                     dd[u] = -1;
                     if (e < total) {
-                        int a;
-                        if (r < (int32_t)kRunCap) {
-                            a = ts.run_tok[r];
-                        } else {
-                            int lo_ = 0, hi_ = cnt;
-                            while (hi_ - lo_ > 1) {
-                                const int mid = (lo_ + hi_) >> 1;
-                                if (ts.pre[mid] <= e)
-                                    lo_ = mid;
-                                else
-                                    hi_ = mid;
-                            }
-                            a = lo_;
-                        }
                         while (ts.pre[a + 1] <= e)
                             a++;
                         const int32_t j = ts.lo[a] + (e - ts.pre[a]);
@@ -522,6 +597,8 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
         if (m0 == m1) {
             pipeline();
             __syncthreads();
+            flush();
+            __syncthreads();  // the flush reads the staged result before it is replaced
         }
 
         // tau = the query's running threshold: some tile already holds k'
@@ -530,9 +607,15 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
         const uint32_t tau = st.tau;
         const uint32_t kp = (uint32_t)min(kprime, wd);
         // Untouched documents score exactly 0: they can matter only if 0
-        // clears tau (and then only if fewer than k' touched ones score > 0).
+        // clears tau (and then only if fewer than k' touched ones score > 0),
+        // and only the k' lowest-id untouched documents of the whole corpus
+        // can: a tile whose predecessors hold at least k' untouched documents
+        // (true once t * W - postings of the query >= k') adds none.
         const bool zero_counts = tau <= kZeroKey;
-        u64* out = cand + (int64_t)item * kprime;
+        const bool may_fill = zero_counts && (int64_t)tile * W < (int64_t)kp + ts.q_post;
+        // candidates go to the staging buffer when they fit (kp <= kOutCap),
+        // else straight to the item's slots
+        u64* out = kp <= kOutCap ? ts.obuf : cand + (int64_t)item * kprime;
         uint32_t n_emit = 0;
         uint32_t new_tau = 0;  // score key of (a lower bound on) the weakest emitted
         bool tau_ok = false;   // new_tau is a valid bound to publish
@@ -541,19 +624,21 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
             // ---- claim each posting's document once; keep the candidates ---------
             const uint32_t mark = zero_counts ? kMarked : kUntouched;
             uint32_t pos = 0, kmin = 0xffffffffu, kmax = 0u, n_keep = 0;
+            float cv[U];  // all exchanges first, so their latencies overlap
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                cv[u] = dd[u] >= 0 ? atomicExch(&acc[dd[u]], __uint_as_float(mark))
+                                   : __uint_as_float(kUntouched);
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 bool keep = false;
-                float v = 0.0f;
+                const float v = cv[u];
+                const uint32_t vb = __float_as_uint(v);
                 uint32_t o = 0;
-                if (dd[u] >= 0) {
-                    v = atomicExch(&acc[dd[u]], __uint_as_float(mark));
-                    const uint32_t vb = __float_as_uint(v);
-                    if (vb != kUntouched && vb != kMarked) {  // the first claim
-                        o = order_f32(v);
-                        pos += (v > 0.0f);
-                        keep = o >= tau;
-                    }
+                if (vb != kUntouched && vb != kMarked) {  // the first claim of the document
+                    o = order_f32(v);
+                    pos += (v > 0.0f);
+                    keep = o >= tau;
                 }
                 const uint32_t bal = __ballot_sync(0xffffffffu, keep);
                 if (keep) {
@@ -589,7 +674,7 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
                 if (warp == 0 && lane <= WARPS)
                     ts.list_pre[lane] = inc - sv;
             }
-            const bool fill_on = zero_counts && n_pos < kp;
+            const bool fill_on = may_fill && n_pos < kp;
             if (!fill_on) {
                 if (zero_counts) {  // lift the marks: the accumulators start the next item clean
 #pragma unroll
@@ -605,7 +690,34 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
                         out[my_base + i] = make_key(my_sval[i], (uint32_t)(d0 + my_sdoc[i]));
                     new_tau = kmin;
                     tau_ok = true;
+                } else if (n_cand <= 32) {
+                    // a few candidates too many (kp < n_cand <= 32): warp 0 sorts
+                    // them in registers, no block barrier
+                    if (warp == 0) {
+                        u64 key = 0ull;
+                        if ((uint32_t)lane < n_cand) {
+                            int a = 0, b = WARPS;  // list_pre[a] <= lane < list_pre[b]
+                            while (b - a > 1) {
+                                const int mid = (a + b) >> 1;
+                                if (ts.list_pre[mid] <= (uint32_t)lane)
+                                    a = mid;
+                                else
+                                    b = mid;
+                            }
+                            const uint32_t sl = a * SPW + (lane - ts.list_pre[a]);
+                            key = make_key(surv_val[sl], (uint32_t)(d0 + surv_doc[sl]));
+                        }
+                        key = warp_sort_desc(key);
+                        if ((uint32_t)lane < kp)
+                            out[lane] = key;
+                        new_tau = (uint32_t)(__shfl_sync(0xffffffffu, key, kp - 1) >> 32);
+                    }
+                    tau_ok = true;
                 } else {
+#ifdef BM25_PHASE_TIMING
+                    if (tid == 0)
+                        ph_acc[6] += 1;
+#endif
                     if (tid == 0)
                         st.ctr = 0;
                     __syncthreads();
@@ -630,29 +742,44 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
                     tau_ok = true;
                 }
             } else {
+#ifdef BM25_PHASE_TIMING
+                if (tid == 0)
+                    ph_acc[7] += 1;
+#endif
                 // Untouched documents compete (rare): put the candidates' sums
-                // back and select from the whole tile, where -0.0 now means
-                // untouched, the mark means touched below tau, anything else is
-                // a candidate.  Then clear what this thread's postings touched.
+                // back (so -0.0 again means untouched and the mark means
+                // touched below tau), find the k' lowest untouched documents,
+                // and select among the candidate lists and those.
                 const uint32_t nw = ts.w_surv[warp];
                 for (uint32_t i = lane; i < nw; i += 32)
                     acc[my_sdoc[i]] = my_sval[i];
-                uint32_t c = 0;
-                for (int d = tid; d < wd; d += THREADS)
-                    c += __float_as_uint(acc[d]) == kUntouched;
-                uint32_t n_untouched;
-                block_exclusive_sum(c, ts.scan, &n_untouched);
-                const uint32_t n_all = n_cand + n_untouched;
+                __syncthreads();
+                const uint32_t n_unt = first_untouched(acc, wd, kp, ts.scan, &ts.cutoff);
+                const uint32_t cut = ts.cutoff;
+                const uint32_t n_all = n_cand + n_unt;
                 n_emit = n_all < kp ? n_all : kp;
                 if (tid == 0)
                     st.ctr = 0;
                 __syncthreads();
-                auto get = [&](uint32_t d) -> u64 {
-                    const float a = acc[d];
-                    return __float_as_uint(a) == kMarked ? 0ull
-                                                         : make_key(a, (uint32_t)(d0 + d));
+                auto get = [&](uint32_t i) -> u64 {
+                    if (i < n_cand) {
+                        int a = 0, b = WARPS;  // list_pre[a] <= i < list_pre[b]
+                        while (b - a > 1) {
+                            const int mid = (a + b) >> 1;
+                            if (ts.list_pre[mid] <= i)
+                                a = mid;
+                            else
+                                b = mid;
+                        }
+                        const uint32_t s = a * SPW + (i - ts.list_pre[a]);
+                        return make_key(surv_val[s], (uint32_t)(d0 + surv_doc[s]));
+                    }
+                    const uint32_t d = i - n_cand;
+                    return __float_as_uint(acc[d]) == kUntouched
+                               ? make_key(0.0f, (uint32_t)(d0 + d))
+                               : 0ull;
                 };
-                block_select_idx<true>(st, (uint32_t)wd, n_all, kp, 0, 0ull, get,
+                block_select_idx<true>(st, n_cand + cut, n_all, kp, 0, 0ull, get,
                                        [&](u64 key, uint32_t slot) { out[slot] = key; });
                 if (n_all > kp) {
                     new_tau = (uint32_t)(st.prefix >> 32);
@@ -673,17 +800,14 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
                     p += a > 0.0f;
                 }
             }
-            uint32_t n_cand, n_pos, n_untouched = 0;
+            uint32_t n_cand, n_pos, n_untouched = 0, cut = 0;
             block_exclusive_sum(c, ts.scan, &n_cand);
             block_exclusive_sum(p, ts.scan, &n_pos);
-            const bool fill_on = zero_counts && n_pos < kp;
+            const bool fill_on = may_fill && n_pos < kp;
             if (fill_on) {
-                uint32_t z = 0;
-                for (int d = tid; d < wd; d += THREADS)
-                    z += __float_as_uint(acc[d]) == kUntouched;
-                block_exclusive_sum(z, ts.scan, &n_untouched);
-            }
-            const uint32_t n_all = n_cand + n_untouched;
+                n_untouched = first_untouched(acc, wd, kp, ts.scan, &ts.cutoff);
+                cut = ts.cutoff;
+            }            const uint32_t n_all = n_cand + n_untouched;
             n_emit = n_all < kp ? n_all : kp;
             if (tid == 0)
                 st.ctr = 0;
@@ -691,7 +815,7 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
             auto get = [&](uint32_t d) -> u64 {
                 const float a = acc[d];
                 const bool touched = __float_as_uint(a) != kUntouched;
-                return (touched ? order_f32(a) >= tau : fill_on)
+                return (touched ? order_f32(a) >= tau : d < cut)
                            ? make_key(a, (uint32_t)(d0 + d))
                            : 0ull;
             };
@@ -706,23 +830,26 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
         }
         BM25_PHASE(3);
         if (tid == 0) {
-            tcount[item] = n_emit;
-            // a full set of k' candidates raises the query's threshold to (a
-            // lower bound on) the score of the weakest of them
-            if (tau_ok && n_emit == kp && kp > 0)
-                atomicMax(&thresh[q], new_tau);
+            // staged for the next item's flush; a full set of k' candidates
+            // raises the query's threshold to (a lower bound on) the score of
+            // the weakest of them
+            ts.o_item = item;
+            ts.o_q = q;
+            ts.o_count = n_emit;
+            ts.o_staged = kp <= kOutCap;
+            ts.o_tau = (tau_ok && n_emit == kp && kp > 0) ? new_tau : 0u;
+            if (kp > kOutCap)
+                tcount[item] = n_emit;  // its candidates were written directly
         }
         __syncthreads();
         BM25_PHASE(4);
 #ifdef BM25_PHASE_TIMING
-        if (tid == 0) {
+        if (tid == 0)
             ph_acc[5] += one_round ? 1 : 0;
-            ph_acc[6] += zero_counts ? 1 : 0;
-            ph_acc[7] += n_emit == kp ? 1 : 0;
-        }
 #endif
         advance(tile, q);
     }
+    flush();  // the CTA's last item
 #ifdef BM25_PHASE_TIMING
     if (tid == 0)
         for (int i = 0; i < 8; i++)
@@ -878,14 +1005,16 @@ int workspace_reserve(const bm25_index* ix, bm25_workspace* ws, int32_t nq, int6
 {
     (void)ix;
     if (nq > ws->max_queries || !ws->shift) {
-        for (void* p : {(void*)ws->shift, (void*)ws->thresh})
+        for (void* p : {(void*)ws->shift, (void*)ws->thresh, (void*)ws->qpost})
             if (p)
                 cudaFree(p);
         ws->shift = nullptr;
         ws->thresh = nullptr;
+        ws->qpost = nullptr;
         const size_t m = (size_t)std::max(nq, 1);
         BM25_CUDA_TRY(cudaMalloc((void**)&ws->shift, sizeof(double) * m));
         BM25_CUDA_TRY(cudaMalloc((void**)&ws->thresh, sizeof(uint32_t) * m));
+        BM25_CUDA_TRY(cudaMalloc((void**)&ws->qpost, sizeof(uint32_t) * m));
         ws->max_queries = (int32_t)m;
     }
     BM25_TRY(grow(&ws->seg, &ws->seg_cap, (size_t)n_tok * (size_t)(n_tiles + 1)));
@@ -896,7 +1025,7 @@ int workspace_reserve(const bm25_index* ix, bm25_workspace* ws, int32_t nq, int6
 
 void workspace_release(bm25_workspace* ws)
 {
-    void* ps[] = {ws->shift, ws->thresh, ws->tcount, ws->seg, ws->cand};
+    void* ps[] = {ws->shift, ws->thresh, ws->qpost, ws->tcount, ws->seg, ws->cand};
     for (void* p : ps)
         if (p)
             cudaFree(p);
@@ -908,6 +1037,7 @@ void workspace_release(bm25_workspace* ws)
     }
     ws->shift = nullptr;
     ws->thresh = nullptr;
+    ws->qpost = nullptr;
     ws->tcount = nullptr;
     ws->seg = nullptr;
     ws->cand = nullptr;
@@ -943,8 +1073,9 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
     int g0 = (int)std::min<int64_t>((nq + 255) / 256, max_blocks);
     {
         ProfileScope ps_("k_query_prep", s);
-        k_query_prep<<<std::max(g0, 1), 256, 0, s>>>(q_tokens, n_tok, q_off, nq, ix->s0, ix->vocab,
-                                                      ws->shift, ws->thresh, ix->status);
+        k_query_prep<<<std::max(g0, 1), 256, 0, s>>>(q_tokens, n_tok, q_off, nq, ix->s0,
+                                                      ix->indptr, ix->vocab, ws->shift,
+                                                      ws->thresh, ws->qpost, ix->status);
     }
     count_launch();
     BM25_LAUNCH_CHECK();
@@ -977,8 +1108,8 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
         {
             ProfileScope ps_("k_tile_topk", s);
             kernel<<<g2, threads, smem, s>>>(q_tokens, n_tok, q_off, nq, N, ix->indices, ix->data,
-                                             ws->seg, W, n_tiles, kprime, ws->thresh, ws->tcount,
-                                             ws->cand);
+                                             ws->seg, W, n_tiles, kprime, ws->thresh, ws->qpost,
+                                             ws->tcount, ws->cand);
         }
         count_launch();
         BM25_LAUNCH_CHECK();
