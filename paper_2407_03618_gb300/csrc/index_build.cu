@@ -33,11 +33,13 @@ constexpr int kMaxDigitBits = 8;
 constexpr int kMaxBuckets = 1 << kMaxDigitBits;
 
 // ---- K1 -------------------------------------------------------------------
-// One warp per document: |D|, the doc id of each of its tokens, and the FP32
-// length factor used by the score kernel (k1 * K_D, or 1 / K_D for BM25L,
-// with K_D = 1 - b + b |D| / Lavg evaluated in FP64).  Offsets are checked;
-// a malformed range records BM25_E_TOKEN_RANGE and writes nothing outside
-// [0, n_tokens).
+// One warp per group of 32 documents (lane l: document g*32 + l): |D|, the
+// FP32 length factor used by the score kernel (k1 * K_D, or 1 / K_D for
+// BM25L, with K_D = 1 - b + b |D| / Lavg evaluated in FP64), and the doc id
+// of every token of the group, written coalesced: each position finds its
+// document by a 5-step search over the lanes' start offsets.  Offsets are
+// checked; a malformed range records BM25_E_TOKEN_RANGE and nothing is
+// written outside [0, n_tokens).
 __global__ void k_doc_prep(const int64_t* __restrict__ off, int64_t n_docs, int64_t n_tokens,
                            int32_t* __restrict__ tok_doc, int32_t* __restrict__ doc_len,
                            float* __restrict__ len_factor, int variant, double k1, double b,
@@ -48,21 +50,44 @@ __global__ void k_doc_prep(const int64_t* __restrict__ off, int64_t n_docs, int6
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     if (warp0 == 0 && lane == 0 && (off[0] != 0 || off[n_docs] != n_tokens))
         set_status(status, BM25_E_TOKEN_RANGE);
-    for (int64_t d = warp0; d < n_docs; d += nwarps) {
-        int64_t lo = off[d], hi = off[d + 1];
-        bool bad = lo < 0 || hi < lo || hi > n_tokens;
-        if (lane == 0) {
-            if (bad)
-                set_status(status, BM25_E_TOKEN_RANGE);
-            int64_t len = bad ? 0 : hi - lo;
+    const int64_t n_groups = (n_docs + 31) >> 5;
+    for (int64_t g = warp0; g < n_groups; g += nwarps) {
+        const int64_t d = (g << 5) + lane;
+        const bool has = d < n_docs;
+        int64_t lo = has ? off[d] : 0, hi = has ? off[d + 1] : 0;
+        const bool bad = has && (lo < 0 || hi < lo || hi > n_tokens);
+        if (bad)
+            set_status(status, BM25_E_TOKEN_RANGE);
+        if (has) {
+            const int64_t len = bad ? 0 : hi - lo;
             doc_len[d] = (int32_t)len;
-            double kd = 1.0 - b + b * (double)len / lavg;
+            const double kd = 1.0 - b + b * (double)len / lavg;
             len_factor[d] = (variant == BM25_L) ? (float)(1.0 / kd) : (float)(k1 * kd);
         }
-        if (bad)
-            continue;
-        for (int64_t p = lo + lane; p < hi; p += 32)
-            tok_doc[p] = (int32_t)d;
+        if (__any_sync(0xffffffffu, bad))
+            continue;  // the build fails; only in-range writes happen above
+        if (!has)
+            lo = hi = n_tokens;  // lanes past the last document start nothing
+        // the group's tokens are [first lo, last hi); lane l's document owns
+        // [lo_l, hi_l), and documents are contiguous
+        const int64_t start = __shfl_sync(0xffffffffu, lo, 0);
+        int last = 31;
+        {
+            const unsigned has_mask = __ballot_sync(0xffffffffu, has);
+            last = 31 - __clz(has_mask);
+        }
+        const int64_t end = __shfl_sync(0xffffffffu, hi, last);
+        for (int64_t p = start + lane; p < end; p += 32) {
+            // the last lane whose document starts at or before p
+            int idx = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int64_t s_lo = __shfl_sync(0xffffffffu, lo, idx + step);
+                if (idx + step <= last && s_lo <= p)
+                    idx += step;
+            }
+            tok_doc[p] = (int32_t)((g << 5) + idx);
+        }
     }
 }
 
@@ -110,7 +135,9 @@ __global__ void __launch_bounds__(kSortThreads)
 // walks them in 16 rounds of 32 consecutive items; __match_any_sync groups a
 // round's lanes by digit, so each item's rank among equal digits follows its
 // position.  Per-warp counters are then turned into per-warp bases by an
-// exclusive scan over warps, which keeps warp order = item order.
+// exclusive scan over warps, which keeps warp order = item order.  The items
+// are reordered in shared memory into the tile's digit order first, so that
+// consecutive threads write consecutive global positions of one digit.
 __global__ void __launch_bounds__(kSortThreads)
     k_radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                       uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n,
@@ -118,6 +145,10 @@ __global__ void __launch_bounds__(kSortThreads)
 {
     __shared__ uint32_t wcnt[kSortWarps][kMaxBuckets];
     __shared__ uint32_t gbase[kMaxBuckets];
+    __shared__ uint32_t dstart[kMaxBuckets];
+    __shared__ uint32_t sk[kSortTile];
+    __shared__ uint32_t sv[kSortTile];
+    __shared__ uint32_t scan_buf[33];
     const int nb = 1 << bits;
     const uint32_t mask = (uint32_t)nb - 1u;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -127,7 +158,9 @@ __global__ void __launch_bounds__(kSortThreads)
         gbase[d] = offsets[(int64_t)d * n_tiles + blockIdx.x];
     __syncthreads();
 
-    const int64_t base = (int64_t)blockIdx.x * kSortTile + warp * (kSortIpt * 32);
+    const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+    const int tile_n = (int)min((int64_t)kSortTile, n - tile0);
+    const int64_t base = tile0 + warp * (kSortIpt * 32);
     const uint32_t lt = lanemask_lt();
     uint32_t k[kSortIpt], v[kSortIpt], rank[kSortIpt];
 #pragma unroll
@@ -151,60 +184,55 @@ __global__ void __launch_bounds__(kSortThreads)
         rank[r] = before + (uint32_t)__popc(peers & lt);
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < nb; d += kSortThreads) {
-        uint32_t run = 0;
+    // per digit: exclusive scan over warps (warp bases) and the tile total;
+    // then the digits' start offsets in the tile
+    uint32_t tot = 0;
+    if ((int)threadIdx.x < nb) {
 #pragma unroll
         for (int w = 0; w < kSortWarps; w++) {
-            uint32_t t = wcnt[w][d];
-            wcnt[w][d] = run;
-            run += t;
+            uint32_t t = wcnt[w][threadIdx.x];
+            wcnt[w][threadIdx.x] = tot;
+            tot += t;
         }
     }
+    uint32_t all;
+    const uint32_t ds = block_exclusive_sum(tot, scan_buf, &all);
+    if ((int)threadIdx.x < nb)
+        dstart[threadIdx.x] = ds;
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kSortIpt; r++) {
         int64_t p = base + r * 32 + lane;
         if (p < n) {
             uint32_t dg = (k[r] >> shift) & mask;
-            uint32_t pos = gbase[dg] + wcnt[warp][dg] + rank[r];
-            keys_out[pos] = k[r];
-            vals_out[pos] = v[r];
+            uint32_t local = dstart[dg] + wcnt[warp][dg] + rank[r];
+            sk[local] = k[r];
+            sv[local] = v[r];
         }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < tile_n; i += kSortThreads) {
+        const uint32_t kk = sk[i];
+        const uint32_t dg = (kk >> shift) & mask;
+        const uint32_t pos = gbase[dg] + ((uint32_t)i - dstart[dg]);
+        keys_out[pos] = kk;
+        vals_out[pos] = sv[i];
     }
 }
 
 // ---- K3: run-length reduce -------------------------------------------------
-// Tile of 4096 sorted positions; thread t owns 16 consecutive positions.  A
-// position starts a run (a distinct (term, doc) pair) when its pair differs
-// from the previous position's.
-__device__ __forceinline__ uint32_t heads_in_chunk(const uint32_t* __restrict__ keys,
-                                                   const uint32_t* __restrict__ vals,
-                                                   int64_t n, int64_t p0, uint32_t& flags)
+// Tile of 4096 sorted positions, striped: in round i, warp w covers the 32
+// consecutive positions tile + i*256 + w*32 + lane.  A position starts a run
+// (a distinct (term, doc) pair) when its pair differs from the previous
+// position's.  Runs are numbered in position order, i.e. by (round, warp,
+// lane), so the writes of one warp-round are consecutive.
+__device__ __forceinline__ bool is_head(const uint32_t* __restrict__ keys,
+                                        const uint32_t* __restrict__ vals, int64_t p,
+                                        uint32_t& kk, uint32_t& vv)
 {
-    uint32_t pk, pv;
-    if (p0 == 0) {
-        pk = ~keys[0];
-        pv = 0;
-    } else {
-        pk = keys[p0 - 1];
-        pv = vals[p0 - 1];
-    }
-    uint32_t c = 0;
-    flags = 0;
-#pragma unroll
-    for (int i = 0; i < kSortIpt; i++) {
-        int64_t p = p0 + i;
-        if (p < n) {
-            uint32_t kk = keys[p], vv = vals[p];
-            if (kk != pk || vv != pv) {
-                flags |= 1u << i;
-                c++;
-            }
-            pk = kk;
-            pv = vv;
-        }
-    }
-    return c;
+    kk = keys[p];
+    vv = vals[p];
+    return p == 0 || kk != keys[p - 1] || vv != vals[p - 1];
 }
 
 __global__ void __launch_bounds__(kSortThreads)
@@ -212,10 +240,18 @@ __global__ void __launch_bounds__(kSortThreads)
                 uint32_t* __restrict__ tile_heads)
 {
     __shared__ uint32_t buf[33];
-    const int64_t p0 = (int64_t)blockIdx.x * kSortTile + threadIdx.x * kSortIpt;
-    uint32_t flags = 0, c = 0;
-    if (p0 < n)
-        c = heads_in_chunk(keys, vals, n, p0, flags);
+    const int lane = threadIdx.x & 31;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    uint32_t c = 0;
+#pragma unroll 4
+    for (int i = 0; i < kSortIpt; i++) {
+        const int64_t p = base + i * kSortThreads + threadIdx.x;
+        uint32_t kk, vv;
+        const bool h = p < n && is_head(keys, vals, p, kk, vv);
+        const uint32_t bal = __ballot_sync(0xffffffffu, h);
+        if (lane == 0)
+            c += __popc(bal);
+    }
     uint32_t tot;
     block_exclusive_sum(c, buf, &tot);
     if (threadIdx.x == 0)
@@ -230,21 +266,38 @@ __global__ void __launch_bounds__(kSortThreads)
                int32_t* __restrict__ run_pos, int32_t* __restrict__ run_term,
                int32_t* __restrict__ indices)
 {
+    __shared__ uint32_t seg_cnt[kSortIpt * kSortWarps];
     __shared__ uint32_t buf[33];
-    const int64_t p0 = (int64_t)blockIdx.x * kSortTile + threadIdx.x * kSortIpt;
-    uint32_t flags = 0, c = 0;
-    if (p0 < n)
-        c = heads_in_chunk(keys, vals, n, p0, flags);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    uint32_t kk[kSortIpt], vv[kSortIpt], bals[kSortIpt];
+#pragma unroll
+    for (int i = 0; i < kSortIpt; i++) {
+        const int64_t p = base + i * kSortThreads + threadIdx.x;
+        const bool h = p < n && is_head(keys, vals, p, kk[i], vv[i]);
+        bals[i] = __ballot_sync(0xffffffffu, h);
+        if (lane == 0)
+            seg_cnt[i * kSortWarps + warp] = __popc(bals[i]);
+    }
+    __syncthreads();
+    // exclusive scan of the 128 (round, warp) counts in (round, warp) order
+    const uint32_t c = (threadIdx.x < kSortIpt * kSortWarps) ? seg_cnt[threadIdx.x] : 0u;
     uint32_t tot;
-    uint32_t j = block_exclusive_sum(c, buf, &tot) + tile_off[blockIdx.x];
-    while (flags) {
-        int i = __ffs(flags) - 1;
-        flags &= flags - 1;
-        int64_t p = p0 + i;
-        run_pos[j] = (int32_t)p;
-        run_term[j] = (int32_t)keys[p];
-        indices[j] = (int32_t)vals[p];
-        j++;
+    const uint32_t ex = block_exclusive_sum(c, buf, &tot);
+    if (threadIdx.x < kSortIpt * kSortWarps)
+        seg_cnt[threadIdx.x] = ex;
+    __syncthreads();
+    const uint32_t t0 = tile_off[blockIdx.x];
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int i = 0; i < kSortIpt; i++) {
+        if (bals[i] & (1u << lane)) {
+            const int64_t p = base + i * kSortThreads + threadIdx.x;
+            const uint32_t j = t0 + seg_cnt[i * kSortWarps + warp] + __popc(bals[i] & lt);
+            run_pos[j] = (int32_t)p;
+            run_term[j] = (int32_t)kk[i];
+            indices[j] = (int32_t)vv[i];
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0)
         run_pos[*d_nnz] = (int32_t)n;
@@ -531,7 +584,7 @@ int build_index_device(const int32_t* d_tokens, int64_t n_tokens, const int64_t*
 
             ProfileScope ps_("k_doc_prep", s);
 
-            k_doc_prep<<<grid_for(n_docs * 32, 256, max_blocks), 256, 0, s>>>(
+            k_doc_prep<<<grid_for(n_docs, 256, max_blocks), 256, 0, s>>>(
                 d_offsets, n_docs, T, tok_doc, ix->doc_len, len_factor, variant, k1, b, lavg,
                 ix->status);
 
