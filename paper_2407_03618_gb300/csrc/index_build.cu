@@ -77,16 +77,19 @@ __global__ void k_doc_prep(const int64_t* __restrict__ off, int64_t n_docs, int6
             last = 31 - __clz(has_mask);
         }
         const int64_t end = __shfl_sync(0xffffffffu, hi, last);
-        for (int64_t p = start + lane; p < end; p += 32) {
+        // warp-uniform loop: every lane runs every step's shuffles
+        for (int64_t pb = start; pb < end; pb += 32) {
+            const int64_t p = pb + lane;
             // the last lane whose document starts at or before p
             int idx = 0;
 #pragma unroll
             for (int step = 16; step > 0; step >>= 1) {
-                const int64_t s_lo = __shfl_sync(0xffffffffu, lo, idx + step);
+                const int64_t s_lo = __shfl_sync(0xffffffffu, lo, (idx + step) & 31);
                 if (idx + step <= last && s_lo <= p)
                     idx += step;
             }
-            tok_doc[p] = (int32_t)((g << 5) + idx);
+            if (p < end)
+                tok_doc[p] = (int32_t)((g << 5) + idx);
         }
     }
 }
