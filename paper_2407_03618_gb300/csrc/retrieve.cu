@@ -570,12 +570,15 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
                             b = mid;
                     }
                 }
+                // runs this warp owns in this round (warp-uniform)
+                const int32_t n_runs = (total + 31) >> 5;
+                const int32_t u_max = (n_runs - r0 + WARPS - 1) / WARPS;
 #pragma unroll
                 for (int u = 0; u < U; u++) {
                     const int32_t r = r0 + u * WARPS;
                     const int32_t e = r * 32 + lane;
                     dd[u] = -1;
-                    if (e < total) {
+                    if (u < u_max && e < total) {
                         while (ts.pre[a + 1] <= e)
                             a++;
                         const int32_t j = ts.lo[a] + (e - ts.pre[a]);
@@ -585,10 +588,12 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
                 }
 #pragma unroll
                 for (int u = 0; u < U; u++) {
-                    if ((uint32_t)dd[u] < (uint32_t)wd)  // holds for any well-formed index
-                        atomicAdd(&acc[dd[u]], vv[u]);   // result unused: a reduction
-                    else
-                        dd[u] = -1;
+                    if (u < u_max) {
+                        if ((uint32_t)dd[u] < (uint32_t)wd)  // holds for any well-formed index
+                            atomicAdd(&acc[dd[u]], vv[u]);   // result unused: a reduction
+                        else
+                            dd[u] = -1;
+                    }
                 }
             }
             __syncthreads();
@@ -624,20 +629,26 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
             // ---- claim each posting's document once; keep the candidates ---------
             const uint32_t mark = zero_counts ? kMarked : kUntouched;
             uint32_t pos = 0, kmin = 0xffffffffu, kmax = 0u, n_keep = 0;
+            // slots this warp filled in the single round (warp-uniform)
+            const int32_t u_max = (((ts.pre[kTokChunk] + 31) >> 5) - warp + WARPS - 1) / WARPS;
             float cv[U];  // all exchanges first, so their latencies overlap
 #pragma unroll
             for (int u = 0; u < U; u++)
-                cv[u] = dd[u] >= 0 ? atomicExch(&acc[dd[u]], __uint_as_float(mark))
-                                   : __uint_as_float(kUntouched);
+                cv[u] = (u < u_max && dd[u] >= 0)
+                            ? atomicExch(&acc[dd[u]], __uint_as_float(mark))
+                            : __uint_as_float(kUntouched);
 #pragma unroll
             for (int u = 0; u < U; u++) {
+                if (u >= u_max)
+                    break;
                 bool keep = false;
                 const float v = cv[u];
                 const uint32_t vb = __float_as_uint(v);
                 uint32_t o = 0;
                 if (vb != kUntouched && vb != kMarked) {  // the first claim of the document
                     o = order_f32(v);
-                    pos += (v > 0.0f);
+                    if (zero_counts)
+                        pos += (v > 0.0f);
                     keep = o >= tau;
                 }
                 const uint32_t bal = __ballot_sync(0xffffffffu, keep);
