@@ -60,14 +60,28 @@ enum bm25_status {
     BM25_E_TOKEN_RANGE = -2, /* a token id outside [0, vocab) or malformed offsets */
     BM25_E_OOM = -3,         /* device allocation failed */
     BM25_E_CUDA = -4,        /* a CUDA runtime call failed */
-    BM25_E_TIMEOUT = -5      /* a bounded device-side wait gave up */
+    BM25_E_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+    BM25_PENDING = 1         /* bm25_server_poll: the request has not finished yet */
 };
 
-/* Accumulator strategies for retrieval. */
+/* Accumulator strategies for retrieval.  A query's accumulator is chosen by
+ * the number of postings in its columns (sum of DF over its tokens):
+ *   SMEM_TILED  every query on the doc-tiled path: FP32 accumulators for one
+ *               doc tile at a time in shared memory, one work item per
+ *               (doc tile, query), a cross-tile merge.
+ *   AUTO        queries with at most dense_max_postings postings on the dense
+ *               path, the rest tiled.
+ *   L2_DENSE    as AUTO with the bound raised to at least 2^19 postings.
+ * The dense path gives each in-flight query (one CTA) a dense FP32 vector of
+ * n_docs accumulators in device memory; only the sectors the query touches
+ * are brought in, and they stay in L2 while it runs.  It allocates
+ * min(2 * SMs, 2 GiB / (4 n_docs)) such vectors per workspace and is off
+ * when none fits. */
 enum bm25_accumulator {
-    BM25_ACC_AUTO = 0,       /* pick per query batch (autotuned plan if one is set) */
-    BM25_ACC_SMEM_TILED = 1, /* doc-tiled FP32 accumulators in shared memory */
-    BM25_ACC_L2_DENSE = 2    /* one dense FP32 vector per in-flight query, L2-resident */
+    BM25_ACC_UNSET = 0,      /* in a plan being set or passed: keep the current choice */
+    BM25_ACC_AUTO = 1,
+    BM25_ACC_SMEM_TILED = 2,
+    BM25_ACC_L2_DENSE = 3
 };
 
 /* Upper bound on min(k, n_docs) for one retrieval call. */
@@ -77,10 +91,11 @@ enum bm25_accumulator {
  * (beyond the order of FP32 additions); only speed does.  Zero fields take
  * the library's defaults. */
 typedef struct bm25_plan {
-    int32_t accumulator;   /* enum bm25_accumulator */
-    int32_t tile_docs;     /* doc-tile width: a multiple of 1024 in [1024, 49152] */
-    int32_t block_threads; /* threads per CTA of the tiled kernel: 128, 256 or 512 */
-    int32_t reserved;      /* must be 0 */
+    int32_t accumulator;        /* enum bm25_accumulator */
+    int32_t tile_docs;          /* doc-tile width: a multiple of 1024 in [1024, 49152] */
+    int32_t block_threads;      /* threads per CTA of the tiled kernel: 128, 256 or 512 */
+    int32_t dense_max_postings; /* dense-path bound for AUTO / L2_DENSE, in [0, 2^22]
+                                   (default 8192) */
 } bm25_plan;
 
 /* ------------------------------------------------------------------ index */
@@ -188,14 +203,25 @@ int bm25_retrieve_host(const bm25_index* index, const int32_t* query_tokens,
                        const int64_t* query_offsets, int32_t n_queries, int32_t k,
                        int32_t* out_ids, float* out_scores, void* cuda_stream);
 
-/* A workspace holds the scratch memory of retrieval.  Sized for at most
- * max_queries queries, max_query_tokens tokens in total and k' <= max_k; a
- * call within those limits allocates nothing (and can be captured in a CUDA
- * graph).  One workspace serves one call at a time. */
+/* A workspace holds the scratch memory of retrieval and grows on demand.
+ * bm25_workspace_create sizes it for a call of max_queries queries,
+ * max_query_tokens tokens and k_max = max_k under the index's current plan
+ * (synchronous).  One workspace serves one call at a time; calls with
+ * different workspaces may overlap on the device. */
 int bm25_workspace_create(const bm25_index* index, int32_t max_queries,
                           int64_t max_query_tokens, int32_t max_k,
                           bm25_workspace** out);
 void bm25_workspace_free(bm25_workspace* ws);
+
+/* Grows `ws` to what one call with these sizes and this plan (HOST pointer;
+ * NULL = the index's plan) needs, so that the call itself allocates nothing:
+ * do this before capturing the call in a CUDA graph.  A call made during
+ * stream capture that would need to grow the workspace fails with
+ * BM25_E_INVALID instead.  May enqueue an initialisation kernel on
+ * `cuda_stream`. */
+int bm25_workspace_reserve(bm25_workspace* ws, const bm25_index* index,
+                           int32_t n_queries, int64_t n_query_tokens, int32_t k_max,
+                           const bm25_plan* plan, void* cuda_stream);
 
 /* bm25_retrieve with an explicit workspace and plan (HOST pointer; NULL =
  * the index's plan).  Calls with different workspaces may overlap on the
@@ -206,6 +232,24 @@ int bm25_retrieve_ws(const bm25_index* index, bm25_workspace* ws,
                      int32_t* out_ids, float* out_scores, const bm25_plan* plan,
                      void* cuda_stream);
 
+/* The general form of bm25_retrieve: queries with different k in one call,
+ * an explicit workspace (NULL = the index's default) and plan (HOST pointer,
+ * NULL = the index's plan).
+ *   query_k[n_queries]  int32, device, each in [1, k_max]; NULL = k_max for
+ *                       every query.  An entry outside that range records
+ *                       BM25_E_INVALID in the status word and is clamped.
+ *   out_ids / out_scores  [n_queries * k_max], device; row q is k_max wide and
+ *                       holds query q's min(k_q, n_docs) results, then -1 /
+ *                       -inf.
+ * Other arguments, results and errors as in bm25_retrieve.  The batch runs
+ * in one pass per sub-batch (queries are split only when the tiled path's
+ * candidate buffer would exceed 2 GiB). */
+int bm25_retrieve_batch(const bm25_index* index, bm25_workspace* ws,
+                        const int32_t* query_tokens, int64_t n_query_tokens,
+                        const int64_t* query_offsets, int32_t n_queries,
+                        const int32_t* query_k, int32_t k_max, int32_t* out_ids,
+                        float* out_scores, const bm25_plan* plan, void* cuda_stream);
+
 /* Retrieval that allocates nothing, for callers that cannot call cudaMalloc
  * at this point: code running where a device allocation would synchronise
  * the device or is not allowed (a host callback, a real-time serving loop
@@ -215,10 +259,11 @@ int bm25_retrieve_ws(const bm25_index* index, bm25_workspace* ws,
  * FP32 additions).
  *
  * Its scratch is one file-scope device array of 16 MiB that every GPU
- * loading the library holds until the process exits.  A batch whose scratch
- * (16 bytes per query, 4 per query token and doc-tile boundary,
- * 4 per query and doc tile, 8 per query, doc tile and k' candidate slot)
- * exceeds 16 MiB fails with BM25_E_INVALID; split it.  The first call on a
+ * loading the library holds until the process exits.  Every query takes the
+ * doc-tiled path.  A batch whose scratch (about 40 bytes per query, 4 per
+ * query token and doc-tile boundary, 4 per query and doc tile, 8 per query,
+ * doc tile and k' candidate slot) exceeds 16 MiB fails with BM25_E_INVALID;
+ * split it.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress), so
  * make that first call before any stream capture.  Every call shares the
  * array: calls that overlap on the GPU (other streams, other threads) race
@@ -233,6 +278,79 @@ int bm25_retrieve_noalloc(const bm25_index* index, const int32_t* query_tokens,
  * BM25_E_INVALID and changes nothing. */
 int bm25_index_set_plan(bm25_index* index, const bm25_plan* plan);
 int bm25_index_get_plan(const bm25_index* index, bm25_plan* plan);
+
+/* Times retrieval of a sample batch (device arrays, as in bm25_retrieve,
+ * with one k for all queries) under candidate plans and makes the fastest
+ * the index's plan.  Candidates: tile widths 8192, 12288 and 16384 with
+ * every query tiled, then, with the best width, dense-path bounds of 2048 ..
+ * 32768 postings (the accumulator per query-length bucket).  Each candidate
+ * runs once untimed and twice timed (CUDA events on `cuda_stream`); the best
+ * of the two counts.  Synchronous; allocates its own scratch.  Results of
+ * retrieval do not depend on the plan.
+ *   best                 the chosen plan (HOST); best_ms its time (may be NULL).
+ *   tried / tried_ms     optional HOST arrays of tried_cap entries: every
+ *                        candidate timed, in order; *n_tried their number. */
+int bm25_autotune(bm25_index* index, const int32_t* query_tokens, int64_t n_query_tokens,
+                  const int64_t* query_offsets, int32_t n_queries, int32_t k,
+                  void* cuda_stream, bm25_plan* best, double* best_ms, bm25_plan* tried,
+                  double* tried_ms, int32_t tried_cap, int32_t* n_tried);
+
+/* ---------------------------------------------------------------- serving */
+
+/* A request loop over resident indexes with continuous batching (the paper
+ * has no serving layer; this is the batched path of Sec. 2 run as requests
+ * arrive).  Each request is one query (HOST tokens) against one index with
+ * its own k.  A worker thread keeps up to max_inflight batches on the device
+ * at once, each on its own stream and workspace; whenever one completes, the
+ * requests that arrived meanwhile are batched per index (oldest first, up to
+ * max_batch_queries) and admitted if the scratch of all running batches
+ * stays within memory_budget (else a smaller batch, or after a running batch
+ * completes).  A request's result does not depend on the batch it ran in
+ * beyond the order of FP32 additions.  Each index's plan is used as set
+ * (bm25_index_set_plan / bm25_autotune); the indexes must outlive the server
+ * and must not be freed or re-planned while it runs. */
+typedef struct bm25_server bm25_server;
+
+typedef struct bm25_server_config {  /* zero fields take the defaults */
+    int32_t max_batch_queries;  /* queries per batch (2048) */
+    int32_t max_inflight;       /* batches on the device at once, <= 16 (3) */
+    int32_t k_max;              /* largest k a request may ask for, <= BM25_MAX_K (1000) */
+    int32_t reserved;           /* 0 */
+    int64_t memory_budget;      /* device scratch bytes all batches may hold (4 GiB) */
+} bm25_server_config;
+
+typedef struct bm25_server_stats {
+    int64_t completed, failed;  /* requests */
+    int64_t batches, batched_queries;
+    double p50_us, p99_us, max_us;  /* submit-to-result latency of completed requests */
+    int64_t bytes_held;         /* device scratch the server holds now */
+} bm25_server_stats;
+
+/* Starts the worker thread.  indexes[n_indexes] live on the current device;
+ * request index ids are positions in this array.  cfg may be NULL. */
+int bm25_server_create(const bm25_index* const* indexes, int32_t n_indexes,
+                       const bm25_server_config* cfg, bm25_server** out);
+
+/* Queues one query: tokens[n_tokens] in HOST memory (copied; n_tokens may be
+ * 0), checked against the index's vocabulary here (BM25_E_TOKEN_RANGE), and
+ * 1 <= k <= k_max.  *ticket identifies the request in bm25_server_poll. */
+int bm25_server_submit(bm25_server* server, int32_t index_id, const int32_t* tokens,
+                       int32_t n_tokens, int32_t k, int64_t* ticket);
+
+/* Waits up to timeout_us microseconds (0: do not wait, < 0: no limit) for a
+ * request.  BM25_PENDING: not finished (poll again).  BM25_OK: ids[k] and
+ * scores[k] (HOST, may be NULL) hold its row as bm25_retrieve would return
+ * it, and the ticket is released.  A failed request returns its error code
+ * once and releases the ticket. */
+int bm25_server_poll(bm25_server* server, int64_t ticket, int32_t* ids, float* scores,
+                     int32_t timeout_us);
+
+/* Counters and latency percentiles since the last reset (reset != 0 clears them). */
+int bm25_server_stats_get(bm25_server* server, int reset, bm25_server_stats* out);
+
+/* Stops accepting requests, lets running batches finish, fails queued
+ * requests, joins the worker and frees the server's device memory. */
+void bm25_server_destroy(bm25_server* server);
 
 /* --------------------------------------------------------------- utility */
 

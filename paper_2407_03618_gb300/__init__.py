@@ -6,8 +6,8 @@ Python binding and ``synth`` the seeded synthetic corpora used by the tests
 and the benchmark.
 """
 from . import build_ext, synth  # noqa: F401
-from .bm25 import (ACC_AUTO, ACC_L2_DENSE, ACC_SMEM_TILED, MAX_K, VARIANTS, BM25Error,  # noqa: F401
-                   Index, Plan, Workspace, launch_count, load)
+from .bm25 import (ACC_AUTO, ACC_L2_DENSE, ACC_SMEM_TILED, ACC_UNSET, MAX_K, VARIANTS,  # noqa: F401
+                   BM25Error, Index, Plan, Server, Workspace, launch_count, load)
 
-__all__ = ["Index", "Plan", "Workspace", "BM25Error", "VARIANTS", "MAX_K", "ACC_AUTO", "ACC_SMEM_TILED",
+__all__ = ["Index", "Plan", "Server", "Workspace", "ACC_UNSET", "BM25Error", "VARIANTS", "MAX_K", "ACC_AUTO", "ACC_SMEM_TILED",
            "ACC_L2_DENSE", "load", "launch_count", "synth", "build_ext"]

@@ -17,20 +17,36 @@ import numpy as np
 from . import build_ext
 
 VARIANTS = {"lucene": 0, "robertson": 1, "atire": 2, "bm25l": 3, "bm25+": 4}
-ACC_AUTO, ACC_SMEM_TILED, ACC_L2_DENSE = 0, 1, 2
+ACC_UNSET, ACC_AUTO, ACC_SMEM_TILED, ACC_L2_DENSE = 0, 1, 2, 3
 STATUS = {0: "BM25_OK", -1: "BM25_E_INVALID", -2: "BM25_E_TOKEN_RANGE", -3: "BM25_E_OOM",
-          -4: "BM25_E_CUDA", -5: "BM25_E_TIMEOUT"}
+          -4: "BM25_E_CUDA", -5: "BM25_E_TIMEOUT", 1: "BM25_PENDING"}
+PENDING = 1
 MAX_K = 4096
 
 
 class Plan(ctypes.Structure):
     """bm25_plan: how retrieval runs (zero fields = library defaults)."""
     _fields_ = [("accumulator", ctypes.c_int32), ("tile_docs", ctypes.c_int32),
-                ("block_threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("block_threads", ctypes.c_int32), ("dense_max_postings", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {"accumulator": self.accumulator, "tile_docs": self.tile_docs,
-                "block_threads": self.block_threads}
+                "block_threads": self.block_threads,
+                "dense_max_postings": self.dense_max_postings}
+
+
+class ServerConfig(ctypes.Structure):
+    """bm25_server_config (zero fields = defaults)."""
+    _fields_ = [("max_batch_queries", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
+                ("k_max", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("memory_budget", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("batched_queries", ctypes.c_int64),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
+                ("max_us", ctypes.c_double), ("bytes_held", ctypes.c_int64)]
 
 
 class BM25Error(RuntimeError):
@@ -78,6 +94,14 @@ def load(path: str | None = None):
         "bm25_workspace_create": (cint, [P, i32, i64, i32, PP]),
         "bm25_workspace_free": (None, [P]),
         "bm25_retrieve_ws": (cint, [P, P, P, i64, P, i32, i32, P, P, P, P]),
+        "bm25_retrieve_batch": (cint, [P, P, P, i64, P, i32, P, i32, P, P, P, P]),
+        "bm25_workspace_reserve": (cint, [P, P, i32, i64, i32, P, P]),
+        "bm25_autotune": (cint, [P, P, i64, P, i32, i32, P, P, P, P, P, i32, P]),
+        "bm25_server_create": (cint, [P, i32, P, PP]),
+        "bm25_server_submit": (cint, [P, i32, P, i32, i32, P]),
+        "bm25_server_poll": (cint, [P, i64, P, P, i32]),
+        "bm25_server_stats_get": (cint, [P, cint, P]),
+        "bm25_server_destroy": (None, [P]),
         "bm25_index_set_plan": (cint, [P, P]),
         "bm25_index_get_plan": (cint, [P, P]),
         "bm25_last_error": (ctypes.c_char_p, []),
@@ -155,6 +179,14 @@ class Workspace:
         _check(load().bm25_workspace_create(index.handle, max_queries, max_query_tokens, max_k,
                                             ctypes.byref(h)))
         self.handle = h
+
+    def reserve(self, index: "Index", n_queries: int, n_query_tokens: int, k_max: int,
+                plan: dict | None = None, stream=None):
+        """Grow to what one such call needs (do this before graph capture)."""
+        p = Plan(**(plan or {}))
+        _check(load().bm25_workspace_reserve(self.handle, index.handle, n_queries,
+                                             n_query_tokens, k_max, ctypes.byref(p),
+                                             _stream(stream)))
 
     def close(self):
         if self.handle:
@@ -245,9 +277,28 @@ class Index:
         out.update(inf)
         return out
 
-    def set_plan(self, accumulator: int = ACC_AUTO, tile_docs: int = 0, block_threads: int = 0):
-        p = Plan(accumulator, tile_docs, block_threads, 0)
+    def set_plan(self, accumulator: int = ACC_UNSET, tile_docs: int = 0, block_threads: int = 0,
+                 dense_max_postings: int = 0):
+        p = Plan(accumulator, tile_docs, block_threads, dense_max_postings)
         _check(load().bm25_index_set_plan(self.handle, ctypes.byref(p)))
+
+    def autotune(self, q_tokens, q_offsets, k: int, stream=None):
+        """Time candidate plans on a sample batch (CUDA tensors) and keep the
+        fastest.  Returns (best plan dict, best ms, [(plan dict, ms), ...])."""
+        import torch
+        qt = _dev_tensor(q_tokens, torch.int32)
+        qo = _dev_tensor(q_offsets, torch.int64)
+        best, best_ms = Plan(), ctypes.c_double()
+        cap = 32
+        tried = (Plan * cap)()
+        tried_ms = (ctypes.c_double * cap)()
+        n = ctypes.c_int32()
+        _check(load().bm25_autotune(self.handle, qt.data_ptr(), qt.numel(), qo.data_ptr(),
+                                    qo.numel() - 1, k, _stream(stream), ctypes.byref(best),
+                                    ctypes.byref(best_ms), tried, tried_ms, cap,
+                                    ctypes.byref(n)))
+        log = [(tried[i].as_dict(), tried_ms[i]) for i in range(min(n.value, cap))]
+        return best.as_dict(), best_ms.value, log
 
     def get_plan(self) -> dict:
         p = Plan()
@@ -280,6 +331,29 @@ class Index:
             _check(load().bm25_retrieve_ws(self.handle, workspace.handle, qt.data_ptr(),
                                            qt.numel(), qo.data_ptr(), nq, k, ids.data_ptr(),
                                            sc.data_ptr(), ctypes.byref(p), _stream(stream)))
+        return ids, sc
+
+    def retrieve_batch(self, q_tokens, q_offsets, k_max: int, q_k=None, out=None, stream=None,
+                       workspace: Workspace | None = None, plan: dict | None = None):
+        """Queries with different k in one call: q_k CUDA int32 [nQ] (None =
+        k_max for all).  Returns (ids, scores) [nQ, k_max]; row q holds
+        min(q_k[q], N) results, then -1 / -inf."""
+        import torch
+        qt = _dev_tensor(q_tokens, torch.int32)
+        qo = _dev_tensor(q_offsets, torch.int64)
+        nq = qo.numel() - 1
+        qk = _dev_tensor(q_k, torch.int32) if q_k is not None else None
+        if out is None:
+            ids = torch.empty((nq, max(k_max, 0)), dtype=torch.int32, device=qo.device)
+            sc = torch.empty((nq, max(k_max, 0)), dtype=torch.float32, device=qo.device)
+        else:
+            ids, sc = out
+        p = Plan(**(plan or {}))
+        _check(load().bm25_retrieve_batch(self.handle, workspace.handle if workspace else None,
+                                          qt.data_ptr(), qt.numel(), qo.data_ptr(), nq,
+                                          qk.data_ptr() if qk is not None else None, k_max,
+                                          ids.data_ptr(), sc.data_ptr(), ctypes.byref(p),
+                                          _stream(stream)))
         return ids, sc
 
     def _default_workspace(self, nq, ntok, k):
@@ -337,3 +411,50 @@ def _hptr(x):
 
 def _hlen(x) -> int:
     return int(x.shape[0]) if isinstance(x, np.ndarray) else int(x.numel())
+
+
+class Server:
+    """Continuous-batching request loop over resident indexes (a worker
+    thread inside the library; queries and results in host memory)."""
+
+    def __init__(self, indexes: list, max_batch_queries: int = 0, max_inflight: int = 0,
+                 k_max: int = 0, memory_budget: int = 0):
+        self._indexes = list(indexes)  # kept alive while the server runs
+        arr = (ctypes.c_void_p * len(indexes))(*[ix.handle.value for ix in indexes])
+        cfg = ServerConfig(max_batch_queries, max_inflight, k_max, 0, memory_budget)
+        h = ctypes.c_void_p()
+        _check(load().bm25_server_create(arr, len(indexes), ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+
+    def submit(self, index_id: int, tokens, k: int) -> int:
+        t = _np(tokens, np.int32)
+        ticket = ctypes.c_int64()
+        _check(load().bm25_server_submit(self.handle, index_id, _ptr(t), int(t.shape[0]), k,
+                                         ctypes.byref(ticket)))
+        return ticket.value
+
+    def poll(self, ticket: int, k: int, timeout_us: int = -1):
+        """(ids, scores) numpy arrays of length k, or None while pending."""
+        ids = np.zeros(k, np.int32)
+        sc = np.zeros(k, np.float32)
+        rc = load().bm25_server_poll(self.handle, ticket, _ptr(ids), _ptr(sc), timeout_us)
+        if rc == PENDING:
+            return None
+        _check(rc)
+        return ids, sc
+
+    def stats(self, reset: bool = False) -> dict:
+        st = ServerStats()
+        _check(load().bm25_server_stats_get(self.handle, int(reset), ctypes.byref(st)))
+        return {n: getattr(st, n) for n, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.handle:
+            load().bm25_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -121,9 +121,10 @@ int merge_plan(const bm25_plan* in, const Plan& base, Plan* out)
 {
     Plan p = base;
     if (in) {
-        if (in->reserved != 0)
-            return set_error(BM25_E_INVALID, "bm25_plan.reserved must be 0");
-        if (in->accumulator < BM25_ACC_AUTO || in->accumulator > BM25_ACC_L2_DENSE)
+        if (in->dense_max_postings < 0 || in->dense_max_postings > (1 << 22))
+            return set_error(BM25_E_INVALID, "dense_max_postings %d must be in [0, 2^22]",
+                             in->dense_max_postings);
+        if (in->accumulator < BM25_ACC_UNSET || in->accumulator > BM25_ACC_L2_DENSE)
             return set_error(BM25_E_INVALID, "unknown accumulator %d", in->accumulator);
         if (in->tile_docs != 0 &&
             (in->tile_docs < 1024 || in->tile_docs > 49152 || in->tile_docs % 1024))
@@ -140,6 +141,8 @@ int merge_plan(const bm25_plan* in, const Plan& base, Plan* out)
             p.tile_docs = in->tile_docs;
         if (in->block_threads)
             p.threads = in->block_threads;
+        if (in->dense_max_postings)
+            p.dense_max = in->dense_max_postings;
     }
     *out = p;
     return BM25_OK;
@@ -361,14 +364,12 @@ int bm25_workspace_create(const bm25_index* ix, int32_t max_queries, int64_t max
     *out = nullptr;
     if (max_queries < 1 || max_query_tokens < 0 || max_k < 1)
         return set_error(BM25_E_INVALID, "bad workspace limits");
-    int32_t kp = (int32_t)(max_k < ix->n_docs ? max_k : ix->n_docs);
-    if (kp > BM25_MAX_K)
-        return set_error(BM25_E_INVALID, "max_k beyond BM25_MAX_K");
+    BM25_TRY(check_retrieve_args(ix, max_query_tokens, max_queries, max_k));
     bm25_workspace* ws = new bm25_workspace();
     ws->device = ix->device;
-    // sized for the smallest doc tile the library uses (1024 documents)
-    int64_t tiles = (ix->n_docs + 1023) / 1024;
-    int rc = workspace_reserve(ix, ws, max_queries, max_query_tokens, kp, tiles);
+    int rc = workspace_reserve_for(ix, ws, max_queries, max_query_tokens, max_k, plan_of(ix), 0);
+    if (rc == BM25_OK && cudaStreamSynchronize(0) != cudaSuccess)
+        rc = set_error(BM25_E_CUDA, "synchronisation failed");
     if (rc != BM25_OK) {
         workspace_release(ws);
         delete ws;
@@ -376,6 +377,22 @@ int bm25_workspace_create(const bm25_index* ix, int32_t max_queries, int64_t max
     }
     *out = ws;
     return BM25_OK;
+}
+
+int bm25_workspace_reserve(bm25_workspace* ws, const bm25_index* ix, int32_t n_queries,
+                           int64_t n_query_tokens, int32_t k_max, const bm25_plan* plan,
+                           void* cuda_stream)
+{
+    clear_error();
+    if (!ws)
+        return set_error(BM25_E_INVALID, "workspace is NULL");
+    BM25_TRY(check_retrieve_args(ix, n_query_tokens, n_queries, k_max));
+    if (ws->device != ix->device)
+        return set_error(BM25_E_INVALID, "workspace and index are on different devices");
+    Plan p;
+    BM25_TRY(merge_plan(plan, plan_of(ix), &p));
+    return workspace_reserve_for(ix, ws, n_queries, n_query_tokens, k_max, p,
+                                 (cudaStream_t)cuda_stream);
 }
 
 void bm25_workspace_free(bm25_workspace* ws)
@@ -394,8 +411,9 @@ int bm25_retrieve(const bm25_index* ix, const int32_t* query_tokens, int64_t n_q
     BM25_TRY(check_retrieve_args(ix, n_query_tokens, n_queries, k));
     bm25_workspace* ws = nullptr;
     BM25_TRY(default_ws(ix, &ws));
-    return retrieve_device(ix, ws, query_tokens, query_offsets, n_queries, n_query_tokens, k,
-                           out_ids, out_scores, plan_of(ix), (cudaStream_t)cuda_stream);
+    return retrieve_device(ix, ws, query_tokens, query_offsets, n_queries, n_query_tokens,
+                           nullptr, k, out_ids, out_scores, plan_of(ix),
+                           (cudaStream_t)cuda_stream);
 }
 
 int bm25_retrieve_ws(const bm25_index* ix, bm25_workspace* ws, const int32_t* query_tokens,
@@ -409,8 +427,28 @@ int bm25_retrieve_ws(const bm25_index* ix, bm25_workspace* ws, const int32_t* qu
         return set_error(BM25_E_INVALID, "workspace is NULL");
     Plan p;
     BM25_TRY(merge_plan(plan, plan_of(ix), &p));
-    return retrieve_device(ix, ws, query_tokens, query_offsets, n_queries, n_query_tokens, k,
-                           out_ids, out_scores, p, (cudaStream_t)cuda_stream);
+    return retrieve_device(ix, ws, query_tokens, query_offsets, n_queries, n_query_tokens,
+                           nullptr, k, out_ids, out_scores, p, (cudaStream_t)cuda_stream);
+}
+
+int bm25_retrieve_batch(const bm25_index* ix, bm25_workspace* ws, const int32_t* query_tokens,
+                        int64_t n_query_tokens, const int64_t* query_offsets, int32_t n_queries,
+                        const int32_t* query_k, int32_t k_max, int32_t* out_ids,
+                        float* out_scores, const bm25_plan* plan, void* cuda_stream)
+{
+    clear_error();
+    BM25_TRY(check_retrieve_args(ix, n_query_tokens, n_queries, k_max));
+    if (n_queries > 0 && (!query_offsets || !out_ids || !out_scores ||
+                          (n_query_tokens > 0 && !query_tokens)))
+        return set_error(BM25_E_INVALID, "NULL array");
+    if (!ws)
+        BM25_TRY(default_ws(ix, &ws));
+    else if (ws->device != ix->device)
+        return set_error(BM25_E_INVALID, "workspace and index are on different devices");
+    Plan p;
+    BM25_TRY(merge_plan(plan, plan_of(ix), &p));
+    return retrieve_device(ix, ws, query_tokens, query_offsets, n_queries, n_query_tokens,
+                           query_k, k_max, out_ids, out_scores, p, (cudaStream_t)cuda_stream);
 }
 
 int bm25_retrieve_host(const bm25_index* ix, const int32_t* query_tokens,
@@ -448,16 +486,16 @@ int bm25_retrieve_host(const bm25_index* ix, const int32_t* query_tokens,
     BM25_TRY(grow((void**)&ws->q_tokens, &ws->staging_cap[0], sizeof(int32_t) * (size_t)n_tok));
     BM25_TRY(grow((void**)&ws->q_offsets, &ws->staging_cap[1],
                   sizeof(int64_t) * (size_t)(n_queries + 1)));
-    BM25_TRY(grow((void**)&ws->out_ids, &ws->staging_cap[2],
+    BM25_TRY(grow((void**)&ws->out_ids, &ws->staging_cap[3],
                   sizeof(int32_t) * (size_t)n_queries * k));
-    BM25_TRY(grow((void**)&ws->out_scores, &ws->staging_cap[3],
+    BM25_TRY(grow((void**)&ws->out_scores, &ws->staging_cap[4],
                   sizeof(float) * (size_t)n_queries * k));
     if (n_tok > 0)
         BM25_CUDA_TRY(cudaMemcpyAsync(ws->q_tokens, query_tokens, sizeof(int32_t) * n_tok,
                                       cudaMemcpyHostToDevice, s));
     BM25_CUDA_TRY(cudaMemcpyAsync(ws->q_offsets, query_offsets,
                                   sizeof(int64_t) * (n_queries + 1), cudaMemcpyHostToDevice, s));
-    BM25_TRY(retrieve_device(ix, ws, ws->q_tokens, ws->q_offsets, n_queries, n_tok, k,
+    BM25_TRY(retrieve_device(ix, ws, ws->q_tokens, ws->q_offsets, n_queries, n_tok, nullptr, k,
                              ws->out_ids, ws->out_scores, plan_of(ix), s));
     BM25_CUDA_TRY(cudaMemcpyAsync(out_ids, ws->out_ids, sizeof(int32_t) * (size_t)n_queries * k,
                                   cudaMemcpyDeviceToHost, s));
@@ -489,7 +527,7 @@ int bm25_index_get_plan(const bm25_index* ix, bm25_plan* plan)
     plan->accumulator = p.accumulator;
     plan->tile_docs = p.tile_docs;
     plan->block_threads = p.threads;
-    plan->reserved = 0;
+    plan->dense_max_postings = p.dense_max;
     return BM25_OK;
 }
 

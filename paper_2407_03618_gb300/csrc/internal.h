@@ -67,6 +67,7 @@ struct Plan {
     int accumulator = BM25_ACC_AUTO;
     int32_t tile_docs = 12288;
     int32_t threads = 256;
+    int32_t dense_max = 8192;   // postings bound of the dense path (AUTO, L2_DENSE)
 };
 // Fills zero fields of `in` from `base`; BM25_E_INVALID (nothing changed) if
 // a field is out of range.
@@ -97,23 +98,35 @@ struct bm25_index {
 
 struct bm25_workspace {
     int device = 0;
-    int32_t max_queries = 0;
-    int64_t max_query_tokens = 0;
-    int32_t max_k = 0;
-    int64_t max_tiles = 0;       // doc tiles the buffers are sized for
-    // device scratch (owned)
-    int32_t* q_tokens = nullptr;     // staging for the _host entry point
-    int64_t* q_offsets = nullptr;    // staging for the _host entry point
-    int32_t* out_ids = nullptr;      // staging for the _host entry point
-    float* out_scores = nullptr;     // staging for the _host entry point
-    double* shift = nullptr;         // [max_queries]  sum_i S0(q_i)
-    uint32_t* thresh = nullptr;      // [max_queries]  running k'-th best score key
-    uint32_t* qpost = nullptr;       // [max_queries]  postings of the query's columns
-    uint32_t* tcount = nullptr;      // [n_queries * n_tiles]  candidates per (tile, query) item
-    int32_t* seg = nullptr;          // [max_query_tokens * (max_tiles + 1)]
-    unsigned long long* cand = nullptr;  // [n_queries * n_tiles * k'], k' slots per item
+    bool fixed = false;  // buffers lent by the caller: never grown, never freed
+    // per-query arrays, carved from qbuf (see bm25::carve_queries)
+    unsigned char* qbuf = nullptr;
+    size_t qbuf_cap = 0;             // bytes
+    int32_t max_queries = 0;         // queries per sub-batch the arrays hold
+    uint32_t* ctr = nullptr;         // [4] tiled count, dense count, dense queue head
+    double* shift = nullptr;         // [q]  sum_i S0(q_i)
+    int4* lrec = nullptr;            // [li] tiled-path record {q, first token, end token, k'}
+    int32_t* qkp = nullptr;          // [q]  k' = min(k_q, N)
+    uint32_t* lpost = nullptr;       // [li] postings of the query's columns
+    uint32_t* thresh = nullptr;      // [li] running k'-th best score key
+    int32_t* sq = nullptr;           // [si] dense-path queries
+    // tiled path
+    int32_t* seg = nullptr;          // [n_query_tokens * (n_tiles + 1)]
+    uint32_t* tcount = nullptr;      // [n_tiles * queries]  candidates per (tile, query) item
+    unsigned long long* cand = nullptr;  // [n_tiles * queries * kstride]
     size_t seg_cap = 0, cand_cap = 0, tcount_cap = 0;  // element capacities
-    size_t staging_cap[4] = {0, 0, 0, 0};  // byte capacities of the staging buffers
+    // dense path: one N-vector (all -0.0 between queries) and one candidate
+    // list per CTA
+    float* dslots = nullptr;
+    unsigned long long* dlists = nullptr;
+    size_t dslots_cap = 0, dlists_cap = 0;  // element capacities
+    // staging for the _host entry points
+    int32_t* q_tokens = nullptr;
+    int64_t* q_offsets = nullptr;
+    int32_t* q_k = nullptr;
+    int32_t* out_ids = nullptr;
+    float* out_scores = nullptr;
+    size_t staging_cap[5] = {0, 0, 0, 0, 0};  // bytes
     bool owns_staging = false;
 };
 
@@ -130,13 +143,29 @@ void free_index_arrays(bm25_index* ix, cudaStream_t s);
 int pool_for_current_device(cudaMemPool_t* out);
 
 // ---- retrieval (retrieve.cu) -------------------------------------------
+// q_k: per-query k (device, NULL = k_max for every query); rows of the
+// outputs are k_max wide.
 int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_tokens,
                     const int64_t* q_offsets, int32_t n_queries, int64_t n_query_tokens,
-                    int32_t k, int32_t* out_ids, float* out_scores, const Plan& plan,
-                    cudaStream_t stream);
-int workspace_reserve(const bm25_index* ix, bm25_workspace* ws, int32_t n_queries,
-                      int64_t n_query_tokens, int32_t kprime, int64_t n_tiles);
+                    const int32_t* q_k, int32_t k_max, int32_t* out_ids, float* out_scores,
+                    const Plan& plan, cudaStream_t stream);
+// Grows ws (unless fixed) to what retrieve_device needs for such a call;
+// allocates nothing when it already fits.  Fails while `stream` is being
+// captured and something would have to grow.
+int workspace_reserve_for(const bm25_index* ix, bm25_workspace* ws, int32_t n_queries,
+                          int64_t n_query_tokens, int32_t k_max, const Plan& plan,
+                          cudaStream_t stream);
 void workspace_release(bm25_workspace* ws);
+// Device bytes a workspace needs for such a call (from scratch), and the
+// bytes a workspace holds now.
+int workspace_bytes_for(const bm25_index* ix, int32_t n_queries, int64_t n_query_tokens,
+                        int32_t k_max, const Plan& plan, size_t* bytes);
+size_t workspace_bytes_held(const bm25_workspace* ws);
+// Bytes of the per-query arrays for m queries, and their carve-up of qbuf.
+size_t query_arrays_bytes(int64_t m);
+void carve_queries(bm25_workspace* ws, unsigned char* base, int32_t m);
+// The doc-tile width a plan gives for an index of n_docs documents.
+int32_t tile_width(const Plan& plan, int64_t n_docs);
 
 // ---- scan (scan.cu) ------------------------------------------------------
 // Exclusive prefix sum of n uint32 values (in and out may alias).  The total

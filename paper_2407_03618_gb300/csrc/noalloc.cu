@@ -89,21 +89,17 @@ extern "C" int bm25_retrieve_noalloc(const bm25_index* ix, const int32_t* query_
         std::lock_guard<std::mutex> g(const_cast<bm25_index*>(ix)->mu);
         plan = ix->plan;
     }
+    plan.accumulator = BM25_ACC_SMEM_TILED;  // the dense path needs vectors of N accumulators
     // the doc-tile geometry retrieve_device derives from the plan
-    int64_t W = plan.tile_docs > 0 ? plan.tile_docs : 12288;
-    const int64_t w_need = (N + 127) / 128 * 128;
-    if (W > w_need)
-        W = w_need;
+    const int64_t W = tile_width(plan, N);
     const int64_t n_tiles = (N + W - 1) / W;
 
-    const size_t b_shift = align_up(sizeof(double) * (size_t)n_queries);
-    const size_t b_thresh = align_up(sizeof(uint32_t) * (size_t)n_queries);
-    const size_t b_qpost = align_up(sizeof(uint32_t) * (size_t)n_queries);
+    const size_t b_q = align_up(query_arrays_bytes(n_queries));
     const size_t b_seg = align_up(sizeof(int32_t) * (size_t)n_query_tokens * (size_t)(n_tiles + 1));
     const size_t b_tcount = align_up(sizeof(uint32_t) * (size_t)n_queries * (size_t)n_tiles);
     const size_t b_cand =
         align_up(sizeof(unsigned long long) * (size_t)n_queries * (size_t)n_tiles * (size_t)kp);
-    const size_t need = b_shift + b_thresh + b_qpost + b_seg + b_tcount + b_cand;
+    const size_t need = b_q + b_seg + b_tcount + b_cand;
     if (need > kScratchBytes)
         return set_error(BM25_E_INVALID,
                          "this batch needs %zu bytes of scratch; bm25_retrieve_noalloc holds %zu "
@@ -117,22 +113,18 @@ extern "C" int bm25_retrieve_noalloc(const bm25_index* ix, const int32_t* query_
     // match this call exactly, so retrieve_device finds nothing to grow.
     bm25_workspace ws;
     ws.device = dev;
-    ws.shift = reinterpret_cast<double*>(p);
-    ws.thresh = reinterpret_cast<uint32_t*>(p + b_shift);
-    ws.qpost = reinterpret_cast<uint32_t*>(p + b_shift + b_thresh);
-    ws.max_queries = n_queries;
-    p += b_shift + b_thresh + b_qpost;
+    ws.fixed = true;
+    carve_queries(&ws, p, n_queries);
+    p += b_q;
     ws.seg = reinterpret_cast<int32_t*>(p);
     ws.seg_cap = (size_t)n_query_tokens * (size_t)(n_tiles + 1);
     ws.tcount = reinterpret_cast<uint32_t*>(p + b_seg);
     ws.tcount_cap = (size_t)n_queries * (size_t)n_tiles;
     ws.cand = reinterpret_cast<unsigned long long*>(p + b_seg + b_tcount);
     ws.cand_cap = (size_t)n_queries * (size_t)n_tiles * (size_t)kp;
-    if (ws.seg_cap == 0)
-        ws.seg_cap = 1;  // an empty batch of tokens still passes a non-null buffer
     ws.owns_staging = false;
-    int rc = retrieve_device(ix, &ws, query_tokens, query_offsets, n_queries, n_query_tokens, k,
-                             out_ids, out_scores, plan, (cudaStream_t)cuda_stream);
+    int rc = retrieve_device(ix, &ws, query_tokens, query_offsets, n_queries, n_query_tokens,
+                             nullptr, k, out_ids, out_scores, plan, (cudaStream_t)cuda_stream);
     // the slices belong to the array: nothing is released
     return rc;
 }

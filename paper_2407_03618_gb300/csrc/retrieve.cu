@@ -36,35 +36,81 @@ constexpr int kMergeBufCap = 4096;     // candidates a merge gathers into shared
 constexpr uint32_t kZeroKey = 0x80000000u;  // order_f32(0.0f)
 
 // ---- R0 ---------------------------------------------------------------------
+// Per query: checks its token range (clamped where malformed), sum_i S0(q_i)
+// in FP64, k' = min(k_q, N), and the postings of its columns (an upper bound
+// on the documents it touches).  Queries with at most dense_max postings go
+// to the list of the dense path (sq, count in ctr[1]); the others get a
+// record {q, first token, end token, k'} on the list of the tiled path
+// (lrec / lpost / thresh, count in ctr[0]), with their running threshold
+// reset.  List order follows the atomic appends; results do not depend on it.
 __global__ void k_query_prep(const int32_t* __restrict__ q_tokens, int64_t n_tok,
-                             const int64_t* __restrict__ q_off, int32_t nq,
-                             const double* __restrict__ s0, const int64_t* __restrict__ indptr,
-                             int32_t vocab, double* __restrict__ shift,
-                             uint32_t* __restrict__ thresh, uint32_t* __restrict__ qpost,
-                             int* status)
+                             const int64_t* __restrict__ q_off, int32_t nq, int check_first,
+                             int check_last, const int32_t* __restrict__ qk, int32_t kmax,
+                             int64_t n_docs, const double* __restrict__ s0,
+                             const int64_t* __restrict__ indptr, int32_t vocab, int64_t dense_max,
+                             double* __restrict__ shift, int32_t* __restrict__ qkp,
+                             int4* __restrict__ lrec, uint32_t* __restrict__ lpost,
+                             uint32_t* __restrict__ thresh, int32_t* __restrict__ sq,
+                             uint32_t* __restrict__ ctr, int* status)
 {
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        int64_t lo = q_off[q], hi = q_off[q + 1];
-        if (lo < 0 || hi < lo || hi > n_tok || (q == 0 && lo != 0) ||
-            (q == nq - 1 && hi != n_tok))
-            set_status(status, BM25_E_TOKEN_RANGE);
-        lo = lo < 0 ? 0 : (lo > n_tok ? n_tok : lo);
-        hi = hi < lo ? lo : (hi > n_tok ? n_tok : hi);
-        double sum = 0.0;
-        int64_t post = 0;
-        for (int64_t m = lo; m < hi; m++) {
-            int32_t t = q_tokens[m];
-            if (t < 0 || t >= vocab) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // warp-uniform loop: the list appends are aggregated per warp
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < nq;
+         base += stride) {
+        const int64_t q = base + lane;
+        const bool act = q < nq;
+        int64_t lo = 0, hi = 0, post = 0;
+        int32_t kp = 0;
+        if (act) {
+            lo = q_off[q];
+            hi = q_off[q + 1];
+            if (lo < 0 || hi < lo || hi > n_tok || (check_first && q == 0 && lo != 0) ||
+                (check_last && q == nq - 1 && hi != n_tok))
                 set_status(status, BM25_E_TOKEN_RANGE);
-                continue;
+            lo = lo < 0 ? 0 : (lo > n_tok ? n_tok : lo);
+            hi = hi < lo ? lo : (hi > n_tok ? n_tok : hi);
+            int32_t kq = qk ? qk[q] : kmax;
+            if (kq < 1 || kq > kmax) {
+                set_status(status, BM25_E_INVALID);
+                kq = kq < 1 ? 1 : kmax;
             }
-            sum += s0[t];
-            post += indptr[t + 1] - indptr[t];
+            kp = (int64_t)kq < n_docs ? kq : (int32_t)n_docs;
+            double sum = 0.0;
+            for (int64_t m = lo; m < hi; m++) {
+                const int32_t t = q_tokens[m];
+                if (t < 0 || t >= vocab) {
+                    set_status(status, BM25_E_TOKEN_RANGE);
+                    continue;
+                }
+                sum += s0[t];
+                post += indptr[t + 1] - indptr[t];
+            }
+            shift[q] = sum;
+            qkp[q] = kp;
         }
-        shift[q] = sum;
-        thresh[q] = 0u;  // below every real score key
-        qpost[q] = post > 0xffffffffll ? 0xffffffffu : (uint32_t)post;
+        const bool dense = act && post <= dense_max;
+        const bool tiled = act && !dense;
+        const uint32_t bd = __ballot_sync(0xffffffffu, dense);
+        const uint32_t bt = __ballot_sync(0xffffffffu, tiled);
+        uint32_t base_d = 0, base_t = 0;
+        if (lane == 0) {
+            if (bd)
+                base_d = atomicAdd(&ctr[1], (uint32_t)__popc(bd));
+            if (bt)
+                base_t = atomicAdd(&ctr[0], (uint32_t)__popc(bt));
+        }
+        base_d = __shfl_sync(0xffffffffu, base_d, 0);
+        base_t = __shfl_sync(0xffffffffu, base_t, 0);
+        const uint32_t lt = lanemask_lt();
+        if (dense)
+            sq[base_d + __popc(bd & lt)] = (int32_t)q;
+        if (tiled) {
+            const uint32_t li = base_t + __popc(bt & lt);
+            lrec[li] = make_int4((int32_t)q, (int32_t)lo, (int32_t)hi, kp);
+            lpost[li] = post > 0xffffffffll ? 0xffffffffu : (uint32_t)post;
+            thresh[li] = 0u;  // below every real score key
+        }
     }
 }
 
@@ -291,6 +337,7 @@ struct TileStage {
     int32_t o_item, o_q;
     uint32_t o_count, o_tau, o_staged;  // o_staged = 0: written directly already
     uint32_t q_post;                    // the current query's postings (all columns)
+    uint32_t q_kp;                      // the current query's k' = min(k, N)
     uint32_t cutoff;                    // fill: docs [0, cutoff) hold the k' lowest untouched
 };
 
@@ -356,12 +403,12 @@ constexpr size_t tile_lists_bytes()
 
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per SM
-    k_tile_topk(const int32_t* __restrict__ q_tokens, int64_t n_tok,
-                const int64_t* __restrict__ q_off, int32_t nq, int64_t n_docs,
-                const int32_t* __restrict__ indices, const float* __restrict__ data,
-                const int32_t* __restrict__ seg, int32_t W, int32_t n_tiles, int32_t kprime,
-                uint32_t* __restrict__ thresh, const uint32_t* __restrict__ qpost,
-                uint32_t* __restrict__ tcount, u64* __restrict__ cand)
+    k_tile_topk(int64_t n_docs, const int32_t* __restrict__ indices,
+                const float* __restrict__ data, const int32_t* __restrict__ seg, int32_t W,
+                int32_t n_tiles, int32_t kstride, const int4* __restrict__ lrec,
+                const uint32_t* __restrict__ lpost, const uint32_t* __restrict__ ctr,
+                uint32_t* __restrict__ thresh, uint32_t* __restrict__ tcount,
+                u64* __restrict__ cand)
 {
     constexpr int WARPS = THREADS / 32;
     constexpr int U = kPostU;
@@ -380,10 +427,15 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
     const float neg0 = __uint_as_float(kUntouched);
     float* my_sval = surv_val + warp * SPW;
     uint16_t* my_sdoc = surv_doc + warp * SPW;
+    // the queries of the tiled path: records {q, first token, end token, k'}
+    // (the grid is sized for the whole sub-batch; CTAs past the items return)
+    const int32_t nq = (int32_t)ctr[0];
+    const int32_t n_items = nq * n_tiles;  // < 2^31 (checked by the host)
+    if ((int32_t)blockIdx.x >= n_items)
+        return;
     for (int i = tid; i < W; i += THREADS)
         acc[i] = neg0;
 
-    const int32_t n_items = nq * n_tiles;  // < 2^31 (checked by the host)
     const int64_t per = (int64_t)n_tiles + 1;
     // Tile-major order: item = tile * nq + q, tile 0 of every query first, so
     // the running threshold of a query is usually known when its later tiles
@@ -398,25 +450,21 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
             t++;
         }
     };
-    const int32_t ntok32 = (int32_t)n_tok;  // < 2^31 (checked by the host)
-    auto clamp_off = [&](int64_t v) -> int32_t {
-        return v < 0 ? 0 : (v > n_tok ? ntok32 : (int32_t)v);
-    };
     // Warp 0 runs a two-stage pipeline over the CTA's items: while item i is
     // processed it loads the segment bounds of item i+1 (lane l: tokens 2l
-    // and 2l+1 of the first chunk) from the token range it loaded during item
-    // i-1, and the (raw, unclamped) token range of item i+2.  Thread 0 also
-    // loads item i+1's threshold.  No load of the pipeline is consumed in the
-    // item it is issued in.
+    // and 2l+1 of the first chunk) from the record it loaded during item
+    // i-1, and the record of item i+2.  Thread 0 also loads item i+1's
+    // threshold and postings count.  No load of the pipeline is consumed in
+    // the item it is issued in.  (q indexes the records here.)
     int32_t tile = (int32_t)(blockIdx.x / nq), q = (int32_t)(blockIdx.x % nq);
     int32_t t1 = tile, q1 = q;
     advance(t1, q1);
     int32_t t2 = t1, q2 = q1;
     advance(t2, q2);
-    int32_t a1 = 0, b1 = 0;                 // clamped token range of item i+1
-    int64_t ra2 = 0, rb2 = 0;               // raw token range of item i+2
+    int4 rec1 = make_int4(0, 0, 0, 0);      // record of item i+1
+    int4 rec2 = make_int4(0, 0, 0, 0);      // record of item i+2
     int32_t pf_lo0 = 0, pf_lo1 = 0, pf_hi0 = 0, pf_hi1 = 0;
-    uint32_t pf_tau = 0, pf_post = 0;
+    uint32_t pf_tau = 0, pf_post = 0, pf_kp = 0;
     auto load_seg = [&](int32_t t_, int32_t a_, int32_t b_) {
         const int32_t m_ = a_ + 2 * tid;
         pf_lo0 = pf_hi0 = pf_lo1 = pf_hi1 = 0;
@@ -432,23 +480,19 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
     if (tid == 0)
         ts.o_item = -1;
     if (tid < 32) {
-        const int32_t a0 = clamp_off(q_off[q]);
-        const int32_t b0 = max(a0, clamp_off(q_off[q + 1]));
-        load_seg(tile, a0, b0);
+        const int4 r0 = lrec[q];
+        load_seg(tile, r0.y, r0.z);
         if (tid == 0) {
-            ts.qoff[0][0] = a0;
-            ts.qoff[0][1] = b0;
+            ts.qoff[0][0] = r0.y;
+            ts.qoff[0][1] = r0.z;
             pf_tau = *(volatile uint32_t*)&thresh[q];
-            pf_post = qpost[q];
+            pf_post = lpost[q];
+            pf_kp = (uint32_t)r0.w;
         }
-        if ((int64_t)blockIdx.x + gridDim.x < n_items) {
-            a1 = clamp_off(q_off[q1]);
-            b1 = max(a1, clamp_off(q_off[q1 + 1]));
-        }
-        if ((int64_t)blockIdx.x + 2 * (int64_t)gridDim.x < n_items) {
-            ra2 = q_off[q2];
-            rb2 = q_off[q2 + 1];
-        }
+        if ((int64_t)blockIdx.x + gridDim.x < n_items)
+            rec1 = lrec[q1];
+        if ((int64_t)blockIdx.x + 2 * (int64_t)gridDim.x < n_items)
+            rec2 = lrec[q2];
     }
     __syncthreads();
 #ifdef BM25_PHASE_TIMING
@@ -465,7 +509,7 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
         const uint32_t pc = ts.o_count;
         if (ts.o_staged) {
             for (uint32_t t = tid; t < pc; t += THREADS)
-                cand[(int64_t)pi * kprime + t] = ts.obuf[t];
+                cand[(int64_t)pi * kstride + t] = ts.obuf[t];
             if (tid == 0)
                 tcount[pi] = pc;
         }
@@ -482,22 +526,20 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
             if (tid < 32) {
                 const int32_t nitem = item + (int32_t)gridDim.x;
                 if (nitem < n_items) {
-                    load_seg(t1, a1, b1);
+                    load_seg(t1, rec1.y, rec1.z);
                     if (tid == 0) {
-                        ts.qoff[parity ^ 1][0] = a1;
-                        ts.qoff[parity ^ 1][1] = b1;
+                        ts.qoff[parity ^ 1][0] = rec1.y;
+                        ts.qoff[parity ^ 1][1] = rec1.z;
                         pf_tau = *(volatile uint32_t*)&thresh[q1];
-                        pf_post = qpost[q1];
+                        pf_post = lpost[q1];
+                        pf_kp = (uint32_t)rec1.w;
                     }
                 }
-                a1 = clamp_off(ra2);
-                b1 = max(a1, clamp_off(rb2));
+                rec1 = rec2;
                 int32_t t3 = t2, q3 = q2;
                 advance(t3, q3);
-                if ((int64_t)nitem + 2 * (int64_t)gridDim.x < n_items) {
-                    ra2 = q_off[q3];
-                    rb2 = q_off[q3 + 1];
-                }
+                if ((int64_t)nitem + 2 * (int64_t)gridDim.x < n_items)
+                    rec2 = lrec[q3];
                 t1 = t2;
                 q1 = q2;
                 t2 = t3;
@@ -507,6 +549,7 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
         if (tid == 0) {
             st.tau = pf_tau;  // thread 0 holds the threshold; the others read st.tau
             ts.q_post = pf_post;
+            ts.q_kp = pf_kp;
         }
         int32_t dd[U];        // doc ids (within the tile) of this thread's postings
 #pragma unroll
@@ -610,17 +653,18 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
         // documents scoring at least tau, so a document below tau cannot be
         // in the top k' (documents AT tau can, through the doc-id tie rule).
         const uint32_t tau = st.tau;
-        const uint32_t kp = (uint32_t)min(kprime, wd);
+        const uint32_t qkp = ts.q_kp;                  // the query's k'
+        const uint32_t kp = min(qkp, (uint32_t)wd);    // at most wd from one tile
         // Untouched documents score exactly 0: they can matter only if 0
         // clears tau (and then only if fewer than k' touched ones score > 0),
         // and only the k' lowest-id untouched documents of the whole corpus
         // can: a tile whose predecessors hold at least k' untouched documents
         // (true once t * W - postings of the query >= k') adds none.
         const bool zero_counts = tau <= kZeroKey;
-        const bool may_fill = zero_counts && (int64_t)tile * W < (int64_t)kp + ts.q_post;
+        const bool may_fill = zero_counts && (int64_t)tile * W < (int64_t)qkp + ts.q_post;
         // candidates go to the staging buffer when they fit (kp <= kOutCap),
         // else straight to the item's slots
-        u64* out = kp <= kOutCap ? ts.obuf : cand + (int64_t)item * kprime;
+        u64* out = kp <= kOutCap ? ts.obuf : cand + (int64_t)item * kstride;
         uint32_t n_emit = 0;
         uint32_t new_tau = 0;  // score key of (a lower bound on) the weakest emitted
         bool tau_ok = false;   // new_tau is a valid bound to publish
@@ -841,14 +885,14 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
         }
         BM25_PHASE(3);
         if (tid == 0) {
-            // staged for the next item's flush; a full set of k' candidates
-            // raises the query's threshold to (a lower bound on) the score of
-            // the weakest of them
+            // staged for the next item's flush; a full set of the query's k'
+            // candidates raises its threshold to (a lower bound on) the score
+            // of the weakest of them (a tile narrower than k' never does)
             ts.o_item = item;
             ts.o_q = q;
             ts.o_count = n_emit;
             ts.o_staged = kp <= kOutCap;
-            ts.o_tau = (tau_ok && n_emit == kp && kp > 0) ? new_tau : 0u;
+            ts.o_tau = (tau_ok && n_emit == qkp && qkp > 0) ? new_tau : 0u;
             if (kp > kOutCap)
                 tcount[item] = n_emit;  // its candidates were written directly
         }
@@ -868,33 +912,85 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
 #endif
 }
 
+// ---- finishing a query's row (R3 and R4) ------------------------------------
+// sel[0 .. sz) holds the k' selected keys (slots past them 0; sz a power of
+// two >= k').  Re-keys them on the final FP32 score B = S + sum_i S0(q_i)
+// (Sec. 2.1), so that equal returned scores list the lower doc id first,
+// sorts them descending (bitonic) and writes row slots 0 .. kout-1: ids and
+// scores, -1 / -inf past the k' documents.  All threads of the block call it.
+__device__ void finish_row(u64* sel, int sz, uint32_t kp, int32_t kout, double sh,
+                           int32_t* __restrict__ ids, float* __restrict__ scores)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < sz; i += nt) {
+        const u64 key = sel[i];
+        if ((uint32_t)i < kp && key != 0ull)
+            sel[i] = make_key((float)((double)key_score(key) + sh), key_doc(key));
+    }
+    __syncthreads();
+    for (int size = 2; size <= sz; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = tid; i < sz / 2; i += nt) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool desc = ((lo & size) == 0);
+                const u64 a = sel[lo], b = sel[hi];
+                if ((a < b) == desc) {
+                    sel[lo] = b;
+                    sel[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int r = tid; r < kout; r += nt) {
+        const u64 key = (uint32_t)r < kp ? sel[r] : 0ull;
+        if (key != 0ull) {
+            ids[r] = (int32_t)key_doc(key);
+            scores[r] = key_score(key);
+        } else {
+            ids[r] = -1;
+            scores[r] = -__int_as_float(0x7f800000);
+        }
+    }
+}
+
 // ---- R3 -----------------------------------------------------------------------
-// Per query: gather the tiles' candidates (tcount[tile * nq + q] of them in
-// item tile * nq + q's slots), select the k' best, re-key them on the final
-// FP32 score (shift added) so that equal returned scores list the lower doc
-// id first, sort, and write (id, score).  Dynamic shared memory:
-// sel[pow2 >= k'] | buf[buf_cap] keys | pre[n_tiles + 1].
+// Per query of the tiled path (block b: record b): gather the tiles'
+// candidates (tcount[tile * n_long + b] of them in that item's kstride
+// slots), select the k' best and finish the query's row.  Dynamic shared
+// memory: sel[pow2 >= kstride] | buf[buf_cap] keys | pre[n_tiles + 1].
 __global__ void __launch_bounds__(kMergeThreads)
-    k_merge(const u64* __restrict__ cand, const uint32_t* __restrict__ tcount, int32_t nq,
-            int32_t n_tiles, int32_t kprime, int32_t k, const double* __restrict__ shift,
+    k_merge(const u64* __restrict__ cand, const uint32_t* __restrict__ tcount,
+            const int4* __restrict__ lrec, const uint32_t* __restrict__ ctr, int32_t n_tiles,
+            int32_t kstride, int32_t kout, const double* __restrict__ shift,
             int32_t* __restrict__ out_ids, float* __restrict__ out_scores, int32_t buf_cap)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SelectState st;
+    const int32_t nl = (int32_t)ctr[0];
+    const int b = blockIdx.x;
+    if (b >= nl)
+        return;
+    const int4 rec = lrec[b];
+    const int32_t q = rec.x;
+    const uint32_t kp = (uint32_t)rec.w;
+    int sz_all = 1;
+    while (sz_all < kstride)
+        sz_all <<= 1;
     int sz = 1;
-    while (sz < kprime)
+    while ((uint32_t)sz < kp)
         sz <<= 1;
     u64* sel = reinterpret_cast<u64*>(smem);
-    u64* buf = sel + sz;
+    u64* buf = sel + sz_all;
     uint32_t* pre = reinterpret_cast<uint32_t*>(buf + buf_cap);
-    const int q = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     // exclusive scan of the per-tile counts
     uint32_t carry = 0;
     for (int t0 = 0; t0 < n_tiles; t0 += kMergeThreads) {
         const int t = t0 + tid;
-        const uint32_t c = t < n_tiles ? tcount[(int64_t)t * nq + q] : 0u;
+        const uint32_t c = t < n_tiles ? tcount[(int64_t)t * nl + b] : 0u;
         uint32_t tot;
         const uint32_t ex = block_exclusive_sum(c, st.red, &tot);
         if (t < n_tiles)
@@ -908,12 +1004,12 @@ __global__ void __launch_bounds__(kMergeThreads)
     if (tid == 0)
         st.ctr = 0;
     __syncthreads();
-    const uint32_t total = pre[n_tiles];  // > 0: the tiles hold at least k' candidates
+    const uint32_t total = pre[n_tiles];  // >= k': the tiles hold enough candidates
     const bool gathered = total <= (uint32_t)buf_cap;
     if (gathered) {  // one warp per tile copies its candidates
         for (int t = warp; t < n_tiles; t += kMergeThreads / 32) {
             const uint32_t c = pre[t + 1] - pre[t];
-            const u64* src = cand + ((int64_t)t * nq + q) * kprime;
+            const u64* src = cand + ((int64_t)t * nl + b) * kstride;
             for (uint32_t s = lane; s < c; s += 32)
                 buf[pre[t] + s] = src[s];
         }
@@ -922,55 +1018,289 @@ __global__ void __launch_bounds__(kMergeThreads)
     auto get = [&](uint32_t i) -> u64 {
         if (gathered)
             return buf[i];
-        int a = 0, b = n_tiles;  // pre[a] <= i < pre[b]
-        while (b - a > 1) {
-            int mid = (a + b) >> 1;
+        int a = 0, e = n_tiles;  // pre[a] <= i < pre[e]
+        while (e - a > 1) {
+            const int mid = (a + e) >> 1;
             if (pre[mid] <= i)
                 a = mid;
             else
-                b = mid;
+                e = mid;
         }
-        return cand[((int64_t)a * nq + q) * kprime + (i - pre[a])];
+        return cand[((int64_t)a * nl + b) * kstride + (i - pre[a])];
     };
-    block_select_idx<true>(st, total, total, (uint32_t)kprime, 0, 0ull, get,
-                           [&](u64 key, uint32_t slot) {
-        if (slot < (uint32_t)kprime)
+    block_select_idx<true>(st, total, total, kp, 0, 0ull, get, [&](u64 key, uint32_t slot) {
+        if (slot < kp)
             sel[slot] = key;
     });
-    const double sh = shift[q];
-    for (int i = tid; i < kprime; i += kMergeThreads) {
-        u64 key = sel[i];
-        if (key != 0ull)
-            sel[i] = make_key((float)((double)key_score(key) + sh), key_doc(key));
+    finish_row(sel, sz, kp, kout, shift[q], out_ids + (int64_t)q * kout,
+               out_scores + (int64_t)q * kout);
+}
+
+// ---- R4 -----------------------------------------------------------------------
+// The dense path for queries with few postings: one CTA per query, taken from
+// the short list by an atomic counter (ctr[2]).  The CTA owns a dense FP32
+// vector of N accumulators in global memory, all -0.0 between queries; only
+// the sectors the query touches are brought in, and they stay in L2 while the
+// query runs.
+//   1. scatter: every posting (d, S) of the query's columns is added to
+//      acc[d] with a fire-and-forget reduction (Sec. 2 "Assigning Query
+//      Scores": the summed column slices);
+//   2. claim: each posting's document is exchanged for -0.0, so the first
+//      claimer of a document gets its sum and the vector is clean again; the
+//      first claims go, as keys, to the CTA's candidate list (global memory);
+//   3. fill: if fewer than k' touched documents score > 0, the untouched
+//      documents (score 0) can rank: the k' lowest-id ones lie below
+//      R = k' + touched, found through a shared-memory bitmap of the touched
+//      documents below R, and are appended to the list;
+//   4. select the k' best of the list (radix select) and finish the row.
+constexpr int kDenseThreads = 256;
+
+struct DenseStage {
+    int32_t lo[kTokChunk];
+    int32_t pre[kTokChunk + 1];
+    uint32_t scan[33];
+    uint32_t n_first, n_pos, kmin, kmax;
+    uint32_t item;
+};
+
+// Loads the columns of query tokens [mb, mb + cnt) into ds.lo / ds.pre
+// (warp 0; cnt <= kTokChunk).  A token outside the vocabulary has an empty
+// column.
+__device__ __forceinline__ void dense_columns(DenseStage& ds, const int32_t* __restrict__ q_tokens,
+                                              const int64_t* __restrict__ indptr, int32_t vocab,
+                                              int64_t mb, int cnt)
+{
+    const int lane = threadIdx.x & 31;
+    int32_t len[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int i = 2 * lane + h;
+        int32_t l = 0, n = 0;
+        if (i < cnt) {
+            const int32_t t = q_tokens[mb + i];
+            if (t >= 0 && t < vocab) {
+                const int64_t a = indptr[t];
+                l = (int32_t)a;  // positions < nnz <= 2^31 - 2
+                n = (int32_t)(indptr[t + 1] - a);
+            }
+        }
+        len[h] = n;
+        ds.lo[i] = l;
     }
-    __syncthreads();
-    // bitonic sort, descending
-    for (int size = 2; size <= sz; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = tid; i < sz / 2; i += kMergeThreads) {
-                int lo = 2 * i - (i & (stride - 1));
-                int hi = lo + stride;
-                bool desc = ((lo & size) == 0);
-                u64 a = sel[lo], b = sel[hi];
-                if ((a < b) == desc) {
-                    sel[lo] = b;
-                    sel[hi] = a;
+    const int32_t s2 = len[0] + len[1];
+    const int32_t inc = warp_inclusive_sum(s2);
+    ds.pre[2 * lane] = inc - s2;
+    ds.pre[2 * lane + 1] = inc - s2 + len[0];
+    if (lane == 31)
+        ds.pre[kTokChunk] = inc;
+}
+
+// Token of the first posting of run r0 (ds.pre[a] <= 32 r0 < ds.pre[a+1]).
+__device__ __forceinline__ int dense_first_token(const DenseStage& ds, int cnt, int32_t eb)
+{
+    int a = 0, b = cnt;
+    while (b - a > 1) {
+        const int mid = (a + b) >> 1;
+        if (ds.pre[mid] <= eb)
+            a = mid;
+        else
+            b = mid;
+    }
+    return a;
+}
+
+__global__ void __launch_bounds__(kDenseThreads)
+    k_dense_topk(const int32_t* __restrict__ q_tokens, int64_t n_tok,
+                 const int64_t* __restrict__ q_off, const int32_t* __restrict__ qkp,
+                 const double* __restrict__ shift, const int64_t* __restrict__ indptr,
+                 const int32_t* __restrict__ indices, const float* __restrict__ data,
+                 int32_t vocab, int64_t n_docs, const int32_t* __restrict__ sq,
+                 uint32_t* __restrict__ ctr, float* __restrict__ slots, u64* __restrict__ lists,
+                 int64_t list_cap, int32_t kstride, int32_t kout, int32_t* __restrict__ out_ids,
+                 float* __restrict__ out_scores)
+{
+    constexpr int WARPS = kDenseThreads / 32;
+    constexpr int U = 8;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SelectState st;
+    __shared__ DenseStage ds;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int sz_all = 1;
+    while (sz_all < kstride)
+        sz_all <<= 1;
+    u64* sel = reinterpret_cast<u64*>(smem);
+    uint32_t* bits = reinterpret_cast<uint32_t*>(sel + sz_all);
+    float* acc = slots + (size_t)blockIdx.x * (size_t)n_docs;
+    u64* list = lists + (size_t)blockIdx.x * (size_t)list_cap;
+    const uint32_t n_short = ctr[1];
+    const uint32_t ltmask = lanemask_lt();
+    const uint32_t N32 = (uint32_t)n_docs;  // n_docs < 2^31
+
+    for (;;) {
+        if (tid == 0) {
+            ds.item = atomicAdd(&ctr[2], 1u);
+            ds.n_first = 0;
+            ds.n_pos = 0;
+            ds.kmin = 0xffffffffu;
+            ds.kmax = 0u;
+            st.ctr = 0;
+        }
+        __syncthreads();
+        const uint32_t item = ds.item;
+        if (item >= n_short)
+            break;
+        const int32_t q = sq[item];
+        int64_t lo = q_off[q], hi = q_off[q + 1];  // checked by k_query_prep; clamped here
+        lo = lo < 0 ? 0 : (lo > n_tok ? n_tok : lo);
+        hi = hi < lo ? lo : (hi > n_tok ? n_tok : hi);
+        const uint32_t kp = (uint32_t)qkp[q];
+        const bool one_chunk = hi - lo <= kTokChunk;
+
+        // ---- 1 and 2: scatter, then claim ----------------------------------------
+        uint32_t pos = 0, kmin = 0xffffffffu, kmax = 0u;
+        for (int pass = 0; pass < 2; pass++) {
+            for (int64_t mb = lo; mb < hi; mb += kTokChunk) {
+                const int cnt = (int)min((int64_t)kTokChunk, hi - mb);
+                if (pass == 0 || !one_chunk) {
+                    __syncthreads();  // earlier readers of ds.lo / ds.pre are done
+                    if (warp == 0)
+                        dense_columns(ds, q_tokens, indptr, vocab, mb, cnt);
+                    __syncthreads();
+                }
+                const int32_t total = ds.pre[kTokChunk];
+                for (int32_t r0 = warp; r0 * 32 < total; r0 += U * WARPS) {
+                    int a = dense_first_token(ds, cnt, r0 * 32);
+                    int32_t dd[U];
+                    float vv[U];
+#pragma unroll
+                    for (int u = 0; u < U; u++) {
+                        const int32_t e = (r0 + u * WARPS) * 32 + lane;
+                        dd[u] = -1;
+                        vv[u] = 0.0f;
+                        if (e < total) {
+                            while (ds.pre[a + 1] <= e)
+                                a++;
+                            const int32_t j = ds.lo[a] + (e - ds.pre[a]);
+                            const int32_t d = __ldg(indices + j);
+                            if ((uint32_t)d < N32) {  // holds for any well-formed index
+                                dd[u] = d;
+                                if (pass == 0)
+                                    vv[u] = __ldg(data + j);
+                            }
+                        }
+                    }
+                    if (pass == 0) {
+#pragma unroll
+                        for (int u = 0; u < U; u++)
+                            if (dd[u] >= 0)
+                                atomicAdd(acc + dd[u], vv[u]);  // result unused: a reduction
+                    } else {
+                        float cv[U];  // all exchanges first, so their latencies overlap
+#pragma unroll
+                        for (int u = 0; u < U; u++)
+                            cv[u] = dd[u] >= 0 ? atomicExch(acc + dd[u], __uint_as_float(kUntouched))
+                                               : __uint_as_float(kUntouched);
+#pragma unroll
+                        for (int u = 0; u < U; u++) {
+                            const bool first = __float_as_uint(cv[u]) != kUntouched;
+                            const uint32_t bal = __ballot_sync(0xffffffffu, first);
+                            if (bal) {
+                                uint32_t base = 0;
+                                if (lane == __ffs(bal) - 1)
+                                    base = atomicAdd(&ds.n_first, (uint32_t)__popc(bal));
+                                base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
+                                if (first) {
+                                    const uint32_t o = order_f32(cv[u]);
+                                    list[base + __popc(bal & ltmask)] = make_key(cv[u], (uint32_t)dd[u]);
+                                    pos += cv[u] > 0.0f;
+                                    kmin = min(kmin, o);
+                                    kmax = max(kmax, o);
+                                }
+                            }
+                        }
+                    }
                 }
             }
+            __syncthreads();  // pass 0: every reduction precedes every exchange
+        }
+        pos = __reduce_add_sync(0xffffffffu, pos);
+        kmin = __reduce_min_sync(0xffffffffu, kmin);
+        kmax = __reduce_max_sync(0xffffffffu, kmax);
+        if (lane == 0) {
+            if (pos)
+                atomicAdd(&ds.n_pos, pos);
+            atomicMin(&ds.kmin, kmin);
+            atomicMax(&ds.kmax, kmax);
+        }
+        __syncthreads();
+        const uint32_t n_first = ds.n_first;
+        const bool fill = ds.n_pos < kp;
+        uint32_t n_all = n_first;
+
+        // ---- 3: the lowest-id untouched documents, when they can rank -------------
+        if (fill) {
+            const int64_t R = min(n_docs, (int64_t)kp + (int64_t)n_first);
+            const int32_t nw = (int32_t)((R + 31) >> 5);
+            for (int w = tid; w < nw; w += kDenseThreads)
+                bits[w] = 0u;
+            __syncthreads();
+            for (uint32_t i = tid; i < n_first; i += kDenseThreads) {
+                const uint32_t d = key_doc(list[i]);
+                if ((int64_t)d < R)
+                    atomicOr(&bits[d >> 5], 1u << (d & 31));
+            }
+            __syncthreads();
+            uint32_t carry = 0;  // block-uniform
+            for (int w0 = 0; w0 < nw && carry < kp; w0 += kDenseThreads) {
+                const int w = w0 + tid;
+                uint32_t z = 0;
+                if (w < nw) {
+                    const int rem = (int)(R - ((int64_t)w << 5));
+                    const uint32_t valid = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+                    z = ~bits[w] & valid;
+                }
+                uint32_t tot;
+                uint32_t r = block_exclusive_sum((uint32_t)__popc(z), ds.scan, &tot) + carry;
+                while (z && r < kp) {
+                    const int bpos = __ffs(z) - 1;
+                    z &= z - 1;
+                    list[n_first + r] = make_key(0.0f, (uint32_t)((w << 5) + bpos));
+                    r++;
+                }
+                carry += tot;
+            }
+            n_all = n_first + min(carry, kp);
             __syncthreads();
         }
+
+        // ---- 4: select and finish -------------------------------------------------
+        int sz = 1;
+        while ((uint32_t)sz < kp)
+            sz <<= 1;
+        for (int i = tid; i < sz; i += kDenseThreads)
+            sel[i] = 0ull;
+        __syncthreads();
+        const int skip = fill ? 0 : common_bytes(ds.kmin, ds.kmax);
+        const u64 common = fill ? 0ull : (u64)ds.kmax << 32;
+        block_select_idx<true>(st, n_all, n_all, kp, skip, common,
+                               [&](uint32_t i) -> u64 { return list[i]; },
+                               [&](u64 key, uint32_t slot) {
+            if (slot < kp)
+                sel[slot] = key;
+        });
+        finish_row(sel, sz, kp, kout, shift[q], out_ids + (int64_t)q * kout,
+                   out_scores + (int64_t)q * kout);
+        // finish_row ends with global writes only; the next query's first
+        // barrier orders the reuse of sel and the stage
     }
-    for (int r = tid; r < k; r += kMergeThreads) {
-        int64_t o = (int64_t)q * k + r;
-        const u64 key = r < kprime ? sel[r] : 0ull;
-        if (key != 0ull) {
-            out_ids[o] = (int32_t)key_doc(key);
-            out_scores[o] = key_score(key);
-        } else {
-            out_ids[o] = -1;
-            out_scores[o] = -__int_as_float(0x7f800000);
-        }
-    }
+}
+
+// Sets n 32-bit words to v (the dense vectors start at -0.0).
+__global__ void k_fill_u32(uint32_t* __restrict__ p, int64_t n, uint32_t v)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
 }
 
 size_t tile_smem_bytes(int32_t W, int threads)
@@ -981,11 +1311,86 @@ size_t tile_smem_bytes(int32_t W, int threads)
     return (size_t)W * 4 + sizeof(SelectState) + sizeof(TileStage) + lists;
 }
 
+constexpr int64_t kCandBudget = int64_t(2) << 30;   // bytes of tile candidates per sub-batch
+constexpr int64_t kDenseBudget = int64_t(2) << 30;  // bytes of dense vectors per workspace
+constexpr int kDenseCtasPerSm = 2;
+constexpr int32_t kDenseMaxL2 = 1 << 19;  // postings bound of the dense path in L2_DENSE mode
+
+// Everything a call's launches depend on, derived from the index, plan and
+// batch shape alone (so that reserving and retrieving agree).
+struct Geometry {
+    int32_t W = 0, n_tiles = 0, kstride = 0, nq_sub = 0;
+    int64_t dense_max = -1;  // -1: no dense path
+    int32_t dense_ctas = 0;
+    int64_t list_cap = 0;
+    size_t dense_smem = 0;
+};
+
+size_t dense_smem_bytes(int32_t kstride, int64_t dense_max)
+{
+    int sz = 1;
+    while (sz < kstride)
+        sz <<= 1;
+    const int64_t bit_words = ((int64_t)kstride + dense_max + 31) / 32 + 1;
+    return (size_t)sz * sizeof(u64) + (size_t)bit_words * sizeof(uint32_t);
+}
+
+int geometry(const bm25_index* ix, const bm25_workspace* ws, int32_t nq, int32_t kmax,
+             const Plan& plan, Geometry* g)
+{
+    DeviceInfo di;
+    BM25_TRY(device_info(&di));
+    const int64_t N = ix->n_docs;
+    g->kstride = (int32_t)std::min<int64_t>(kmax, N);
+    g->W = tile_width(plan, N);
+    const int64_t n_tiles64 = (N + g->W - 1) / g->W;
+    if (n_tiles64 > 65536)
+        return set_error(BM25_E_INVALID, "%lld doc tiles of %d documents: use wider tiles",
+                         (long long)n_tiles64, g->W);
+    g->n_tiles = (int32_t)n_tiles64;
+    // queries per sub-batch: tile candidates within kCandBudget, work items < 2^31
+    const int64_t per_q = (int64_t)g->n_tiles * g->kstride * (int64_t)sizeof(u64);
+    int64_t sub = std::max<int64_t>(1, kCandBudget / per_q);
+    sub = std::min<int64_t>(sub, (INT32_MAX - 1) / g->n_tiles);
+    if (ws->fixed)  // a lent workspace holds the whole batch or the caller splits it
+        sub = nq;
+    g->nq_sub = (int32_t)std::min<int64_t>(std::max(nq, 1), sub);
+    if ((int64_t)g->nq_sub * g->n_tiles >= INT32_MAX)
+        return set_error(BM25_E_INVALID, "%d queries x %d doc tiles is too many work items for "
+                         "one call", g->nq_sub, g->n_tiles);
+    g->dense_max = -1;
+    g->dense_ctas = 0;
+    if (plan.accumulator != BM25_ACC_SMEM_TILED && !ws->fixed) {
+        const int64_t dmax = plan.accumulator == BM25_ACC_L2_DENSE
+                                 ? std::max<int64_t>(plan.dense_max, kDenseMaxL2)
+                                 : plan.dense_max;
+        // CTAs in flight: the dense vectors within kDenseBudget, and the
+        // sectors their queries touch (32 bytes per posting at most) within
+        // half of L2, so that scatter and claim meet in L2
+        const int64_t by_mem = kDenseBudget / ((int64_t)sizeof(float) * N);
+        const int64_t by_l2 = std::max<int64_t>(1, (int64_t)di.l2_bytes / 2 / (32 * dmax));
+        const int64_t ctas = std::min<int64_t>(
+            std::min<int64_t>((int64_t)di.sm_count * kDenseCtasPerSm, by_mem), by_l2);
+        const size_t smem = dense_smem_bytes(g->kstride, dmax);
+        if (dmax > 0 && ctas >= 1 && smem + sizeof(SelectState) + sizeof(DenseStage) <=
+                                         (size_t)di.max_smem_optin) {
+            g->dense_max = dmax;
+            g->dense_ctas = (int32_t)ctas;
+            g->list_cap = dmax + g->kstride;
+            g->dense_smem = smem;
+        }
+    }
+    return BM25_OK;
+}
+
 template <typename T>
-int grow(T** p, size_t* cap, size_t need)
+int grow(T** p, size_t* cap, size_t need, bool capturing)
 {
     if (need <= *cap && *p)
         return BM25_OK;
+    if (capturing)
+        return set_error(BM25_E_INVALID, "the workspace must grow, which cannot happen during "
+                         "stream capture: reserve it for this call first");
     if (*p)
         cudaFree(*p);
     *p = nullptr;
@@ -993,6 +1398,47 @@ int grow(T** p, size_t* cap, size_t need)
     size_t n = need > 0 ? need : 1;
     BM25_CUDA_TRY(cudaMalloc((void**)p, n * sizeof(T)));
     *cap = n;
+    return BM25_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int reserve(const bm25_index* ix, bm25_workspace* ws, const Geometry& g, int64_t n_tok,
+            cudaStream_t s)
+{
+    const size_t m = (size_t)g.nq_sub;
+    const size_t n_seg = (size_t)n_tok * (size_t)(g.n_tiles + 1);
+    const size_t n_tc = m * (size_t)g.n_tiles;
+    const size_t n_cand = n_tc * (size_t)g.kstride;
+    const size_t n_slots = (size_t)g.dense_ctas * (size_t)ix->n_docs;
+    const size_t n_lists = (size_t)g.dense_ctas * (size_t)g.list_cap;
+    if (ws->fixed) {
+        if ((int32_t)m > ws->max_queries || n_seg > ws->seg_cap || n_tc > ws->tcount_cap ||
+            n_cand > ws->cand_cap)
+            return set_error(BM25_E_INVALID, "the lent scratch is too small for this batch");
+        return BM25_OK;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    BM25_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    const bool capturing = cs != cudaStreamCaptureStatusNone;
+    if ((int32_t)m > ws->max_queries || !ws->qbuf) {
+        const size_t bytes = query_arrays_bytes((int64_t)m);
+        BM25_TRY(grow(&ws->qbuf, &ws->qbuf_cap, bytes, capturing));
+        carve_queries(ws, ws->qbuf, (int32_t)m);
+    }
+    BM25_TRY(grow(&ws->seg, &ws->seg_cap, n_seg, capturing));
+    BM25_TRY(grow(&ws->tcount, &ws->tcount_cap, n_tc, capturing));
+    BM25_TRY(grow(&ws->cand, &ws->cand_cap, n_cand, capturing));
+    if (n_slots > 0 && (n_slots > ws->dslots_cap || !ws->dslots)) {
+        BM25_TRY(grow(&ws->dslots, &ws->dslots_cap, n_slots, capturing));
+        // every dense accumulator starts untouched (-0.0); queries leave them so
+        k_fill_u32<<<1024, 256, 0, s>>>(reinterpret_cast<uint32_t*>(ws->dslots),
+                                        (int64_t)ws->dslots_cap, kUntouched);
+        count_launch();
+        BM25_LAUNCH_CHECK();
+    }
+    if (n_lists > 0)
+        BM25_TRY(grow(&ws->dlists, &ws->dlists_cap, n_lists, capturing));
     return BM25_OK;
 }
 
@@ -1011,88 +1457,114 @@ extern "C" int bm25_debug_phase_read(unsigned long long* out, int reset)
 }
 #endif
 
-int workspace_reserve(const bm25_index* ix, bm25_workspace* ws, int32_t nq, int64_t n_tok,
-                      int32_t kprime, int64_t n_tiles)
+int32_t tile_width(const Plan& plan, int64_t n_docs)
 {
-    (void)ix;
-    if (nq > ws->max_queries || !ws->shift) {
-        for (void* p : {(void*)ws->shift, (void*)ws->thresh, (void*)ws->qpost})
-            if (p)
-                cudaFree(p);
-        ws->shift = nullptr;
-        ws->thresh = nullptr;
-        ws->qpost = nullptr;
-        const size_t m = (size_t)std::max(nq, 1);
-        BM25_CUDA_TRY(cudaMalloc((void**)&ws->shift, sizeof(double) * m));
-        BM25_CUDA_TRY(cudaMalloc((void**)&ws->thresh, sizeof(uint32_t) * m));
-        BM25_CUDA_TRY(cudaMalloc((void**)&ws->qpost, sizeof(uint32_t) * m));
-        ws->max_queries = (int32_t)m;
-    }
-    BM25_TRY(grow(&ws->seg, &ws->seg_cap, (size_t)n_tok * (size_t)(n_tiles + 1)));
-    BM25_TRY(grow(&ws->tcount, &ws->tcount_cap, (size_t)nq * (size_t)n_tiles));
-    BM25_TRY(grow(&ws->cand, &ws->cand_cap, (size_t)nq * (size_t)n_tiles * (size_t)kprime));
+    int32_t W = plan.tile_docs > 0 ? plan.tile_docs : 12288;
+    // multiples of 128 keep the shared-memory carve-up 16-byte aligned
+    const int64_t w_need = (n_docs + 127) / 128 * 128;
+    if (W > w_need)
+        W = (int32_t)w_need;
+    return W;
+}
+
+size_t query_arrays_bytes(int64_t m)
+{
+    const size_t q = (size_t)std::max<int64_t>(m, 1);
+    return align256(4 * sizeof(uint32_t)) + align256(q * sizeof(double)) +
+           align256(q * sizeof(int4)) + 4 * align256(q * sizeof(uint32_t));
+}
+
+void carve_queries(bm25_workspace* ws, unsigned char* base, int32_t m)
+{
+    const size_t q = (size_t)std::max(m, 1);
+    unsigned char* p = base;
+    ws->ctr = reinterpret_cast<uint32_t*>(p);
+    p += align256(4 * sizeof(uint32_t));
+    ws->shift = reinterpret_cast<double*>(p);
+    p += align256(q * sizeof(double));
+    ws->lrec = reinterpret_cast<int4*>(p);
+    p += align256(q * sizeof(int4));
+    ws->qkp = reinterpret_cast<int32_t*>(p);
+    p += align256(q * sizeof(uint32_t));
+    ws->lpost = reinterpret_cast<uint32_t*>(p);
+    p += align256(q * sizeof(uint32_t));
+    ws->thresh = reinterpret_cast<uint32_t*>(p);
+    p += align256(q * sizeof(uint32_t));
+    ws->sq = reinterpret_cast<int32_t*>(p);
+    ws->max_queries = (int32_t)q;
+}
+
+int workspace_bytes_for(const bm25_index* ix, int32_t nq, int64_t n_tok, int32_t kmax,
+                        const Plan& plan, size_t* bytes)
+{
+    bm25_workspace probe;
+    Geometry g;
+    BM25_TRY(geometry(ix, &probe, nq, kmax, plan, &g));
+    const size_t m = (size_t)g.nq_sub;
+    *bytes = query_arrays_bytes((int64_t)m) +
+             sizeof(int32_t) * (size_t)n_tok * (size_t)(g.n_tiles + 1) +
+             m * (size_t)g.n_tiles * (sizeof(uint32_t) + sizeof(u64) * (size_t)g.kstride) +
+             (size_t)g.dense_ctas * ((size_t)ix->n_docs * sizeof(float) +
+                                     (size_t)g.list_cap * sizeof(u64));
     return BM25_OK;
+}
+
+size_t workspace_bytes_held(const bm25_workspace* ws)
+{
+    if (ws->fixed)
+        return 0;
+    return ws->qbuf_cap + ws->seg_cap * sizeof(int32_t) + ws->tcount_cap * sizeof(uint32_t) +
+           ws->cand_cap * sizeof(u64) + ws->dslots_cap * sizeof(float) +
+           ws->dlists_cap * sizeof(u64);
+}
+
+int workspace_reserve_for(const bm25_index* ix, bm25_workspace* ws, int32_t nq, int64_t n_tok,
+                          int32_t kmax, const Plan& plan, cudaStream_t s)
+{
+    Geometry g;
+    BM25_TRY(geometry(ix, ws, nq, kmax, plan, &g));
+    return reserve(ix, ws, g, n_tok, s);
 }
 
 void workspace_release(bm25_workspace* ws)
 {
-    void* ps[] = {ws->shift, ws->thresh, ws->qpost, ws->tcount, ws->seg, ws->cand};
-    for (void* p : ps)
-        if (p)
-            cudaFree(p);
+    if (!ws->fixed) {
+        void* ps[] = {ws->qbuf, ws->tcount, ws->seg, ws->cand, ws->dslots, ws->dlists};
+        for (void* p : ps)
+            if (p)
+                cudaFree(p);
+    }
     if (ws->owns_staging) {
-        void* st[] = {ws->q_tokens, ws->q_offsets, ws->out_ids, ws->out_scores};
+        void* st[] = {ws->q_tokens, ws->q_offsets, ws->q_k, ws->out_ids, ws->out_scores};
         for (void* p : st)
             if (p)
                 cudaFree(p);
     }
-    ws->shift = nullptr;
-    ws->thresh = nullptr;
-    ws->qpost = nullptr;
-    ws->tcount = nullptr;
-    ws->seg = nullptr;
-    ws->cand = nullptr;
+    bm25_workspace clean;
+    clean.device = ws->device;
+    *ws = clean;
 }
 
 int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_tokens,
-                    const int64_t* q_off, int32_t nq, int64_t n_tok, int32_t k, int32_t* out_ids,
-                    float* out_scores, const Plan& plan, cudaStream_t s)
+                    const int64_t* q_off, int32_t nq, int64_t n_tok, const int32_t* q_k,
+                    int32_t kmax, int32_t* out_ids, float* out_scores, const Plan& plan,
+                    cudaStream_t s)
 {
-    const int32_t tile_docs = plan.tile_docs;
     if (nq == 0)
         return BM25_OK;
     DeviceInfo di;
     BM25_TRY(device_info(&di));
     const int64_t N = ix->n_docs;
-    const int32_t kprime = (int32_t)std::min<int64_t>(k, N);
-    int32_t W = tile_docs > 0 ? tile_docs : 12288;
-    // multiples of 128 keep the shared-memory carve-up 16-byte aligned
-    int64_t w_need = (N + 127) / 128 * 128;
-    if (W > w_need)
-        W = (int32_t)w_need;
-    const int64_t n_tiles64 = (N + W - 1) / W;
-    if (n_tiles64 > 65536)
-        return set_error(BM25_E_INVALID, "%lld doc tiles of %d documents: use wider tiles",
-                         (long long)n_tiles64, W);
-    const int32_t n_tiles = (int32_t)n_tiles64;
-    if ((int64_t)nq * n_tiles >= INT32_MAX)
-        return set_error(BM25_E_INVALID, "%d queries x %d doc tiles is too many work items for "
-                         "one call", nq, n_tiles);
-    BM25_TRY(workspace_reserve(ix, ws, nq, n_tok, kprime, n_tiles));
-
+    Geometry g;
+    BM25_TRY(geometry(ix, ws, nq, kmax, plan, &g));
+    BM25_TRY(reserve(ix, ws, g, n_tok, s));
+    const int32_t W = g.W, n_tiles = g.n_tiles, kstride = g.kstride;
     const int max_blocks = di.sm_count * 16;
-    int g0 = (int)std::min<int64_t>((nq + 255) / 256, max_blocks);
-    {
-        ProfileScope ps_("k_query_prep", s);
-        k_query_prep<<<std::max(g0, 1), 256, 0, s>>>(q_tokens, n_tok, q_off, nq, ix->s0,
-                                                      ix->indptr, ix->vocab, ws->shift,
-                                                      ws->thresh, ws->qpost, ix->status);
-    }
-    count_launch();
-    BM25_LAUNCH_CHECK();
+
+    // R1 once for every token of the batch
     const int64_t n_seg = n_tok * ((int64_t)n_tiles + 1);
     if (n_seg > 0) {
-        int g1 = (int)std::min<int64_t>((n_seg + 255) / 256, max_blocks);
+        const int g1 = (int)std::min<int64_t>((n_seg + 255) / 256, max_blocks);
         {
             ProfileScope ps_("k_seg_bounds", s);
             k_seg_bounds<<<g1, 256, 0, s>>>(q_tokens, n_tok, ix->indptr, ix->indices, ix->vocab, W,
@@ -1101,53 +1573,81 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
         count_launch();
         BM25_LAUNCH_CHECK();
     }
+
+    // launch shapes that do not depend on the sub-batch
     const size_t smem = tile_smem_bytes(W, plan.threads);
-    const int64_t n_items = (int64_t)nq * n_tiles;
-    auto launch_tile = [&](auto kernel, int threads) -> int {
-        BM25_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-        int per_sm = 0;
-        BM25_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads,
-                                                                    smem));
-        if (per_sm < 1)
-            return set_error(BM25_E_INVALID, "doc tile of %d documents does not fit on an SM", W);
+    auto tile_kernel = plan.threads == 128   ? k_tile_topk<128>
+                       : plan.threads == 256 ? k_tile_topk<256>
+                                             : k_tile_topk<512>;
+    BM25_CUDA_TRY(cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    int per_sm = 0;
+    BM25_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_kernel,
+                                                                plan.threads, smem));
+    if (per_sm < 1)
+        return set_error(BM25_E_INVALID, "doc tile of %d documents does not fit on an SM", W);
 #ifdef BM25_PHASE_TIMING
-        if (const char* e = getenv("BM25_CTAS_PER_SM"))
-            per_sm = std::min(per_sm, atoi(e));
+    if (const char* e = getenv("BM25_CTAS_PER_SM"))
+        per_sm = std::min(per_sm, atoi(e));
 #endif
-        const int g2 = (int)std::min<int64_t>(n_items, (int64_t)di.sm_count * per_sm);
-        {
-            ProfileScope ps_("k_tile_topk", s);
-            kernel<<<g2, threads, smem, s>>>(q_tokens, n_tok, q_off, nq, N, ix->indices, ix->data,
-                                             ws->seg, W, n_tiles, kprime, ws->thresh, ws->qpost,
-                                             ws->tcount, ws->cand);
-        }
-        count_launch();
-        BM25_LAUNCH_CHECK();
-        return BM25_OK;
-    };
-    if (plan.threads == 128)
-        BM25_TRY(launch_tile(k_tile_topk<128>, 128));
-    else if (plan.threads == 256)
-        BM25_TRY(launch_tile(k_tile_topk<256>, 256));
-    else
-        BM25_TRY(launch_tile(k_tile_topk<512>, 512));
-    int sz = 1;
-    while (sz < kprime)
-        sz <<= 1;
-    const int32_t buf_cap =
-        (int32_t)std::min<int64_t>(kMergeBufCap, (int64_t)n_tiles * kprime);
-    const size_t msmem = (size_t)sz * sizeof(u64) + (size_t)buf_cap * sizeof(u64) +
+    int sz_all = 1;
+    while (sz_all < kstride)
+        sz_all <<= 1;
+    const int32_t buf_cap = (int32_t)std::min<int64_t>(kMergeBufCap, (int64_t)n_tiles * kstride);
+    const size_t msmem = (size_t)sz_all * sizeof(u64) + (size_t)buf_cap * sizeof(u64) +
                          (size_t)(n_tiles + 1) * sizeof(uint32_t);
     BM25_CUDA_TRY(cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)msmem));
-    {
-        ProfileScope ps_("k_merge", s);
-        k_merge<<<nq, kMergeThreads, msmem, s>>>(ws->cand, ws->tcount, nq, n_tiles, kprime, k,
-                                                 ws->shift, out_ids, out_scores, buf_cap);
+    if (g.dense_ctas > 0)
+        BM25_CUDA_TRY(cudaFuncSetAttribute(k_dense_topk,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)g.dense_smem));
+
+    for (int32_t q0 = 0; q0 < nq; q0 += g.nq_sub) {
+        const int32_t nb = std::min(g.nq_sub, nq - q0);
+        int32_t* ids = out_ids + (int64_t)q0 * kmax;
+        float* scores = out_scores + (int64_t)q0 * kmax;
+        const int64_t* qo = q_off + q0;
+        BM25_CUDA_TRY(cudaMemsetAsync(ws->ctr, 0, 4 * sizeof(uint32_t), s));
+        {
+            const int g0 = (int)std::min<int64_t>((nb + 255) / 256, max_blocks);
+            ProfileScope ps_("k_query_prep", s);
+            k_query_prep<<<std::max(g0, 1), 256, 0, s>>>(
+                q_tokens, n_tok, qo, nb, q0 == 0, q0 + nb == nq, q_k ? q_k + q0 : nullptr, kmax,
+                N, ix->s0, ix->indptr, ix->vocab, g.dense_max, ws->shift, ws->qkp, ws->lrec,
+                ws->lpost, ws->thresh, ws->sq, ws->ctr, ix->status);
+        }
+        count_launch();
+        BM25_LAUNCH_CHECK();
+        {
+            const int g2 = (int)std::min<int64_t>((int64_t)nb * n_tiles,
+                                                  (int64_t)di.sm_count * per_sm);
+            ProfileScope ps_("k_tile_topk", s);
+            tile_kernel<<<g2, plan.threads, smem, s>>>(N, ix->indices, ix->data, ws->seg, W,
+                                                       n_tiles, kstride, ws->lrec, ws->lpost,
+                                                       ws->ctr, ws->thresh, ws->tcount, ws->cand);
+        }
+        count_launch();
+        BM25_LAUNCH_CHECK();
+        {
+            ProfileScope ps_("k_merge", s);
+            k_merge<<<nb, kMergeThreads, msmem, s>>>(ws->cand, ws->tcount, ws->lrec, ws->ctr,
+                                                     n_tiles, kstride, kmax, ws->shift, ids,
+                                                     scores, buf_cap);
+        }
+        count_launch();
+        BM25_LAUNCH_CHECK();
+        if (g.dense_ctas > 0) {
+            const int g4 = std::min(g.dense_ctas, nb);
+            ProfileScope ps_("k_dense_topk", s);
+            k_dense_topk<<<g4, kDenseThreads, g.dense_smem, s>>>(
+                q_tokens, n_tok, qo, ws->qkp, ws->shift, ix->indptr, ix->indices, ix->data,
+                ix->vocab, N, ws->sq, ws->ctr, ws->dslots, ws->dlists, g.list_cap, kstride, kmax,
+                ids, scores);
+            count_launch();
+            BM25_LAUNCH_CHECK();
+        }
     }
-    count_launch();
-    BM25_LAUNCH_CHECK();
     return BM25_OK;
 }
 

@@ -19,6 +19,14 @@ pytestmark = pytest.mark.gpu
 
 VARIANTS = ["lucene", "robertson", "atire", "bm25l", "bm25+"]
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "toy_corpus.json")
+# accumulator plans every retrieval check runs under: all queries on the
+# doc-tiled path, all on the dense path, and a split by postings count
+PLANS = {"tiled": (2, 0), "dense": (3, 0), "mixed": (1, 3000)}
+
+
+def _plan(ix, name):
+    acc, dmax = PLANS[name]
+    ix.set_plan(acc, 0, 0, dmax)
 
 
 @pytest.fixture(scope="module")
@@ -118,8 +126,10 @@ def test_tiny_workload_build_and_retrieve(torch_dev, variant):
     ix = _build(torch_dev, c, variant)
     orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.VARIANTS[variant], 1.5, 0.75, 0.5)
     _check_structure(ix, orc)
-    for k in (1, 10, 100):
-        _check_retrieval(torch_dev, ix, orc, q, k, where=f"{variant} k={k}")
+    for name in PLANS:
+        _plan(ix, name)
+        for k in (1, 10, 100):
+            _check_retrieval(torch_dev, ix, orc, q, k, where=f"{variant} {name} k={k}")
     ix.close()
 
 
@@ -142,10 +152,11 @@ def test_retrieval_across_tiles(torch_dev, tile_docs, threads):
     c = synth.make_corpus(9_999, 3_000, 1.1, ("poisson", 30), seed=2)
     q = synth.make_queries(64, 3_000, 1.1, ("uniform", 0, 12), seed=3)
     ix = _build(torch_dev, c, "bm25+")
-    ix.set_plan(0, tile_docs, threads)
-    assert ix.get_plan() == {"accumulator": 0, "tile_docs": tile_docs, "block_threads": threads}
+    ix.set_plan(2, tile_docs, threads)
+    assert ix.get_plan() == {"accumulator": 2, "tile_docs": tile_docs, "block_threads": threads,
+                             "dense_max_postings": 8192}
     orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.BM25PLUS)
-    for k in (1, 7, 100, 1000):
+    for k in (1, 7, 100, 1000, 2500):  # 2500: k' wider than the narrow tiles
         _check_retrieval(torch_dev, ix, orc, q, k, where=f"W={tile_docs} k={k}")
     ix.close()
 
@@ -165,8 +176,10 @@ def test_negative_and_zero_idf(torch_dev, variant):
     if variant == "robertson":
         assert (orc.idf[:6] < 0).any()
     q = synth.random_queries(rng, 6, 40, 5)
-    for k in (5, 50, 299, 300):
-        _check_retrieval(torch_dev, ix, orc, q, k, where=f"{variant} k={k}")
+    for name in PLANS:
+        _plan(ix, name)
+        for k in (5, 50, 299, 300):
+            _check_retrieval(torch_dev, ix, orc, q, k, where=f"{variant} {name} k={k}")
     ix.close()
 
 
@@ -181,8 +194,10 @@ def test_edge_cases(torch_dev):
         _check_structure(ix, orc)
         q = synth.Queries(np.array([1, 1, 0, 3, 4, 4, 2], np.int32),
                           np.array([0, 0, 3, 5, 7], np.int64))  # empty, dups, DF=0, mixed
-        for k in (1, 3, 5, 9):
-            _check_retrieval(torch_dev, ix, orc, q, k, where=f"{variant} edge k={k}")
+        for name in PLANS:
+            _plan(ix, name)
+            for k in (1, 3, 5, 9):
+                _check_retrieval(torch_dev, ix, orc, q, k, where=f"{variant} {name} edge k={k}")
         ix.close()
     one = synth.Corpus(np.array([0, 0, 0], np.int32), np.array([0, 3], np.int64), 1)
     ix = _build(torch_dev, one, "lucene")
@@ -279,4 +294,117 @@ def test_workspace_and_bad_retrieve_args(torch_dev):
     with pytest.raises(bm25.BM25Error):
         ix.set_plan(0, 0, 96)
     ws.close()
+    ix.close()
+
+
+# ------------------------------------------------ batches and plans -----
+
+def _check_rows(ids, sc, orc, queries, ks, n_docs, where):
+    """Row q: the oracle's top min(k_q, N), then -1 / -inf to the row's end."""
+    for q in range(queries.n_queries):
+        kp = min(int(ks[q]), n_docs)
+        full, ab = oracle.score_all(orc, queries.query(q), with_abs=True)
+        check_topk(ids[q, :kp], sc[q, :kp], full, ab, kp, where=f"{where} q{q}")
+        assert (ids[q, kp:] == -1).all() and np.isneginf(sc[q, kp:]).all(), f"{where} q{q} tail"
+
+
+@pytest.mark.parametrize("name", list(PLANS))
+def test_per_query_k_in_one_call(torch_dev, name):
+    """Queries with k in {1, 10, 100, 1000} mixed in one call; rows are
+    k_max wide."""
+    c = synth.make_corpus(20_000, 8_000, 1.1, ("poisson", 40), seed=21)
+    q = synth.make_queries(150, 8_000, 1.1, ("uniform", 0, 20), seed=22)
+    ix = _build(torch_dev, c, "bm25l")
+    orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.BM25L)
+    _plan(ix, name)
+    ks = np.random.default_rng(5).choice([1, 10, 100, 1000], q.n_queries).astype(np.int32)
+    ids, sc = ix.retrieve_batch(_to(torch_dev, q.tokens), _to(torch_dev, q.offsets), 1000,
+                                q_k=_to(torch_dev, ks))
+    ix.sync_status()
+    _check_rows(ids.cpu().numpy(), sc.cpu().numpy(), orc, q, ks, c.n_docs, f"{name} per-k")
+    # an entry outside [1, k_max] is reported through the status word
+    from paper_2407_03618_gb300 import bm25
+    bad = ks.copy()
+    bad[3] = 1001
+    ix.retrieve_batch(_to(torch_dev, q.tokens), _to(torch_dev, q.offsets), 1000,
+                      q_k=_to(torch_dev, bad))
+    with pytest.raises(bm25.BM25Error) as e:
+        ix.sync_status()
+    assert e.value.code == -1
+    ix.close()
+
+
+@pytest.mark.parametrize("name", list(PLANS))
+def test_long_queries_span_token_chunks(torch_dev, name):
+    """Queries of 60..200 tokens (more than one 64-token chunk)."""
+    c = synth.make_corpus(6_000, 4_000, 1.1, ("poisson", 30), seed=31)
+    q = synth.make_queries(40, 4_000, 1.1, ("uniform", 60, 200), 50, seed=32)
+    ix = _build(torch_dev, c, "lucene")
+    orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.LUCENE)
+    _plan(ix, name)
+    ix.set_plan(0, 2048, 256)
+    for k in (10, 300):
+        _check_retrieval(torch_dev, ix, orc, q, k, where=f"{name} long k={k}")
+    ix.close()
+
+
+def test_sub_batches_when_candidates_exceed_the_budget(torch_dev):
+    """k = 4096 over 196 doc tiles of 1024 needs 6.4 MB of tile candidates per
+    query, so 800 queries run as three sub-batches of at most 2 GiB."""
+    c = synth.make_corpus(200_000, 30_000, 1.05, ("poisson", 12), seed=41)
+    q = synth.make_queries(800, 30_000, 1.05, ("uniform", 1, 6), 100, seed=42)
+    ix = _build(torch_dev, c, "lucene")
+    orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.LUCENE)
+    ix.set_plan(2, 1024, 256)
+    ids, sc = ix.retrieve(_to(torch_dev, q.tokens), _to(torch_dev, q.offsets), 4096)
+    ix.sync_status()
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    for i in [0, 1, 334, 335, 336, 669, 670, 671, 799] + list(range(100, 800, 97)):
+        full, ab = oracle.score_all(orc, q.query(i), with_abs=True)
+        check_topk(ids[i], sc[i], full, ab, 4096, where=f"sub-batch q{i}")
+    ix.close()
+
+
+@pytest.mark.parametrize("name", ["tiled", "mixed"])
+def test_cuda_graph_capture_and_replay(torch_dev, name):
+    """A reserved workspace lets a call be captured in a CUDA graph; replays
+    on new query contents of the same shape give the oracle's results."""
+    import torch
+    from paper_2407_03618_gb300 import bm25
+    w = synth.WORKLOADS["tiny"]
+    c = w.corpus()
+    ix = _build(torch_dev, c, "bm25+")
+    orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.BM25PLUS)
+    _plan(ix, name)
+    qa = synth.make_queries(64, c.vocab, 1.1, ("uniform", 4, 4), seed=51)
+    qb = synth.make_queries(64, c.vocab, 1.1, ("uniform", 4, 4), seed=52)
+    assert np.array_equal(qa.offsets, qb.offsets)
+    qt = _to(torch_dev, qa.tokens)
+    qo = _to(torch_dev, qa.offsets)
+    ks = torch.full((64,), 10, dtype=torch.int32, device=torch_dev)
+    ids = torch.empty((64, 10), dtype=torch.int32, device=torch_dev)
+    sc = torch.empty((64, 10), dtype=torch.float32, device=torch_dev)
+    ws = bm25.Workspace(ix, 64, qt.numel(), 10)
+    s = torch.cuda.Stream()
+    ws.reserve(ix, 64, qt.numel(), 10, stream=s)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+        ix.retrieve_batch(qt, qo, 10, q_k=ks, out=(ids, sc), workspace=ws, stream=s)
+    for qq in (qa, qb, qa):
+        qt.copy_(_to(torch_dev, qq.tokens))
+        g.replay()
+        torch.cuda.synchronize()
+        ix.sync_status()
+        _check_rows(ids.cpu().numpy(), sc.cpu().numpy(), orc, qq, np.full(64, 10), c.n_docs,
+                    f"graph {name}")
+    # capturing a call the workspace is too small for fails instead of allocating
+    small = bm25.Workspace(ix, 1, 1, 1)
+    g2 = torch.cuda.CUDAGraph()
+    with pytest.raises(bm25.BM25Error):
+        with torch.cuda.graph(g2, stream=s, capture_error_mode="thread_local"):
+            ix.retrieve_batch(qt, qo, 10, out=(ids, sc), workspace=small, stream=s)
+    del g, g2
+    ws.close()
+    small.close()
     ix.close()
