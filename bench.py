@@ -48,6 +48,9 @@ def parse():
                    help="use only the first N queries of the batch (small profiler cases)")
     p.add_argument("--no-extras", action="store_true",
                    help="only the timed steps (used for profiler runs)")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the library's default plan instead of autotuning it")
+    p.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     return p.parse_args()
 
 
@@ -180,7 +183,9 @@ def reference_arm(args):
 def kernel_bytes(name, ctx):
     """Algorithmic bytes per launch of the kernels a roofline is quoted for."""
     if name == "k_tile_topk":
-        return ctx["retrieval_bytes"]
+        return ctx["tile_bytes"]
+    if name == "k_dense_topk":
+        return ctx["dense_bytes"]
     if name == "k_radix_downsweep":
         return 16 * ctx["n_tokens"]  # read key + doc, write key + doc, 4 B each
     if name == "k_radix_upsweep":
@@ -223,9 +228,22 @@ def main():
     sc = torch.empty((nq, k), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    # the retrieval plan: autotuned once on this batch (a resident index),
+    # then set on the index each step builds
+    tuned = None
+    if not args.no_autotune:
+        ixt = bm25.Index.build(tok, off, corpus.vocab, args.variant, prm["k1"], prm["b"],
+                               prm["delta"])
+        tuned = ixt.autotune(qt, qo, k)
+        ixt.close()
+    plan = tuned[0] if tuned else None
+
     def step():
         ix = bm25.Index.build(tok, off, corpus.vocab, args.variant, prm["k1"], prm["b"],
                               prm["delta"])
+        if plan:
+            ix.set_plan(plan["accumulator"], plan["tile_docs"], plan["block_threads"],
+                        plan["dense_max_postings"])
         ix.retrieve(qt, qo, k, out=(ids, sc))
         ix.close()
 
@@ -273,9 +291,12 @@ def main():
                        "l2": "inputs larger than L2 (no flush needed)",
                        "parallelism": f"replicated index, {nq} queries per GPU"},
             "clocks": clock_info, "gpu_launches": launches * world}
+    if tuned:
+        line["plan"] = {"chosen": tuned[0], "ms": tuned[1],
+                        "tried": [{"plan": p_, "ms": m_} for p_, m_ in tuned[2]]}
 
     if not args.no_extras and rank == 0:
-        extras(args, line, bm25, corpus, queries, tok, off, qt, qo, ids, sc, dev, prof, w)
+        extras(args, line, bm25, corpus, queries, tok, off, qt, qo, ids, sc, dev, prof, w, plan)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -283,7 +304,7 @@ def main():
     return 0
 
 
-def extras(args, line, bm25, corpus, queries, tok, off, qt, qo, ids, sc, dev, prof, w):
+def extras(args, line, bm25, corpus, queries, tok, off, qt, qo, ids, sc, dev, prof, w, plan):
     import torch
     prm = w.params
     k = args.k
@@ -299,13 +320,32 @@ def extras(args, line, bm25, corpus, queries, tok, off, qt, qo, ids, sc, dev, pr
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
     ix = bm25.Index.build(tok, off, corpus.vocab, args.variant, prm["k1"], prm["b"], prm["delta"])
+    if plan:
+        ix.set_plan(plan["accumulator"], plan["tile_docs"], plan["block_threads"],
+                    plan["dense_max_postings"])
+    used = ix.get_plan()
     info = ix.info()
     ex_indptr = ix.export()["indptr"]
     df = np.diff(ex_indptr)
     qlen = np.diff(queries.offsets)
     postings = int(df[queries.tokens].sum())
     retrieval_bytes = 8 * postings + 20 * int(qlen.sum()) + 8 * k * nq
-    ctx = {"retrieval_bytes": retrieval_bytes, "n_tokens": corpus.n_tokens, "nnz": info["nnz"]}
+    # per-query algorithmic bytes (postings, indptr pair and token, output),
+    # split the way the library routes queries: at most dense_max postings ->
+    # dense path, the rest tiled
+    cs = np.concatenate([[0], np.cumsum(df[queries.tokens], dtype=np.int64)])
+    qpost = cs[queries.offsets[1:]] - cs[queries.offsets[:-1]]
+    qbytes = 8 * qpost + 20 * qlen + 8 * k
+    dense_on = used["accumulator"] in (bm25.ACC_AUTO, bm25.ACC_L2_DENSE)
+    dmax = used["dense_max_postings"] if used["accumulator"] == bm25.ACC_AUTO else \
+        max(used["dense_max_postings"], 1 << 19)
+    is_dense = (qpost <= dmax) if dense_on else np.zeros(nq, bool)
+    ctx = {"retrieval_bytes": retrieval_bytes, "tile_bytes": int(qbytes[~is_dense].sum()),
+           "dense_bytes": int(qbytes[is_dense].sum()), "n_tokens": corpus.n_tokens,
+           "nnz": info["nnz"]}
+    line["routing"] = {"plan": used, "dense_queries": int(is_dense.sum()),
+                       "tiled_queries": int((~is_dense).sum()),
+                       "dense_postings_frac": float(qpost[is_dense].sum() / max(1, qpost.sum()))}
 
     # kernel shares over the timed region
     total_ms = sum(v[1] for v in prof.values()) or 1.0
@@ -344,7 +384,7 @@ def extras(args, line, bm25, corpus, queries, tok, off, qt, qo, ids, sc, dev, pr
             line["roofline"] = {"kernel": top, "bound": "hbm", "achieved": None,
                                 "peak": hbm_peak, "unit": "GB/s", "frac": None, "traffic": None}
         others = {}
-        for n in ("k_tile_topk", "k_radix_downsweep"):
+        for n in ("k_tile_topk", "k_dense_topk", "k_radix_downsweep"):
             if n in prof and n != top:
                 others[n] = roofline_for(n, *prof[n])
         line["roofline_other"] = others
@@ -398,6 +438,24 @@ def extras(args, line, bm25, corpus, queries, tok, off, qt, qo, ids, sc, dev, pr
     line["plain_path"] = {"queries": P, "qps": P / wall,
                           "p50_ms": lat[len(lat) // 2], "p99_ms": lat[int(0.99 * (len(lat) - 1))],
                           "batched_speedup": (nq / (r_ms / 1e3)) / (P / wall)}
+    # the same one-query calls through the host-buffer entry point (query in,
+    # result out of host memory): comparable with served latency
+    hl = []
+    hq = [(queries.query(i).astype(np.int32), np.array([0, queries.query(i).shape[0]], np.int64))
+          for i in range(min(P, 300))]
+    hout = (np.zeros((1, k), np.int32), np.zeros((1, k), np.float32))
+    for t_, o_ in hq[:10]:
+        ix.retrieve_host(t_, o_, k, out=hout)
+    t0 = time.perf_counter()
+    for t_, o_ in hq:
+        a_ = time.perf_counter()
+        ix.retrieve_host(t_, o_, k, out=hout)
+        hl.append((time.perf_counter() - a_) * 1e3)
+    hwall = time.perf_counter() - t0
+    hl.sort()
+    line["plain_path"]["host"] = {"queries": len(hq), "qps": len(hq) / hwall,
+                                  "p50_ms": hl[len(hl) // 2],
+                                  "p99_ms": hl[int(0.99 * (len(hl) - 1))]}
     line["batched_latency_ms"] = {"p50": r_ms, "p99": r_ms,
                                   "note": "every query of a batch completes with the batch"}
 
@@ -442,11 +500,86 @@ def extras(args, line, bm25, corpus, queries, tok, off, qt, qo, ids, sc, dev, pr
     line["e2e"] = {"value": nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": 8 * nq * k, "ms_per_step": e2e_s * 1e3}
 
+    if not args.no_serving:
+        line["serving"] = serving(args, bm25, corpus, queries, tok, off, dev, w, plan,
+                                  line["plain_path"])
+
     # CPU oracle on a bounded sample (rank 0, N = 1 only)
     if line["n_gpus"] == 1:
         _, cpu = oracle_rate(corpus, queries, args.variant, k, args.cpu_sample_queries,
                              os.cpu_count() or 1, prm)
         line["cpu_baseline"] = cpu
+
+
+def serving(args, bm25, corpus, queries, tok, off, dev, w, plan, plain):
+    """Requests one query at a time with Poisson arrivals over eight resident
+    indexes (the batch's corpus and seven smaller ones of the other workload
+    shapes), k drawn from {10, 100, 1000}, through the library's
+    continuous-batching server.  Latency = submit to result, measured by the
+    server; compared with the one-query-per-launch path (plain_path)."""
+    import torch
+    prm = w.params
+    shapes = [  # (docs, vocab, zipf s, length law): the tiny, 1M and passage shapes, scaled
+        (10_000, 5_000, 1.1, ("poisson", 60)), (25_000, 20_000, 1.05, ("lognormal", 60, 0.6)),
+        (50_000, 50_000, 1.0, ("lognormal", 56, 0.5)), (100_000, 5_000, 1.1, ("poisson", 60)),
+        (200_000, 100_000, 1.05, ("lognormal", 60, 0.6)),
+        (400_000, 200_000, 1.0, ("lognormal", 56, 0.5)),
+        (150_000, 50_000, 1.1, ("poisson", 30))]
+    idx, vocabs = [], []
+    ix0 = bm25.Index.build(tok, off, corpus.vocab, args.variant, prm["k1"], prm["b"], prm["delta"])
+    if plan:
+        ix0.set_plan(plan["accumulator"], plan["tile_docs"], plan["block_threads"],
+                     plan["dense_max_postings"])
+    idx.append(ix0)
+    vocabs.append(corpus.vocab)
+    for i, (n, v, s_, L) in enumerate(shapes):
+        c = synth.make_corpus(n, v, s_, L, seed=100 + i)
+        idx.append(bm25.Index.build(torch.from_numpy(c.tokens).to(dev),
+                                    torch.from_numpy(c.doc_offsets).to(dev), c.vocab,
+                                    args.variant, prm["k1"], prm["b"], prm["delta"]))
+        vocabs.append(c.vocab)
+    rng = np.random.default_rng(11)
+    out = {"indexes": [ix.info()["n_docs"] for ix in idx], "rates": []}
+    srv = bm25.Server(idx, max_batch_queries=2048, max_inflight=3, k_max=1000)
+    for rate, n_req in ((5_000, 5_000), (20_000, 20_000), (50_000, 40_000)):
+        which = rng.integers(0, len(idx), n_req)
+        lens = rng.integers(1, 33, n_req)
+        ks = rng.choice([10, 100, 1000], n_req)
+        reqs = []
+        for i in range(n_req):
+            if which[i] == 0:  # a query of the batch's own workload
+                reqs.append(queries.query(int(rng.integers(0, queries.n_queries))))
+            else:
+                reqs.append(synth.zipf_sampler(vocabs[which[i]], 1.05)(rng, int(lens[i])))
+        gaps = rng.exponential(1.0 / rate, n_req)
+        srv.stats(reset=True)
+        tickets = []
+        t0 = time.perf_counter()
+        due = t0
+        for i in range(n_req):
+            due += gaps[i]
+            while time.perf_counter() < due:
+                pass
+            tickets.append(srv.submit(int(which[i]), reqs[i], int(ks[i])))
+        t_sub = time.perf_counter() - t0
+        for i, tk in enumerate(tickets):
+            srv.poll(tk, int(ks[i]))
+        t_all = time.perf_counter() - t0
+        st = srv.stats()
+        out["rates"].append({"offered_qps": rate, "requests": n_req,
+                             "submit_s": t_sub, "achieved_qps": n_req / t_all,
+                             "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
+                             "max_ms": st["max_us"] / 1e3,
+                             "mean_batch": st["batched_queries"] / max(1, st["batches"]),
+                             "failed": st["failed"]})
+    srv.close()
+    for ix in idx:
+        ix.close()
+    out["plain_path_host"] = plain.get("host")
+    out["note"] = ("plain_path_host = one query per call through the host-buffer entry point "
+                   "on the 1M index at k=" + str(args.k) + ", back to back (latency without "
+                   "queueing); offered rates above its qps cannot be served by it")
+    return out
 
 
 if __name__ == "__main__":
