@@ -182,7 +182,7 @@ def reference_arm(args):
 
 def kernel_bytes(name, ctx):
     """Algorithmic bytes per launch of the kernels a roofline is quoted for."""
-    if name == "k_tile_topk":
+    if name == "k_tile_staged":
         return ctx["tile_bytes"]
     if name == "k_dense_topk":
         return ctx["dense_bytes"]
@@ -384,7 +384,7 @@ def extras(args, line, bm25, corpus, queries, tok, off, qt, qo, ids, sc, dev, pr
             line["roofline"] = {"kernel": top, "bound": "hbm", "achieved": None,
                                 "peak": hbm_peak, "unit": "GB/s", "frac": None, "traffic": None}
         others = {}
-        for n in ("k_tile_topk", "k_dense_topk", "k_radix_downsweep"):
+        for n in ("k_tile_staged", "k_dense_topk", "k_radix_downsweep"):
             if n in prof and n != top:
                 others[n] = roofline_for(n, *prof[n])
         line["roofline_other"] = others

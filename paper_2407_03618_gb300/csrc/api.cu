@@ -314,6 +314,7 @@ int bm25_index_import(int64_t n_docs, int64_t n_tokens, int64_t nnz, int32_t voc
     if (rc == BM25_OK) rc = cp(ix->doc_len, doc_len, sizeof(int32_t) * n_docs);
     if (rc == BM25_OK) rc = cp(ix->idf, idf, sizeof(double) * vocab);
     if (rc == BM25_OK) rc = cp(ix->s0, s0, sizeof(double) * vocab);
+    if (rc == BM25_OK) rc = pack_posts(ix, 0);
     if (rc == BM25_OK && cudaDeviceSynchronize() != cudaSuccess)
         rc = set_error(BM25_E_CUDA, "synchronisation failed");
     if (rc != BM25_OK) {

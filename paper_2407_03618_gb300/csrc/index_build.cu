@@ -13,7 +13,10 @@
 //   K4/K5 k_indptr       column starts (the exclusive prefix sum of DF) by a
 //                        lower bound over the term of each run; DF = difference
 //   K6 k_idf             IDF and S0 per term in FP64, FP32 score coefficient
-//   K7 k_score           S(t,D) - S0(t) per CSC entry in FP32
+//   K7 k_pad_posts       padding slots of the packed (doc, score) copy
+//   K8 k_score           S(t,D) - S0(t) per CSC entry in FP32, written to the
+//                        CSC and to the packed copy that staged retrieval
+//                        reads (each column 16-byte aligned)
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -380,16 +383,19 @@ __global__ void k_idf(const int64_t* __restrict__ indptr, int32_t vocab, int64_t
 __global__ void k_score(const int32_t* __restrict__ run_pos, const int32_t* __restrict__ run_term,
                         const int32_t* __restrict__ indices, const uint32_t* __restrict__ d_nnz,
                         const float* __restrict__ coef, const float* __restrict__ len_factor,
-                        int variant, float k1_plus_delta, int32_t* __restrict__ tf_out,
-                        float* __restrict__ data)
+                        int variant, float k1_plus_delta, const int64_t* __restrict__ indptr,
+                        int32_t* __restrict__ tf_out, float* __restrict__ data,
+                        uint2* __restrict__ posts)
 {
     const int64_t nnz = *d_nnz;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz;
          j += (int64_t)gridDim.x * blockDim.x) {
         int32_t tf = run_pos[j + 1] - run_pos[j];
         float f = (float)tf;
-        float a = len_factor[indices[j]];
-        float c = coef[run_term[j]];
+        const int32_t doc = indices[j];
+        const int32_t term = run_term[j];
+        float a = len_factor[doc];
+        float c = coef[term];
         float s;
         if (variant == BM25_L) {
             float cc = f * a;
@@ -397,8 +403,54 @@ __global__ void k_score(const int32_t* __restrict__ run_pos, const int32_t* __re
         } else {
             s = c * f / (f + a);
         }
+        s = (s == 0.0f) ? 0.0f : s;  // never -0.0: retrieval uses -0.0 as "untouched"
         tf_out[j] = tf;
-        data[j] = (s == 0.0f) ? 0.0f : s;  // never -0.0: retrieval uses -0.0 as "untouched"
+        data[j] = s;
+        const int64_t c0 = indptr[term];
+        posts[post_start(c0, term) + (j - c0)] = make_uint2((uint32_t)doc, __float_as_uint(s));
+    }
+}
+
+// The padding slots of the packed layout: after column t up to the start of
+// column t+1, and past the last column up to n_posts.
+__global__ void k_pad_posts(const int64_t* __restrict__ indptr, int32_t vocab, int64_t n_posts,
+                            uint2* __restrict__ posts)
+{
+    const uint2 pad = make_uint2(kPostPad, 0u);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= vocab;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t from, to;
+        if (t < vocab) {
+            from = post_start(indptr[t], t) + (indptr[t + 1] - indptr[t]);
+            to = post_start(indptr[t + 1], t + 1);
+        } else {
+            from = post_start(indptr[vocab], vocab);
+            to = n_posts;
+        }
+        for (int64_t p = from; p < to; p++)
+            posts[p] = pad;
+    }
+}
+
+// Packed entries from the CSC arrays (after an import): one thread per
+// entry finds its column by a binary search over indptr.
+__global__ void k_pack_posts(const int64_t* __restrict__ indptr, int32_t vocab, int64_t nnz,
+                             const int32_t* __restrict__ indices, const float* __restrict__ data,
+                             uint2* __restrict__ posts)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = 0, hi = vocab;  // last t with indptr[t] <= j
+        while (hi - lo > 1) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (indptr[mid] <= j)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const int64_t c0 = indptr[lo];
+        posts[post_start(c0, lo) + (j - c0)] =
+            make_uint2((uint32_t)indices[j], __float_as_uint(data[j]));
     }
 }
 
@@ -496,6 +548,30 @@ int alloc_index_arrays(bm25_index* ix, cudaStream_t s, bool fixed, bool per_entr
         BM25_TRY(pool_alloc(&ix->indices, ix->nnz, pool, s));
         BM25_TRY(pool_alloc(&ix->data, ix->nnz, pool, s));
         BM25_TRY(pool_alloc(&ix->tf, ix->nnz, pool, s));
+        ix->n_posts = ix->nnz + ix->vocab + 3;
+        BM25_TRY(pool_alloc(&ix->posts, ix->n_posts, pool, s));
+    }
+    return BM25_OK;
+}
+
+int pack_posts(bm25_index* ix, cudaStream_t s)
+{
+    DeviceInfo di;
+    BM25_TRY(device_info(&di));
+    const int max_blocks = di.sm_count * 16;
+    {
+        ProfileScope ps_("k_pad_posts", s);
+        k_pad_posts<<<grid_for((int64_t)ix->vocab + 1, 256, max_blocks), 256, 0, s>>>(
+            ix->indptr, ix->vocab, ix->n_posts, ix->posts);
+    }
+    count_launch();
+    BM25_LAUNCH_CHECK();
+    if (ix->nnz > 0) {
+        ProfileScope ps_("k_pack_posts", s);
+        k_pack_posts<<<grid_for(ix->nnz, 256, max_blocks), 256, 0, s>>>(
+            ix->indptr, ix->vocab, ix->nnz, ix->indices, ix->data, ix->posts);
+        count_launch();
+        BM25_LAUNCH_CHECK();
     }
     return BM25_OK;
 }
@@ -503,7 +579,7 @@ int alloc_index_arrays(bm25_index* ix, cudaStream_t s, bool fixed, bool per_entr
 void free_index_arrays(bm25_index* ix, cudaStream_t s)
 {
     void* ps[] = {ix->indptr, ix->indices, ix->data, ix->tf, ix->df,
-                  ix->doc_len, ix->idf, ix->s0, ix->status};
+                  ix->doc_len, ix->idf, ix->s0, ix->status, ix->posts};
     for (void* p : ps)
         if (p)
             cudaFreeAsync(p, s);
@@ -516,6 +592,8 @@ void free_index_arrays(bm25_index* ix, cudaStream_t s)
     ix->idf = nullptr;
     ix->s0 = nullptr;
     ix->status = nullptr;
+    ix->posts = nullptr;
+    ix->n_posts = 0;
 }
 
 int build_index_device(const int32_t* d_tokens, int64_t n_tokens, const int64_t* d_offsets,
@@ -666,14 +744,19 @@ int build_index_device(const int32_t* d_tokens, int64_t n_tokens, const int64_t*
                 k_idf<<<grid_for(vocab, 256, max_blocks), 256, 0, s>>>(
                     ix->indptr, vocab, n_docs, variant, k1, delta, ix->df, ix->idf, ix->s0, coef);
             }
-            count_launch(2);
+            {
+                ProfileScope ps_("k_pad_posts", s);
+                k_pad_posts<<<grid_for((int64_t)vocab + 1, 256, max_blocks), 256, 0, s>>>(
+                    ix->indptr, vocab, ix->n_posts, ix->posts);
+            }
+            count_launch(3);
             BM25_LAUNCH_CHECK();
             if (nnz > 0) {
                 {
                     ProfileScope ps_("k_score", s);
                     k_score<<<grid_for(nnz, 256, max_blocks), 256, 0, s>>>(
                         run_pos, run_term, ix->indices, d_total, coef, len_factor, variant,
-                        (float)(k1 + delta), ix->tf, ix->data);
+                        (float)(k1 + delta), ix->indptr, ix->tf, ix->data, ix->posts);
                 }
                 count_launch();
                 BM25_LAUNCH_CHECK();

@@ -63,6 +63,15 @@ struct DeviceInfo {
 int device_info(DeviceInfo* out);
 
 // ---- the index --------------------------------------------------------
+// Packed posting layout (bm25_index::posts): the first slot of column t.
+// Rounding indptr[t] + t up to an even number keeps the columns disjoint
+// (each gains at most one slot over the previous) and 16-byte aligned.
+__host__ __device__ inline int64_t post_start(int64_t indptr_t, int64_t t)
+{
+    return (indptr_t + t + 1) & ~int64_t(1);
+}
+constexpr uint32_t kPostPad = 0xffffffffu;  // doc id of a padding slot (beyond any document)
+
 struct Plan {
     int accumulator = BM25_ACC_AUTO;
     int32_t tile_docs = 12288;
@@ -90,6 +99,12 @@ struct bm25_index {
     int32_t* doc_len = nullptr;  // [n_docs]
     double* idf = nullptr;       // [vocab]
     double* s0 = nullptr;        // [vocab]
+    // The same entries packed as (doc id, S - S0 bits) pairs for staged
+    // retrieval: column t starts at post_start(indptr[t], t), an even
+    // position, so every column begins on a 16-byte boundary; the 0-2 slots
+    // between columns and the slots past the last one hold kPostPad.
+    uint2* posts = nullptr;      // [n_posts]
+    int64_t n_posts = 0;         // nnz + vocab + 3
     int* status = nullptr;       // device status word (first error code)
     bm25::Plan plan;
     bm25_workspace* default_ws = nullptr;
@@ -140,6 +155,9 @@ int build_index_device(const int32_t* d_tokens, int64_t n_tokens, const int64_t*
 // (per_entry) from the library's pool on stream s.
 int alloc_index_arrays(bm25_index* ix, cudaStream_t s, bool fixed, bool per_entry);
 void free_index_arrays(bm25_index* ix, cudaStream_t s);
+// Fills ix->posts from indptr / indices / data (used after an import; the
+// build writes the packed entries as it scores them).  Stream-ordered.
+int pack_posts(bm25_index* ix, cudaStream_t s);
 int pool_for_current_device(cudaMemPool_t* out);
 
 // ---- retrieval (retrieve.cu) -------------------------------------------

@@ -2,22 +2,27 @@
 // Sec. 2 "Assigning Query Scores" and "Top-k selection"; Sec. 2.1 for the
 // shift added back to every returned score).
 //
-// Doc-tiled shared-memory path, four launches per call:
+// Launches per call (per sub-batch for R0, R2, R3, R4):
 //   R0 k_query_prep   sum_i S0(q_i) per query in FP64; token / offset checks;
-//                     resets the per-query running threshold; counts the
-//                     query's postings (a bound on the documents it touches)
+//                     the query's postings (sum of DF); routes each query to
+//                     the dense path (few postings) or the doc-tiled path and
+//                     resets the running threshold of the tiled ones
 //   R1 k_seg_bounds   for every query token and every doc-tile boundary, the
 //                     first posting of the token's column at or past the
-//                     boundary (binary search: doc ids ascend in a column)
-//   R2 k_tile_topk    persistent CTAs over (doc tile, query) items: each item
-//                     scatter-adds its postings into FP32 accumulators in
-//                     shared memory, marks touched documents in a bitmask,
-//                     keeps the documents that clear the query's running
-//                     threshold, and radix-selects the tile's best k' of them
-//                     (including the lowest-id untouched documents, score 0,
-//                     when they can matter)
-//   R3 k_merge        per query: the k' best of the tiles' candidates,
+//                     boundary (binary search: doc ids ascend in a column),
+//                     as a slot of the packed (doc, score) layout
+//   R2 k_tile_staged  persistent CTAs over (doc tile, query) items: a
+//                     producer warp stages each item's posting segments into
+//                     shared memory with bulk asynchronous copies; consumer
+//                     warps scatter-add them into the tile's FP32
+//                     accumulators, claim each touched document once, keep
+//                     the ones that clear the query's running threshold and
+//                     select the tile's best k' (including the lowest-id
+//                     untouched documents, score 0, when they can matter)
+//   R3 k_merge        per tiled query: the k' best of the tiles' candidates,
 //                     re-keyed on the final score, sorted, written out
+//   R4 k_dense_topk   per dense-path query: scatter into a dense FP32 vector
+//                     in global memory (L2-resident), claim, select, write out
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -118,6 +123,9 @@ __global__ void k_query_prep(const int32_t* __restrict__ q_tokens, int64_t n_tok
 // seg[m * (n_tiles + 1) + j] = first position p in column q_tokens[m] with
 // indices[p] >= j * W (j = n_tiles gives the column end).  A token outside
 // the vocabulary gets an empty column.
+// PACKED: the positions are slots of the packed layout (bm25_index::posts,
+// column t shifted by post_start(indptr[t], t) - indptr[t]), as uint32.
+template <bool PACKED>
 __global__ void k_seg_bounds(const int32_t* __restrict__ q_tokens, int64_t n_tok,
                              const int64_t* __restrict__ indptr,
                              const int32_t* __restrict__ indices, int32_t vocab, int32_t W,
@@ -130,15 +138,18 @@ __global__ void k_seg_bounds(const int32_t* __restrict__ q_tokens, int64_t n_tok
         int64_t m = i / per;
         int32_t j = (int32_t)(i - m * per);
         int32_t t = q_tokens[m];
-        int64_t lo = 0, hi = 0;
+        int64_t lo = 0, hi = 0, shift = 0;
         if (t >= 0 && t < vocab) {
             lo = indptr[t];
             hi = indptr[t + 1];
+            if (PACKED)
+                shift = post_start(lo, t) - lo;
         }
+        int64_t pos;
         if (j == 0) {
-            seg[i] = (int32_t)lo;
+            pos = lo;
         } else if (j == n_tiles) {
-            seg[i] = (int32_t)hi;
+            pos = hi;
         } else {
             const int32_t target = j * W;
             while (lo < hi) {
@@ -148,8 +159,12 @@ __global__ void k_seg_bounds(const int32_t* __restrict__ q_tokens, int64_t n_tok
                 else
                     hi = mid;
             }
-            seg[i] = (int32_t)lo;
+            pos = lo;
         }
+        if (PACKED)
+            reinterpret_cast<uint32_t*>(seg)[i] = (uint32_t)(pos + shift);
+        else
+            seg[i] = (int32_t)pos;
     }
 }
 
@@ -205,12 +220,14 @@ __device__ __forceinline__ void select_bucket(SelectState& st, int shift)
 // __ballot_sync): keys sharing a prefix would otherwise serialise on one
 // shared-memory counter.  st.ctr must be 0 on entry.  With TRAIL_SYNC false
 // the block is not synchronised after the emit loop.
-template <bool TRAIL_SYNC, class Get, class Emit>
-__device__ void block_select_idx(SelectState& st, uint32_t n_index, uint32_t n_real, uint32_t k,
-                                 int skip, u64 common, Get get, Emit emit)
+// The selection runs on threads 0 .. nthreads-1 (whole warps), which meet at
+// sync() (__syncthreads() for a whole block, a named barrier for a subset).
+template <bool TRAIL_SYNC, class Sync, class Get, class Emit>
+__device__ void select_top(SelectState& st, uint32_t nthreads, Sync sync, uint32_t n_index,
+                           uint32_t n_real, uint32_t k, int skip, u64 common, Get get, Emit emit)
 {
     const int lane = threadIdx.x & 31;
-    const uint32_t stride = blockDim.x;
+    const uint32_t stride = nthreads;
     const uint32_t base0 = threadIdx.x & ~31u;
     u64 pm = 0, pf = 0;
     if (n_real > k) {
@@ -222,9 +239,9 @@ __device__ void block_select_idx(SelectState& st, uint32_t n_index, uint32_t n_r
         }
         for (int pass = skip; pass < 8; pass++) {
             const int shift = 56 - 8 * pass;
-            for (int i = threadIdx.x; i < 256; i += blockDim.x)
+            for (uint32_t i = threadIdx.x; i < 256; i += nthreads)
                 st.hist[i] = 0;
-            __syncthreads();
+            sync();
             const u64 cpm = st.pmask, cpf = st.prefix;
             for (uint32_t b = base0; b < n_index; b += stride) {
                 const uint32_t i = b + lane;
@@ -238,10 +255,10 @@ __device__ void block_select_idx(SelectState& st, uint32_t n_index, uint32_t n_r
                 if (dg != 0xffffffffu && (peers & lanemask_lt()) == 0)
                     atomicAdd(&st.hist[dg], (uint32_t)__popc(peers));
             }
-            __syncthreads();
+            sync();
             if (threadIdx.x < 32)
                 select_bucket(st, shift);
-            __syncthreads();
+            sync();
             if (st.bucket == st.need)
                 break;
         }
@@ -267,7 +284,15 @@ __device__ void block_select_idx(SelectState& st, uint32_t n_index, uint32_t n_r
         }
     }
     if (TRAIL_SYNC)
-        __syncthreads();
+        sync();
+}
+
+template <bool TRAIL_SYNC, class Get, class Emit>
+__device__ void block_select_idx(SelectState& st, uint32_t n_index, uint32_t n_real, uint32_t k,
+                                 int skip, u64 common, Get get, Emit emit)
+{
+    select_top<TRAIL_SYNC>(st, blockDim.x, [] { __syncthreads(); }, n_index, n_real, k, skip,
+                           common, get, emit);
 }
 
 // Number of leading bytes shared by every key whose high word lies in
@@ -278,68 +303,7 @@ __device__ __forceinline__ int common_bytes(uint32_t kmin, uint32_t kmax)
     return x ? (__clz(x) >> 3) : 4;
 }
 
-// ---- R2 -----------------------------------------------------------------------
-// Dynamic shared memory: acc[W] FP32 | SelectState | TileStage |
-// surv_val[WARPS * SPW] FP32 | surv_doc[WARPS * SPW] (doc id within the tile).
-//
-// An accumulator holds -0.0 until a posting lands on it (stored scores are
-// never -0.0 and -0.0 + x == x, so a touched accumulator is never -0.0).
-// Postings are added with fire-and-forget shared-memory reductions.  In the
-// common case an item's postings fit in one round of U per thread, and each
-// thread keeps the doc ids of its postings in registers; after the barrier
-// it claims each of those documents with an atomic exchange that returns the
-// document's sum and leaves a mark behind: the first claimer of a document
-// gets its score, later claimers (the document appeared in several columns)
-// see the mark.  With the query's threshold above 0 the mark is -0.0, so the
-// claim also resets the accumulator for the next item; otherwise (untouched
-// documents may compete) the mark is a NaN pattern, which keeps touched and
-// untouched documents apart until the tile is done.  Documents that clear
-// the threshold go, with their score, to a list of the claiming warp, sized
-// to the postings the warp owns (no overflow, no shared counters).  Items
-// with more postings than one round, or more tokens than one chunk, take a
-// path that walks the whole tile.
-#ifdef BM25_PHASE_TIMING
-// Diagnostic build only: per-phase cycle totals of k_tile_topk, summed over
-// CTAs (thread 0's view), and item statistics.
-__device__ unsigned long long g_phase[16];
-#define BM25_PHASE(I)                                                                \
-    do {                                                                             \
-        if (tid == 0) {                                                              \
-            const long long now_ = clock64();                                        \
-            ph_acc[I] += (unsigned long long)(now_ - ph_t);                          \
-            ph_t = now_;                                                             \
-        }                                                                            \
-    } while (0)
-#else
-#define BM25_PHASE(I) \
-    do {              \
-    } while (0)
-#endif
 constexpr uint32_t kUntouched = 0x80000000u;  // bits of -0.0f
-constexpr uint32_t kMarked = 0x7fffffffu;     // a NaN: claimed while untouched ones still count
-constexpr int kMaxWarps = 16;
-constexpr int kPostU = 8;                     // postings per thread in one round
-constexpr uint32_t kOutCap = 128;             // candidates an item stages for a deferred write
-
-struct TileStage {
-    int32_t lo[kTokChunk];
-    int32_t pre[kTokChunk + 1];
-    uint32_t scan[33];
-    int32_t qoff[2][2];                   // token range of the current / next item
-    uint32_t w_surv[kMaxWarps];           // per warp: its candidates
-    uint32_t w_pos[kMaxWarps];            // per warp: claimed documents scoring > 0
-    uint32_t w_kmin[kMaxWarps], w_kmax[kMaxWarps];  // per warp: candidate score keys
-    uint32_t list_pre[kMaxWarps + 1];     // exclusive prefix of the candidate lists
-    // The previous item's result, written to global memory by the next item
-    // once its first barrier has passed, so that no barrier waits on those
-    // writes: its candidates (when at most kOutCap), count and threshold.
-    u64 obuf[kOutCap];
-    int32_t o_item, o_q;
-    uint32_t o_count, o_tau, o_staged;  // o_staged = 0: written directly already
-    uint32_t q_post;                    // the current query's postings (all columns)
-    uint32_t q_kp;                      // the current query's k' = min(k, N)
-    uint32_t cutoff;                    // fill: docs [0, cutoff) hold the k' lowest untouched
-};
 
 // Bitonic sort of one 64-bit key per lane, descending across the warp.
 __device__ __forceinline__ u64 warp_sort_desc(u64 key)
@@ -360,18 +324,160 @@ __device__ __forceinline__ u64 warp_sort_desc(u64 key)
     return key;
 }
 
-// Counts the untouched documents (accumulator -0.0) among the tile's first
-// wd, up to k of them, and stores in *cutoff the smallest c such that docs
-// [0, c) hold min(k, untouched) of them.  All threads call it (block scans
-// over words of 32 documents); ends with __syncthreads().
-__device__ uint32_t first_untouched(const float* acc, int32_t wd, uint32_t k, uint32_t* scan_buf,
-                                    uint32_t* cutoff)
+// ---- R2 -----------------------------------------------------------------------
+// The tiled path as a producer/consumer pipeline.  One producer warp walks
+// the CTA's (doc tile, query) items ahead of the consumers: for each query
+// token it copies the token's posting segment inside the tile from the
+// packed (doc, score) layout into a shared-memory staging buffer with a
+// bulk asynchronous copy (cp.async.bulk, completion counted in bytes on an
+// mbarrier).  Segments start on 16-byte boundaries, so each copy is
+// widened to whole pairs: the extra slots hold postings of the same column
+// outside the tile, or padding, and are dropped by the doc-range test.
+// Staging buffers form a ring of kNumStages; an item larger than one buffer
+// spans several.  The consumer warps (named barrier 1):
+//   scatter  every staged posting in the tile is added to the tile's FP32
+//            accumulator in shared memory (Sec. 2 "Assigning Query Scores":
+//            the column slices summed per document); the atomic add returns
+//            the old value, and -0.0 there (untouched; stored scores are
+//            never -0.0) marks the document's first touch, which appends it
+//            to the tile's touched list;
+//   claim    the touched list is walked once: each document's sum is read
+//            and its accumulator reset to -0.0, and the sums that clear the
+//            query's running threshold become candidate keys (score, ~doc);
+//   select   the k' best candidates of the tile go to the item's slots, and
+//            a full set of k' raises the query's threshold (Sec. 2 "Top-k
+//            selection", restated as a radix select with exact pruning).
+// While a document scoring 0 can still rank (threshold at or below the key
+// of 0), items take a general path that counts first, adds the lowest-id
+// untouched documents when fewer than k' touched ones score above 0, and
+// selects over the touched list; candidates beyond kCandCap do the same.
+constexpr int kStageEntries = 1024;  // packed postings per staging buffer (8 KB)
+constexpr int kNumStages = 2;
+constexpr int kCandCap = 256;        // candidate keys an item collects in the common case
+constexpr int kWaitPolls = 1 << 22;  // mbarrier polls before a wait gives up
+
+struct StageHdr {
+    int32_t n;       // entries in the buffer
+    int32_t last;    // 1: the item's last buffer
+    int32_t item, tile, qi;  // work item, its doc tile, its query record
+    uint32_t kp, post, tau;  // the query's k', postings, threshold when staged
+};
+
+struct StagedFront {
+    unsigned long long full[kNumStages];   // producer -> consumers (bytes landed)
+    unsigned long long empty[kNumStages];  // consumers -> producer (buffer free)
+    StageHdr hdr[kNumStages];
+    uint32_t tl_count[2], lc[2], ovf[2];   // per item parity
+    uint32_t abort_flag;
+    uint32_t scan[33];
+    uint32_t cutoff;
+    SelectState st;
+};
+constexpr size_t kStagedFront = (sizeof(StagedFront) + 15) / 16 * 16;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Global -> shared bulk copy; bytes a multiple of 16, both addresses 16-byte
+// aligned; completion is counted on `bar`.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
+                                              unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"((unsigned long long)__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Warp-uniform bounded wait for the phase of `bar` with the given parity.
+// Gives up (false) after kWaitPolls polls or once another warp has given up.
+__device__ __forceinline__ bool warp_wait(unsigned long long* bar, uint32_t parity,
+                                          const volatile uint32_t* abort_flag)
+{
+    for (int i = 0; i < kWaitPolls; i++) {
+        if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity)))
+            return true;
+        if (*abort_flag)
+            return false;
+    }
+    return false;
+}
+
+template <int NT>
+__device__ __forceinline__ void consumer_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
+
+// Exclusive scan across the NT consumer threads (see block_exclusive_sum).
+template <int NT, typename T>
+__device__ __forceinline__ T consumer_exclusive_sum(T v, T* warp_buf, T* total)
+{
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T inc = warp_inclusive_sum(v);
+    if (lane == 31)
+        warp_buf[warp] = inc;
+    consumer_sync<NT>();
+    if (warp == 0) {
+        T w = (lane < NW) ? warp_buf[lane] : T(0);
+        T wi = warp_inclusive_sum(w);
+        if (lane < NW)
+            warp_buf[lane] = wi - w;
+        if (lane == NW - 1)
+            warp_buf[32] = wi;
+    }
+    consumer_sync<NT>();
+    T r = warp_buf[warp] + inc - v;
+    *total = warp_buf[32];
+    consumer_sync<NT>();
+    return r;
+}
+
+// first_untouched over the consumer threads.
+template <int NT>
+__device__ uint32_t consumer_first_untouched(const float* acc, int32_t wd, uint32_t k,
+                                             uint32_t* scan_buf, uint32_t* cutoff)
 {
     const int32_t nwords = (wd + 31) >> 5;
     uint32_t carry = 0;
     if (threadIdx.x == 0)
         *cutoff = (uint32_t)wd;
-    for (int w0 = 0; w0 < nwords && carry < k; w0 += blockDim.x) {
+    for (int w0 = 0; w0 < nwords && carry < k; w0 += NT) {
         const int w = w0 + threadIdx.x;
         uint32_t zeros = 0;
         if (w < nwords) {
@@ -382,65 +488,68 @@ __device__ uint32_t first_untouched(const float* acc, int32_t wd, uint32_t k, ui
         }
         const uint32_t z = __popc(zeros);
         uint32_t tot;
-        const uint32_t ex = block_exclusive_sum(z, scan_buf, &tot) + carry;
-        if (w < nwords && ex < k && ex + z >= k) {  // the k-th untouched one is here
+        const uint32_t ex = consumer_exclusive_sum<NT>(z, scan_buf, &tot) + carry;
+        if (w < nwords && ex < k && ex + z >= k) {
             uint32_t f = zeros;
             for (uint32_t c = ex + 1; c < k; c++)
                 f &= f - 1;
-            *cutoff = (uint32_t)((w << 5) + __ffs(f));  // one past it
+            *cutoff = (uint32_t)((w << 5) + __ffs(f));
         }
         carry += tot;
     }
-    __syncthreads();
+    consumer_sync<NT>();
     return carry < k ? carry : k;
 }
 
-template <int THREADS>
-constexpr size_t tile_lists_bytes()
+size_t staged_smem_bytes(int32_t W)
 {
-    return (size_t)(THREADS / 32) * (kPostU * 32) * (sizeof(float) + sizeof(uint16_t));
+    return kStagedFront + (size_t)W * (sizeof(float) + sizeof(uint16_t)) +
+           (size_t)kCandCap * sizeof(u64) + (size_t)kNumStages * kStageEntries * sizeof(uint2);
 }
 
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per SM
-    k_tile_topk(int64_t n_docs, const int32_t* __restrict__ indices,
-                const float* __restrict__ data, const int32_t* __restrict__ seg, int32_t W,
-                int32_t n_tiles, int32_t kstride, const int4* __restrict__ lrec,
-                const uint32_t* __restrict__ lpost, const uint32_t* __restrict__ ctr,
-                uint32_t* __restrict__ thresh, uint32_t* __restrict__ tcount,
-                u64* __restrict__ cand)
+// seg (packed): for query token m and tile boundary j, the first slot of the
+// token's packed column at or past document j * W (j = n_tiles: the column
+// end), from k_seg_bounds<true>.
+template <int CW>
+__global__ void __launch_bounds__((CW + 1) * 32)
+    k_tile_staged(int64_t n_docs, const uint2* __restrict__ posts, const uint32_t* __restrict__ seg,
+                  int32_t W, int32_t n_tiles, int32_t kstride, const int4* __restrict__ lrec,
+                  const uint32_t* __restrict__ lpost, const uint32_t* __restrict__ ctr,
+                  uint32_t* __restrict__ thresh, uint32_t* __restrict__ tcount,
+                  u64* __restrict__ cand, int* __restrict__ status)
 {
-    constexpr int WARPS = THREADS / 32;
-    constexpr int U = kPostU;
-    constexpr uint32_t SPW = U * 32;  // candidates a warp can claim in one round
-    static_assert(WARPS <= kMaxWarps, "too many warps");
+    constexpr int NT = CW * 32;  // consumer threads
     extern __shared__ __align__(16) unsigned char smem[];
-    float* acc = reinterpret_cast<float*>(smem);
-    SelectState& st = *reinterpret_cast<SelectState*>(acc + W);
-    TileStage& ts = *reinterpret_cast<TileStage*>(&st + 1);
-    float* surv_val = reinterpret_cast<float*>(&ts + 1);
-    uint16_t* surv_doc = reinterpret_cast<uint16_t*>(surv_val + WARPS * SPW);
+    StagedFront& sh = *reinterpret_cast<StagedFront*>(smem);
+    float* acc = reinterpret_cast<float*>(smem + kStagedFront);
+    uint16_t* tl = reinterpret_cast<uint16_t*>(acc + W);
+    u64* clist = reinterpret_cast<u64*>(tl + W);
+    uint2* stage = reinterpret_cast<uint2*>(clist + kCandCap);
+    SelectState& st = sh.st;
 
-    const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    const uint32_t ltmask = lanemask_lt();
-    const float neg0 = __uint_as_float(kUntouched);
-    float* my_sval = surv_val + warp * SPW;
-    uint16_t* my_sdoc = surv_doc + warp * SPW;
-    // the queries of the tiled path: records {q, first token, end token, k'}
-    // (the grid is sized for the whole sub-batch; CTAs past the items return)
     const int32_t nq = (int32_t)ctr[0];
     const int32_t n_items = nq * n_tiles;  // < 2^31 (checked by the host)
     if ((int32_t)blockIdx.x >= n_items)
         return;
-    for (int i = tid; i < W; i += THREADS)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float neg0 = __uint_as_float(kUntouched);
+    for (int i = tid; i < W; i += blockDim.x)
         acc[i] = neg0;
-
-    const int64_t per = (int64_t)n_tiles + 1;
-    // Tile-major order: item = tile * nq + q, tile 0 of every query first, so
-    // the running threshold of a query is usually known when its later tiles
-    // run, and the segments in flight at once all belong to one doc tile.
-    // (tile, q) advance by the grid stride without dividing.
+    if (tid == 0) {
+        for (int s = 0; s < kNumStages; s++) {
+            mbar_init(&sh.full[s], 1);
+            mbar_init(&sh.empty[s], CW);
+        }
+        sh.tl_count[0] = sh.tl_count[1] = 0;
+        sh.lc[0] = sh.lc[1] = 0;
+        sh.ovf[0] = sh.ovf[1] = 0;
+        sh.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const volatile uint32_t* abort_flag = &sh.abort_flag;
+    // tile-major items: item = tile * nq + q; (tile, q) advance by the grid
+    // stride without dividing
     const int32_t step_t = (int32_t)(gridDim.x / nq), step_q = (int32_t)(gridDim.x % nq);
     auto advance = [&](int32_t& t, int32_t& qq) {
         t += step_t;
@@ -450,466 +559,371 @@ __global__ void __launch_bounds__(THREADS, 3)  // three 12K-document tiles per S
             t++;
         }
     };
-    // Warp 0 runs a two-stage pipeline over the CTA's items: while item i is
-    // processed it loads the segment bounds of item i+1 (lane l: tokens 2l
-    // and 2l+1 of the first chunk) from the record it loaded during item
-    // i-1, and the record of item i+2.  Thread 0 also loads item i+1's
-    // threshold and postings count.  No load of the pipeline is consumed in
-    // the item it is issued in.  (q indexes the records here.)
-    int32_t tile = (int32_t)(blockIdx.x / nq), q = (int32_t)(blockIdx.x % nq);
-    int32_t t1 = tile, q1 = q;
-    advance(t1, q1);
-    int32_t t2 = t1, q2 = q1;
-    advance(t2, q2);
-    int4 rec1 = make_int4(0, 0, 0, 0);      // record of item i+1
-    int4 rec2 = make_int4(0, 0, 0, 0);      // record of item i+2
-    int32_t pf_lo0 = 0, pf_lo1 = 0, pf_hi0 = 0, pf_hi1 = 0;
-    uint32_t pf_tau = 0, pf_post = 0, pf_kp = 0;
-    auto load_seg = [&](int32_t t_, int32_t a_, int32_t b_) {
-        const int32_t m_ = a_ + 2 * tid;
-        pf_lo0 = pf_hi0 = pf_lo1 = pf_hi1 = 0;
-        if (m_ < b_) {
-            pf_lo0 = seg[(int64_t)m_ * per + t_];
-            pf_hi0 = seg[(int64_t)m_ * per + t_ + 1];
-        }
-        if (m_ + 1 < b_) {
-            pf_lo1 = seg[(int64_t)(m_ + 1) * per + t_];
-            pf_hi1 = seg[(int64_t)(m_ + 1) * per + t_ + 1];
-        }
-    };
-    if (tid == 0)
-        ts.o_item = -1;
-    if (tid < 32) {
-        const int4 r0 = lrec[q];
-        load_seg(tile, r0.y, r0.z);
-        if (tid == 0) {
-            ts.qoff[0][0] = r0.y;
-            ts.qoff[0][1] = r0.z;
-            pf_tau = *(volatile uint32_t*)&thresh[q];
-            pf_post = lpost[q];
-            pf_kp = (uint32_t)r0.w;
-        }
-        if ((int64_t)blockIdx.x + gridDim.x < n_items)
-            rec1 = lrec[q1];
-        if ((int64_t)blockIdx.x + 2 * (int64_t)gridDim.x < n_items)
-            rec2 = lrec[q2];
-    }
-    __syncthreads();
-#ifdef BM25_PHASE_TIMING
-    unsigned long long ph_acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    long long ph_t = clock64();
-#endif
+    const int64_t per = (int64_t)n_tiles + 1;
 
-    // writes the previous item's staged result (all threads; call between
-    // two barriers)
-    auto flush = [&]() {
-        const int32_t pi = ts.o_item;
-        if (pi < 0)
-            return;
-        const uint32_t pc = ts.o_count;
-        if (ts.o_staged) {
-            for (uint32_t t = tid; t < pc; t += THREADS)
-                cand[(int64_t)pi * kstride + t] = ts.obuf[t];
-            if (tid == 0)
-                tcount[pi] = pc;
-        }
-        if (tid == 0 && ts.o_tau != 0u)
-            atomicMax(&thresh[ts.o_q], ts.o_tau);
-    };
-    int parity = 0;
-    for (int32_t item = blockIdx.x; item < n_items; item += gridDim.x, parity ^= 1) {
-        const int64_t d0 = (int64_t)tile * W;
-        const int32_t wd = (int32_t)min((int64_t)W, n_docs - d0);
-        const int32_t m0 = ts.qoff[parity][0], m1 = ts.qoff[parity][1];
-        // warp 0: advance the pipeline once this item's prefetched values are used
-        auto pipeline = [&]() {
-            if (tid < 32) {
-                const int32_t nitem = item + (int32_t)gridDim.x;
-                if (nitem < n_items) {
-                    load_seg(t1, rec1.y, rec1.z);
-                    if (tid == 0) {
-                        ts.qoff[parity ^ 1][0] = rec1.y;
-                        ts.qoff[parity ^ 1][1] = rec1.z;
-                        pf_tau = *(volatile uint32_t*)&thresh[q1];
-                        pf_post = lpost[q1];
-                        pf_kp = (uint32_t)rec1.w;
-                    }
+    if (warp == CW) {
+        // ================================ producer ================================
+        // Loads run one item (segments, threshold) and two items (records)
+        // ahead of the item being staged.
+        int32_t t0 = (int32_t)(blockIdx.x / nq), q0 = (int32_t)(blockIdx.x % nq);
+        int32_t t1 = t0, q1 = q0;
+        advance(t1, q1);
+        int32_t t2 = t1, q2 = q1;
+        advance(t2, q2);
+        const int32_t G = (int32_t)gridDim.x;
+        auto load_pair = [&](int32_t t_, int4 r_, uint32_t* lo, uint32_t* hi) {
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int32_t m = r_.y + 2 * lane + h;
+                lo[h] = hi[h] = 0u;
+                if (m < r_.z) {
+                    lo[h] = seg[(int64_t)m * per + t_];
+                    hi[h] = seg[(int64_t)m * per + t_ + 1];
                 }
-                rec1 = rec2;
-                int32_t t3 = t2, q3 = q2;
-                advance(t3, q3);
-                if ((int64_t)nitem + 2 * (int64_t)gridDim.x < n_items)
-                    rec2 = lrec[q3];
-                t1 = t2;
-                q1 = q2;
-                t2 = t3;
-                q2 = q3;
             }
         };
-        if (tid == 0) {
-            st.tau = pf_tau;  // thread 0 holds the threshold; the others read st.tau
-            ts.q_post = pf_post;
-            ts.q_kp = pf_kp;
-        }
-        int32_t dd[U];        // doc ids (within the tile) of this thread's postings
-#pragma unroll
-        for (int u = 0; u < U; u++)
-            dd[u] = -1;
-        bool one_round = true;  // one chunk of tokens, one round of postings (uniform)
-
-        // ---- scatter-add the item's postings, a chunk of tokens at a time ----
-        for (int32_t mb = m0; mb < m1; mb += kTokChunk) {
-            const int cnt = min(kTokChunk, m1 - mb);
-            if (tid < 32) {
-                int32_t len[2];
+        int4 rec0 = lrec[q0];
+        int4 rec1 = make_int4(0, 0, 0, 0), rec2 = make_int4(0, 0, 0, 0);
+        if ((int64_t)blockIdx.x + G < n_items)
+            rec1 = lrec[q1];
+        uint32_t lo0[2], hi0[2];
+        load_pair(t0, rec0, lo0, hi0);
+        uint32_t tau0 = *(const volatile uint32_t*)&thresh[q0];
+        uint32_t post0 = lpost[q0];
+        int s = 0;
+        uint32_t round = 0;
+        bool aborted = false;
+        for (int32_t item = blockIdx.x; item < n_items; item += G) {
+            // next items' loads (consumed in the next iteration)
+            const bool has1 = (int64_t)item + G < n_items;
+            const bool has2 = (int64_t)item + 2 * (int64_t)G < n_items;
+            if (has2)
+                rec2 = lrec[q2];
+            uint32_t lo1[2] = {0u, 0u}, hi1[2] = {0u, 0u}, tau1 = 0u, post1 = 0u;
+            if (has1) {
+                load_pair(t1, rec1, lo1, hi1);
+                tau1 = *(const volatile uint32_t*)&thresh[q1];
+                post1 = lpost[q1];
+            }
+            // stage item (t0, q0)
+            const int32_t m0 = rec0.y, m1 = rec0.z;
+            for (int32_t mb = m0;; mb += 2 * 32) {
+                const int cnt = (int)min((int64_t)64, (int64_t)m1 - mb);  // may be <= 0
+                uint32_t a[2], n[2];
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
-                    const int i = 2 * tid + h;
-                    int32_t l = 0, hh = 0;
-                    if (mb == m0) {  // prefetched during the previous item
-                        l = h ? pf_lo1 : pf_lo0;
-                        hh = h ? pf_hi1 : pf_hi0;
-                    } else if (i < cnt) {
-                        const int32_t* sg = seg + (int64_t)(mb + i) * per + tile;
-                        l = sg[0];
-                        hh = sg[1];
+                    uint32_t lo = lo0[h], hi = hi0[h];
+                    if (mb != m0) {  // tokens past the first 64: loaded here
+                        lo = hi = 0u;
+                        const int32_t m = mb + 2 * lane + h;
+                        if (m < m1) {
+                            lo = seg[(int64_t)m * per + t0];
+                            hi = seg[(int64_t)m * per + t0 + 1];
+                        }
                     }
-                    if (i >= cnt)
-                        l = hh = 0;
-                    len[h] = hh - l;
-                    ts.lo[i] = l;
+                    const bool live = (2 * lane + h) < cnt && lo < hi;
+                    a[h] = lo & ~1u;
+                    n[h] = live ? ((hi + 1u) & ~1u) - a[h] : 0u;
                 }
-                const int32_t s2 = len[0] + len[1];
-                const int32_t inc = warp_inclusive_sum(s2);
-                ts.pre[2 * tid] = inc - s2;
-                ts.pre[2 * tid + 1] = inc - s2 + len[0];
-                if (tid == 31)
-                    ts.pre[kTokChunk] = inc;
-                if (mb == m0)
-                    pipeline();
-            }
-            __syncthreads();
-            BM25_PHASE(0);
-            if (mb == m0)
-                flush();
-            const int32_t total = ts.pre[kTokChunk];
-            if (mb != m0 || total > U * THREADS)
-                one_round = false;
-            // Warp w takes runs of 32 consecutive postings, r = w, w + WARPS, ...
-            // The token of its first run comes from one warp-uniform binary
-            // search; runs only move forward, so each later one (and each
-            // lane) steps on from there over finished or empty segments.
-            for (int32_t r0 = warp; r0 * 32 < total; r0 += U * WARPS) {
-                float vv[U];
-                int a = 0;
-                {
-                    const int32_t eb = r0 * 32;
-                    int b = cnt;  // pre[a] <= eb < pre[b]
-                    while (b - a > 1) {
-                        const int mid = (a + b) >> 1;
-                        if (ts.pre[mid] <= eb)
-                            a = mid;
-                        else
-                            b = mid;
+                const uint32_t s2 = n[0] + n[1];
+                const uint32_t inc = warp_inclusive_sum(s2);
+                const uint32_t off[2] = {inc - s2, inc - s2 + n[0]};
+                const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+                const bool last_chunk = (int64_t)mb + 64 >= (int64_t)m1;
+                if (total == 0u && !last_chunk)
+                    continue;
+                const uint32_t nst = total == 0u ? 1u : (total + kStageEntries - 1) / kStageEntries;
+                for (uint32_t k = 0; k < nst; k++) {
+                    const uint32_t e0 = k * kStageEntries;
+                    const uint32_t e1 = min(total, e0 + (uint32_t)kStageEntries);
+                    if (!aborted && !warp_wait(&sh.empty[s], (round & 1u) ^ 1u, abort_flag)) {
+                        aborted = true;
+                        if (lane == 0) {
+                            set_status(status, BM25_E_TIMEOUT);
+                            sh.abort_flag = 1;
+                        }
                     }
-                }
-                // runs this warp owns in this round (warp-uniform)
-                const int32_t n_runs = (total + 31) >> 5;
-                const int32_t u_max = (n_runs - r0 + WARPS - 1) / WARPS;
+                    if (lane == 0) {
+                        StageHdr& hd = sh.hdr[s];
+                        hd.n = aborted ? 0 : (int32_t)(e1 - e0);
+                        hd.last = (last_chunk && k + 1 == nst) ? 1 : 0;
+                        hd.item = item;
+                        hd.tile = t0;
+                        hd.qi = q0;
+                        hd.kp = (uint32_t)rec0.w;
+                        hd.post = post0;
+                        hd.tau = tau0;
+                        mbar_arrive_expect_tx(&sh.full[s],
+                                              aborted ? 0u : (e1 - e0) * (uint32_t)sizeof(uint2));
+                    }
+                    __syncwarp();
+                    if (!aborted) {
 #pragma unroll
-                for (int u = 0; u < U; u++) {
-                    const int32_t r = r0 + u * WARPS;
-                    const int32_t e = r * 32 + lane;
-                    dd[u] = -1;
-                    if (u < u_max && e < total) {
-                        while (ts.pre[a + 1] <= e)
-                            a++;
-                        const int32_t j = ts.lo[a] + (e - ts.pre[a]);
-                        dd[u] = __ldg(indices + j) - (int32_t)d0;
-                        vv[u] = __ldg(data + j);
+                        for (int h = 0; h < 2; h++) {
+                            const uint32_t lo_e = max(off[h], e0);
+                            const uint32_t hi_e = min(off[h] + n[h], e1);
+                            if (lo_e < hi_e)
+                                bulk_copy_g2s(stage + (size_t)s * kStageEntries + (lo_e - e0),
+                                              posts + a[h] + (lo_e - off[h]),
+                                              (hi_e - lo_e) * (uint32_t)sizeof(uint2), &sh.full[s]);
+                        }
+                    }
+                    if (++s == kNumStages) {
+                        s = 0;
+                        round++;
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < U; u++) {
-                    if (u < u_max) {
-                        if ((uint32_t)dd[u] < (uint32_t)wd)  // holds for any well-formed index
-                            atomicAdd(&acc[dd[u]], vv[u]);   // result unused: a reduction
-                        else
-                            dd[u] = -1;
-                    }
-                }
-            }
-            __syncthreads();
-            BM25_PHASE(1);
-        }
-        if (m0 == m1) {
-            pipeline();
-            __syncthreads();
-            flush();
-            __syncthreads();  // the flush reads the staged result before it is replaced
-        }
-
-        // tau = the query's running threshold: some tile already holds k'
-        // documents scoring at least tau, so a document below tau cannot be
-        // in the top k' (documents AT tau can, through the doc-id tie rule).
-        const uint32_t tau = st.tau;
-        const uint32_t qkp = ts.q_kp;                  // the query's k'
-        const uint32_t kp = min(qkp, (uint32_t)wd);    // at most wd from one tile
-        // Untouched documents score exactly 0: they can matter only if 0
-        // clears tau (and then only if fewer than k' touched ones score > 0),
-        // and only the k' lowest-id untouched documents of the whole corpus
-        // can: a tile whose predecessors hold at least k' untouched documents
-        // (true once t * W - postings of the query >= k') adds none.
-        const bool zero_counts = tau <= kZeroKey;
-        const bool may_fill = zero_counts && (int64_t)tile * W < (int64_t)qkp + ts.q_post;
-        // candidates go to the staging buffer when they fit (kp <= kOutCap),
-        // else straight to the item's slots
-        u64* out = kp <= kOutCap ? ts.obuf : cand + (int64_t)item * kstride;
-        uint32_t n_emit = 0;
-        uint32_t new_tau = 0;  // score key of (a lower bound on) the weakest emitted
-        bool tau_ok = false;   // new_tau is a valid bound to publish
-
-        if (one_round) {
-            // ---- claim each posting's document once; keep the candidates ---------
-            const uint32_t mark = zero_counts ? kMarked : kUntouched;
-            uint32_t pos = 0, kmin = 0xffffffffu, kmax = 0u, n_keep = 0;
-            // slots this warp filled in the single round (warp-uniform)
-            const int32_t u_max = (((ts.pre[kTokChunk] + 31) >> 5) - warp + WARPS - 1) / WARPS;
-            float cv[U];  // all exchanges first, so their latencies overlap
-#pragma unroll
-            for (int u = 0; u < U; u++)
-                cv[u] = (u < u_max && dd[u] >= 0)
-                            ? atomicExch(&acc[dd[u]], __uint_as_float(mark))
-                            : __uint_as_float(kUntouched);
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                if (u >= u_max)
+                if (last_chunk)
                     break;
+            }
+            // shift the pipeline
+            rec0 = rec1;
+            rec1 = rec2;
+            lo0[0] = lo1[0];
+            lo0[1] = lo1[1];
+            hi0[0] = hi1[0];
+            hi0[1] = hi1[1];
+            tau0 = tau1;
+            post0 = post1;
+            t0 = t1;
+            q0 = q1;
+            t1 = t2;
+            q1 = q2;
+            advance(t2, q2);
+        }
+        // the copies of the last fills have landed before the warp leaves
+        for (int k = 0; k < kNumStages; k++) {
+            if (s == 0) {
+                s = kNumStages;
+                if (round == 0)
+                    break;
+                round--;
+            }
+            s--;
+            warp_wait(&sh.full[s], round & 1u, abort_flag);
+        }
+        return;
+    }
+
+    // ================================ consumers ================================
+    int s = 0;
+    uint32_t round = 0, par = 0;
+    bool aborted = false;
+    for (int32_t item = blockIdx.x; item < n_items; item += gridDim.x, par ^= 1u) {
+        int32_t tile = 0, qi = 0;
+        uint32_t qkp = 0, post = 0, tau = 0;
+        // ---- scatter the item's staged postings ----------------------------------
+        for (;;) {
+            if (!aborted && !warp_wait(&sh.full[s], round & 1u, abort_flag)) {
+                aborted = true;
+                if (lane == 0) {
+                    set_status(status, BM25_E_TIMEOUT);
+                    sh.abort_flag = 1;
+                }
+            }
+            const StageHdr hd = sh.hdr[s];
+            // (clamped so that a header left stale by an abandoned wait
+            // still indexes inside the arrays)
+            tile = min(max(hd.tile, 0), n_tiles - 1);
+            qi = min(max(hd.qi, 0), nq - 1);
+            qkp = min(max(hd.kp, 1u), (uint32_t)kstride);
+            post = hd.post;
+            tau = hd.tau;
+            const int64_t d0 = (int64_t)tile * W;
+            const uint32_t wd = (uint32_t)min((int64_t)W, n_docs - d0);
+            const int32_t n_e = aborted ? 0 : min(max(hd.n, 0), kStageEntries);
+            const uint2* sb = stage + (size_t)s * kStageEntries;
+            for (int32_t e0 = warp * 32; e0 < n_e; e0 += NT) {
+                const int32_t e = e0 + lane;
+                bool first = false;
+                uint32_t dl = 0;
+                if (e < n_e) {
+                    const uint2 p = sb[e];
+                    dl = p.x - (uint32_t)d0;
+                    if (dl < wd) {
+                        const float old = atomicAdd(&acc[dl], __uint_as_float(p.y));
+                        first = __float_as_uint(old) == kUntouched;
+                    }
+                }
+                const uint32_t bal = __ballot_sync(0xffffffffu, first);
+                if (bal) {
+                    const int leader = __ffs(bal) - 1;
+                    uint32_t base = 0;
+                    if (lane == leader)
+                        base = atomicAdd(&sh.tl_count[par], (uint32_t)__popc(bal));
+                    base = __shfl_sync(0xffffffffu, base, leader);
+                    if (first)
+                        tl[base + __popc(bal & lanemask_lt())] = (uint16_t)dl;
+                }
+            }
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&sh.empty[s]);
+            if (++s == kNumStages) {
+                s = 0;
+                round++;
+            }
+            if (hd.last || aborted)
+                break;
+        }
+        consumer_sync<NT>();  // every posting added, every first touch listed
+
+        const int64_t d0 = (int64_t)tile * W;
+        const int32_t wd = (int32_t)min((int64_t)W, n_docs - d0);
+        const uint32_t n_t = sh.tl_count[par];
+        if (tid == 0) {  // counters of the next item (its scatter follows the claim barrier)
+            sh.tl_count[par ^ 1u] = 0;
+            sh.lc[par ^ 1u] = 0;
+            sh.ovf[par ^ 1u] = 0;
+        }
+        const uint32_t kp = min(qkp, (uint32_t)wd);
+        const bool zero_counts = tau <= kZeroKey;
+        const bool may_fill = zero_counts && (int64_t)tile * W < (int64_t)qkp + (int64_t)post;
+        u64* out = cand + (int64_t)item * kstride;
+        uint32_t n_emit = 0, new_tau = 0;
+        bool tau_ok = false;
+        auto csync = [] { consumer_sync<NT>(); };
+        auto emit = [&](u64 key, uint32_t slot) { out[slot] = key; };
+
+        if (!zero_counts) {
+            // ---- claim: read and reset each touched document once ------------------
+            for (uint32_t b0 = warp * 32; b0 < n_t; b0 += NT) {
+                const uint32_t t = b0 + lane;
                 bool keep = false;
-                const float v = cv[u];
-                const uint32_t vb = __float_as_uint(v);
-                uint32_t o = 0;
-                if (vb != kUntouched && vb != kMarked) {  // the first claim of the document
-                    o = order_f32(v);
-                    if (zero_counts)
-                        pos += (v > 0.0f);
-                    keep = o >= tau;
+                uint32_t dl = 0;
+                float v = 0.0f;
+                if (t < n_t) {
+                    dl = tl[t];
+                    v = acc[dl];
+                    acc[dl] = neg0;
+                    keep = order_f32(v) >= tau;
                 }
                 const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-                if (keep) {
-                    const uint32_t slot = n_keep + __popc(bal & ltmask);  // < SPW
-                    my_sval[slot] = v;
-                    my_sdoc[slot] = (uint16_t)dd[u];
-                    kmin = min(kmin, o);
-                    kmax = max(kmax, o);
-                }
-                n_keep += __popc(bal);
-            }
-            pos = __reduce_add_sync(0xffffffffu, pos);
-            kmin = __reduce_min_sync(0xffffffffu, kmin);
-            kmax = __reduce_max_sync(0xffffffffu, kmax);
-            if (lane == 0) {
-                ts.w_surv[warp] = n_keep;
-                ts.w_pos[warp] = pos;
-                ts.w_kmin[warp] = kmin;
-                ts.w_kmax[warp] = kmax;
-            }
-            __syncthreads();
-            BM25_PHASE(2);
-            uint32_t n_cand, n_pos, my_base;
-            {
-                const bool has = lane < WARPS;
-                const uint32_t sv = has ? ts.w_surv[lane] : 0u;
-                const uint32_t inc = warp_inclusive_sum(sv);
-                n_cand = __shfl_sync(0xffffffffu, inc, 31);
-                my_base = __shfl_sync(0xffffffffu, inc - sv, warp);
-                n_pos = __reduce_add_sync(0xffffffffu, has ? ts.w_pos[lane] : 0u);
-                kmin = __reduce_min_sync(0xffffffffu, has ? ts.w_kmin[lane] : 0xffffffffu);
-                kmax = __reduce_max_sync(0xffffffffu, has ? ts.w_kmax[lane] : 0u);
-                if (warp == 0 && lane <= WARPS)
-                    ts.list_pre[lane] = inc - sv;
-            }
-            const bool fill_on = may_fill && n_pos < kp;
-            if (!fill_on) {
-                if (zero_counts) {  // lift the marks: the accumulators start the next item clean
-#pragma unroll
-                    for (int u = 0; u < U; u++)
-                        if (dd[u] >= 0)
-                            acc[dd[u]] = neg0;
-                }
-                n_emit = n_cand < kp ? n_cand : kp;
-                if (n_cand <= kp) {
-                    // every candidate is kept: warp w writes its own at its offset
-                    const uint32_t nw = ts.w_surv[warp];
-                    for (uint32_t i = lane; i < nw; i += 32)
-                        out[my_base + i] = make_key(my_sval[i], (uint32_t)(d0 + my_sdoc[i]));
-                    new_tau = kmin;
-                    tau_ok = true;
-                } else if (n_cand <= 32) {
-                    // a few candidates too many (kp < n_cand <= 32): warp 0 sorts
-                    // them in registers, no block barrier
-                    if (warp == 0) {
-                        u64 key = 0ull;
-                        if ((uint32_t)lane < n_cand) {
-                            int a = 0, b = WARPS;  // list_pre[a] <= lane < list_pre[b]
-                            while (b - a > 1) {
-                                const int mid = (a + b) >> 1;
-                                if (ts.list_pre[mid] <= (uint32_t)lane)
-                                    a = mid;
-                                else
-                                    b = mid;
-                            }
-                            const uint32_t sl = a * SPW + (lane - ts.list_pre[a]);
-                            key = make_key(surv_val[sl], (uint32_t)(d0 + surv_doc[sl]));
+                if (bal) {
+                    const int leader = __ffs(bal) - 1;
+                    uint32_t base = 0;
+                    if (lane == leader)
+                        base = atomicAdd(&sh.lc[par], (uint32_t)__popc(bal));
+                    base = __shfl_sync(0xffffffffu, base, leader);
+                    if (keep) {
+                        const uint32_t pos = base + __popc(bal & lanemask_lt());
+                        if (pos < (uint32_t)kCandCap) {
+                            clist[pos] = make_key(v, (uint32_t)(d0 + dl));
+                        } else {  // no room: the sum goes back for the general select
+                            acc[dl] = v;
+                            sh.ovf[par] = 1;
                         }
+                    }
+                }
+            }
+            consumer_sync<NT>();
+            const uint32_t n_c = sh.lc[par];
+            if (!sh.ovf[par]) {
+                if (n_c <= kp) {
+                    for (uint32_t i = tid; i < n_c; i += NT)
+                        out[i] = clist[i];
+                    n_emit = n_c;
+                    if (warp == 0 && n_c == qkp && n_c > 0) {
+                        uint32_t m = 0xffffffffu;
+                        for (uint32_t i = lane; i < n_c; i += 32)
+                            m = min(m, (uint32_t)(clist[i] >> 32));
+                        new_tau = __reduce_min_sync(0xffffffffu, m);
+                        tau_ok = true;
+                    }
+                } else if (n_c <= 32) {
+                    if (warp == 0) {  // a few too many: sorted in registers
+                        u64 key = (uint32_t)lane < n_c ? clist[lane] : 0ull;
                         key = warp_sort_desc(key);
                         if ((uint32_t)lane < kp)
                             out[lane] = key;
                         new_tau = (uint32_t)(__shfl_sync(0xffffffffu, key, kp - 1) >> 32);
+                        tau_ok = true;
                     }
-                    tau_ok = true;
+                    n_emit = kp;
                 } else {
-#ifdef BM25_PHASE_TIMING
-                    if (tid == 0)
-                        ph_acc[6] += 1;
-#endif
                     if (tid == 0)
                         st.ctr = 0;
-                    __syncthreads();
-                    auto get = [&](uint32_t i) -> u64 {
-                        int a = 0, b = WARPS;  // list_pre[a] <= i < list_pre[b]
-                        while (b - a > 1) {
-                            const int mid = (a + b) >> 1;
-                            if (ts.list_pre[mid] <= i)
-                                a = mid;
-                            else
-                                b = mid;
-                        }
-                        const uint32_t s = a * SPW + (i - ts.list_pre[a]);
-                        return make_key(surv_val[s], (uint32_t)(d0 + surv_doc[s]));
-                    };
-                    block_select_idx<true>(st, n_cand, n_cand, kp, common_bytes(kmin, kmax),
-                                           (u64)kmax << 32, get,
-                                           [&](u64 key, uint32_t slot) { out[slot] = key; });
-                    // the selected keys are those at or above the final prefix,
-                    // so its score word bounds the weakest of them from below
+                    select_top<false>(st, NT, csync, n_c, n_c, kp, 0, 0ull,
+                                      [&](uint32_t i) -> u64 { return clist[i]; }, emit);
                     new_tau = (uint32_t)(st.prefix >> 32);
                     tau_ok = true;
+                    n_emit = kp;
                 }
             } else {
-#ifdef BM25_PHASE_TIMING
-                if (tid == 0)
-                    ph_acc[7] += 1;
-#endif
-                // Untouched documents compete (rare): put the candidates' sums
-                // back (so -0.0 again means untouched and the mark means
-                // touched below tau), find the k' lowest untouched documents,
-                // and select among the candidate lists and those.
-                const uint32_t nw = ts.w_surv[warp];
-                for (uint32_t i = lane; i < nw; i += 32)
-                    acc[my_sdoc[i]] = my_sval[i];
-                __syncthreads();
-                const uint32_t n_unt = first_untouched(acc, wd, kp, ts.scan, &ts.cutoff);
-                const uint32_t cut = ts.cutoff;
-                const uint32_t n_all = n_cand + n_unt;
-                n_emit = n_all < kp ? n_all : kp;
+                // more candidates than the list holds: select over the list and
+                // the sums put back on the touched documents
                 if (tid == 0)
                     st.ctr = 0;
-                __syncthreads();
-                auto get = [&](uint32_t i) -> u64 {
-                    if (i < n_cand) {
-                        int a = 0, b = WARPS;  // list_pre[a] <= i < list_pre[b]
-                        while (b - a > 1) {
-                            const int mid = (a + b) >> 1;
-                            if (ts.list_pre[mid] <= i)
-                                a = mid;
-                            else
-                                b = mid;
-                        }
-                        const uint32_t s = a * SPW + (i - ts.list_pre[a]);
-                        return make_key(surv_val[s], (uint32_t)(d0 + surv_doc[s]));
-                    }
-                    const uint32_t d = i - n_cand;
-                    return __float_as_uint(acc[d]) == kUntouched
-                               ? make_key(0.0f, (uint32_t)(d0 + d))
-                               : 0ull;
-                };
-                block_select_idx<true>(st, n_cand + cut, n_all, kp, 0, 0ull, get,
-                                       [&](u64 key, uint32_t slot) { out[slot] = key; });
-                if (n_all > kp) {
+                select_top<true>(st, NT, csync, (uint32_t)kCandCap + n_t, n_c, kp, 0, 0ull,
+                                 [&](uint32_t i) -> u64 {
+                                     if (i < (uint32_t)kCandCap)
+                                         return clist[i];
+                                     const uint32_t dl = tl[i - kCandCap];
+                                     const float v = acc[dl];
+                                     return __float_as_uint(v) != kUntouched
+                                                ? make_key(v, (uint32_t)(d0 + dl))
+                                                : 0ull;
+                                 },
+                                 emit);
+                n_emit = min(n_c, kp);
+                if (n_c > kp) {
                     new_tau = (uint32_t)(st.prefix >> 32);
                     tau_ok = true;
                 }
-#pragma unroll
-                for (int u = 0; u < U; u++)
-                    if (dd[u] >= 0)
-                        acc[dd[u]] = neg0;
+                for (uint32_t t = tid; t < n_t; t += NT)
+                    acc[tl[t]] = neg0;
+                consumer_sync<NT>();
             }
         } else {
-            // ---- many postings or tokens: walk the whole tile --------------------
+            // ---- a score of 0 can still rank: count, fill, select, reset ------------
             uint32_t c = 0, p = 0;
-            for (int d = tid; d < wd; d += THREADS) {
-                const float a = acc[d];
-                if (__float_as_uint(a) != kUntouched) {
-                    c += order_f32(a) >= tau;
-                    p += a > 0.0f;
-                }
+            for (uint32_t t = tid; t < n_t; t += NT) {
+                const float v = acc[tl[t]];
+                c += order_f32(v) >= tau;
+                p += v > 0.0f;
             }
-            uint32_t n_cand, n_pos, n_untouched = 0, cut = 0;
-            block_exclusive_sum(c, ts.scan, &n_cand);
-            block_exclusive_sum(p, ts.scan, &n_pos);
-            const bool fill_on = may_fill && n_pos < kp;
-            if (fill_on) {
-                n_untouched = first_untouched(acc, wd, kp, ts.scan, &ts.cutoff);
-                cut = ts.cutoff;
-            }            const uint32_t n_all = n_cand + n_untouched;
-            n_emit = n_all < kp ? n_all : kp;
+            uint32_t n_cand, n_pos, n_unt = 0, cut = 0;
+            consumer_exclusive_sum<NT>(c, sh.scan, &n_cand);
+            consumer_exclusive_sum<NT>(p, sh.scan, &n_pos);
+            if (may_fill && n_pos < kp) {
+                n_unt = consumer_first_untouched<NT>(acc, wd, kp, sh.scan, &sh.cutoff);
+                cut = sh.cutoff;
+            }
+            const uint32_t n_all = n_cand + n_unt;
+            n_emit = min(n_all, kp);
             if (tid == 0)
                 st.ctr = 0;
-            __syncthreads();
-            auto get = [&](uint32_t d) -> u64 {
-                const float a = acc[d];
-                const bool touched = __float_as_uint(a) != kUntouched;
-                return (touched ? order_f32(a) >= tau : d < cut)
-                           ? make_key(a, (uint32_t)(d0 + d))
-                           : 0ull;
-            };
-            block_select_idx<true>(st, (uint32_t)wd, n_all, kp, 0, 0ull, get,
-                                   [&](u64 key, uint32_t slot) { out[slot] = key; });
+            consumer_sync<NT>();
+            select_top<true>(st, NT, csync, n_t + cut, n_all, kp, 0, 0ull,
+                             [&](uint32_t i) -> u64 {
+                                 if (i < n_t) {
+                                     const uint32_t dl = tl[i];
+                                     const float v = acc[dl];
+                                     return order_f32(v) >= tau ? make_key(v, (uint32_t)(d0 + dl))
+                                                                : 0ull;
+                                 }
+                                 const uint32_t d = i - n_t;
+                                 return __float_as_uint(acc[d]) == kUntouched
+                                            ? make_key(0.0f, (uint32_t)(d0 + d))
+                                            : 0ull;
+                             },
+                             emit);
             if (n_all > kp) {
                 new_tau = (uint32_t)(st.prefix >> 32);
                 tau_ok = true;
             }
-            for (int i = tid; i < wd; i += THREADS)
-                acc[i] = neg0;
+            for (uint32_t t = tid; t < n_t; t += NT)
+                acc[tl[t]] = neg0;
+            consumer_sync<NT>();
         }
-        BM25_PHASE(3);
         if (tid == 0) {
-            // staged for the next item's flush; a full set of the query's k'
-            // candidates raises its threshold to (a lower bound on) the score
-            // of the weakest of them (a tile narrower than k' never does)
-            ts.o_item = item;
-            ts.o_q = q;
-            ts.o_count = n_emit;
-            ts.o_staged = kp <= kOutCap;
-            ts.o_tau = (tau_ok && n_emit == qkp && qkp > 0) ? new_tau : 0u;
-            if (kp > kOutCap)
-                tcount[item] = n_emit;  // its candidates were written directly
+            tcount[item] = n_emit;
+            // a full set of the query's k' candidates raises its threshold to (a
+            // lower bound on) the weakest of them (a tile narrower than k' never does)
+            if (tau_ok && n_emit == qkp && qkp > 0)
+                atomicMax(&thresh[qi], new_tau);
         }
-        __syncthreads();
-        BM25_PHASE(4);
-#ifdef BM25_PHASE_TIMING
-        if (tid == 0)
-            ph_acc[5] += one_round ? 1 : 0;
-#endif
-        advance(tile, q);
     }
-    flush();  // the CTA's last item
-#ifdef BM25_PHASE_TIMING
-    if (tid == 0)
-        for (int i = 0; i < 8; i++)
-            atomicAdd(&g_phase[i], ph_acc[i]);
-#endif
 }
 
 // ---- finishing a query's row (R3 and R4) ------------------------------------
@@ -1303,14 +1317,6 @@ __global__ void k_fill_u32(uint32_t* __restrict__ p, int64_t n, uint32_t v)
         p[i] = v;
 }
 
-size_t tile_smem_bytes(int32_t W, int threads)
-{
-    const size_t lists = threads == 128   ? tile_lists_bytes<128>()
-                         : threads == 256 ? tile_lists_bytes<256>()
-                                          : tile_lists_bytes<512>();
-    return (size_t)W * 4 + sizeof(SelectState) + sizeof(TileStage) + lists;
-}
-
 constexpr int64_t kCandBudget = int64_t(2) << 30;   // bytes of tile candidates per sub-batch
 constexpr int64_t kDenseBudget = int64_t(2) << 30;  // bytes of dense vectors per workspace
 constexpr int kDenseCtasPerSm = 2;
@@ -1444,19 +1450,6 @@ int reserve(const bm25_index* ix, bm25_workspace* ws, const Geometry& g, int64_t
 
 }  // namespace
 
-#ifdef BM25_PHASE_TIMING
-extern "C" int bm25_debug_phase_read(unsigned long long* out, int reset)
-{
-    if (cudaMemcpyFromSymbol(out, g_phase, sizeof(unsigned long long) * 8) != cudaSuccess)
-        return -4;
-    if (reset) {
-        unsigned long long z[16] = {0};
-        cudaMemcpyToSymbol(g_phase, z, sizeof(z));
-    }
-    return 0;
-}
-#endif
-
 int32_t tile_width(const Plan& plan, int64_t n_docs)
 {
     int32_t W = plan.tile_docs > 0 ? plan.tile_docs : 12288;
@@ -1567,29 +1560,27 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
         const int g1 = (int)std::min<int64_t>((n_seg + 255) / 256, max_blocks);
         {
             ProfileScope ps_("k_seg_bounds", s);
-            k_seg_bounds<<<g1, 256, 0, s>>>(q_tokens, n_tok, ix->indptr, ix->indices, ix->vocab, W,
-                                            n_tiles, ws->seg);
+            k_seg_bounds<true><<<g1, 256, 0, s>>>(q_tokens, n_tok, ix->indptr, ix->indices,
+                                                  ix->vocab, W, n_tiles, ws->seg);
         }
         count_launch();
         BM25_LAUNCH_CHECK();
     }
 
     // launch shapes that do not depend on the sub-batch
-    const size_t smem = tile_smem_bytes(W, plan.threads);
-    auto tile_kernel = plan.threads == 128   ? k_tile_topk<128>
-                       : plan.threads == 256 ? k_tile_topk<256>
-                                             : k_tile_topk<512>;
+    const size_t smem = staged_smem_bytes(W);
+    // plan.threads consumer threads (4, 8 or 16 warps) and one producer warp
+    auto tile_kernel = plan.threads == 128   ? k_tile_staged<4>
+                       : plan.threads == 256 ? k_tile_staged<8>
+                                             : k_tile_staged<16>;
+    const int tile_threads = plan.threads + 32;
     BM25_CUDA_TRY(cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
     int per_sm = 0;
     BM25_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_kernel,
-                                                                plan.threads, smem));
+                                                                tile_threads, smem));
     if (per_sm < 1)
         return set_error(BM25_E_INVALID, "doc tile of %d documents does not fit on an SM", W);
-#ifdef BM25_PHASE_TIMING
-    if (const char* e = getenv("BM25_CTAS_PER_SM"))
-        per_sm = std::min(per_sm, atoi(e));
-#endif
     int sz_all = 1;
     while (sz_all < kstride)
         sz_all <<= 1;
@@ -1622,10 +1613,10 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
         {
             const int g2 = (int)std::min<int64_t>((int64_t)nb * n_tiles,
                                                   (int64_t)di.sm_count * per_sm);
-            ProfileScope ps_("k_tile_topk", s);
-            tile_kernel<<<g2, plan.threads, smem, s>>>(N, ix->indices, ix->data, ws->seg, W,
-                                                       n_tiles, kstride, ws->lrec, ws->lpost,
-                                                       ws->ctr, ws->thresh, ws->tcount, ws->cand);
+            ProfileScope ps_("k_tile_staged", s);
+            tile_kernel<<<g2, tile_threads, smem, s>>>(
+                N, ix->posts, reinterpret_cast<const uint32_t*>(ws->seg), W, n_tiles, kstride,
+                ws->lrec, ws->lpost, ws->ctr, ws->thresh, ws->tcount, ws->cand, ix->status);
         }
         count_launch();
         BM25_LAUNCH_CHECK();
