@@ -92,8 +92,10 @@ enum bm25_accumulator {
  * the library's defaults. */
 typedef struct bm25_plan {
     int32_t accumulator;        /* enum bm25_accumulator */
-    int32_t tile_docs;          /* doc-tile width: a multiple of 1024 in [1024, 49152] */
-    int32_t block_threads;      /* threads per CTA of the tiled kernel: 128, 256 or 512 */
+    int32_t tile_docs;          /* doc-tile width: a multiple of 1024 in [1024, 49152]
+                                   (default 7168) */
+    int32_t block_threads;      /* consumer threads per CTA of the tiled kernel: 128, 256
+                                   or 512 (default 256; one producer warp is added) */
     int32_t dense_max_postings; /* dense-path bound for AUTO / L2_DENSE, in [0, 2^22]
                                    (default 8192) */
 } bm25_plan;
@@ -281,7 +283,7 @@ int bm25_index_get_plan(const bm25_index* index, bm25_plan* plan);
 
 /* Times retrieval of a sample batch (device arrays, as in bm25_retrieve,
  * with one k for all queries) under candidate plans and makes the fastest
- * the index's plan.  Candidates: tile widths 8192, 12288 and 16384 with
+ * the index's plan.  Candidates: tile widths 6144, 7168, 8192 and 12288 with
  * every query tiled, then, with the best width, dense-path bounds of 2048 ..
  * 32768 postings (the accumulator per query-length bucket).  Each candidate
  * runs once untimed and twice timed (CUDA events on `cuda_stream`); the best

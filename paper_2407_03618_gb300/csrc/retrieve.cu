@@ -341,25 +341,27 @@ __device__ __forceinline__ u64 warp_sort_desc(u64 key)
 //            the old value, and -0.0 there (untouched; stored scores are
 //            never -0.0) marks the document's first touch, which appends it
 //            to the tile's touched list;
-//   claim    the touched list is walked once: each document's sum is read
-//            and its accumulator reset to -0.0, and the sums that clear the
-//            query's running threshold become candidate keys (score, ~doc);
+//   claim    the touched list is walked once: each document's sum is read,
+//            its accumulator reset to -0.0, and a sum that clears the
+//            query's running threshold becomes a candidate key (score, ~doc);
 //   select   the k' best candidates of the tile go to the item's slots, and
 //            a full set of k' raises the query's threshold (Sec. 2 "Top-k
 //            selection", restated as a radix select with exact pruning).
 // While a document scoring 0 can still rank (threshold at or below the key
-// of 0), items take a general path that counts first, adds the lowest-id
-// untouched documents when fewer than k' touched ones score above 0, and
-// selects over the touched list; candidates beyond kCandCap do the same.
-constexpr int kStageEntries = 1024;  // packed postings per staging buffer (8 KB)
+// of 0), an item counts over its touched list first, adds the lowest-id
+// untouched documents when fewer than k' touched ones score above 0,
+// selects over both, and resets through the list.  Candidates beyond
+// kCandCap in a claim are put back and selected by a scan of the tile.
+constexpr int kStageEntries = 512;   // packed postings per staging buffer (4 KB)
 constexpr int kNumStages = 2;
 constexpr int kCandCap = 256;        // candidate keys an item collects in the common case
 constexpr int kWaitPolls = 1 << 22;  // mbarrier polls before a wait gives up
 
+
 struct StageHdr {
     int32_t n;       // entries in the buffer
     int32_t last;    // 1: the item's last buffer
-    int32_t item, tile, qi;  // work item, its doc tile, its query record
+    int32_t tile, qi;        // the item's doc tile and query record
     uint32_t kp, post, tau;  // the query's k', postings, threshold when staged
 };
 
@@ -367,7 +369,8 @@ struct StagedFront {
     unsigned long long full[kNumStages];   // producer -> consumers (bytes landed)
     unsigned long long empty[kNumStages];  // consumers -> producer (buffer free)
     StageHdr hdr[kNumStages];
-    uint32_t tl_count[2], lc[2], ovf[2];   // per item parity
+    uint32_t lc[2], ovf[2];                // candidate count / overflow, per item parity
+    uint32_t tl_count[2];                  // touched-list length, per item parity
     uint32_t abort_flag;
     uint32_t scan[33];
     uint32_t cutoff;
@@ -510,8 +513,10 @@ size_t staged_smem_bytes(int32_t W)
 // seg (packed): for query token m and tile boundary j, the first slot of the
 // token's packed column at or past document j * W (j = n_tiles: the column
 // end), from k_seg_bounds<true>.
+// Four CTAs per SM at the default tile width (shared memory allows it; the
+// register bound, 56 per thread at 8 consumer warps, makes it so).
 template <int CW>
-__global__ void __launch_bounds__((CW + 1) * 32)
+__global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
     k_tile_staged(int64_t n_docs, const uint2* __restrict__ posts, const uint32_t* __restrict__ seg,
                   int32_t W, int32_t n_tiles, int32_t kstride, const int4* __restrict__ lrec,
                   const uint32_t* __restrict__ lpost, const uint32_t* __restrict__ ctr,
@@ -519,12 +524,13 @@ __global__ void __launch_bounds__((CW + 1) * 32)
                   u64* __restrict__ cand, int* __restrict__ status)
 {
     constexpr int NT = CW * 32;  // consumer threads
+    constexpr int OW = CW - 1;   // the output warp (the fewest postings per item)
     extern __shared__ __align__(16) unsigned char smem[];
     StagedFront& sh = *reinterpret_cast<StagedFront*>(smem);
     float* acc = reinterpret_cast<float*>(smem + kStagedFront);
-    uint16_t* tl = reinterpret_cast<uint16_t*>(acc + W);
-    u64* clist = reinterpret_cast<u64*>(tl + W);
+    u64* clist = reinterpret_cast<u64*>(acc + W);
     uint2* stage = reinterpret_cast<uint2*>(clist + kCandCap);
+    uint16_t* tl = reinterpret_cast<uint16_t*>(stage + (size_t)kNumStages * kStageEntries);
     SelectState& st = sh.st;
 
     const int32_t nq = (int32_t)ctr[0];
@@ -540,9 +546,9 @@ __global__ void __launch_bounds__((CW + 1) * 32)
             mbar_init(&sh.full[s], 1);
             mbar_init(&sh.empty[s], CW);
         }
-        sh.tl_count[0] = sh.tl_count[1] = 0;
         sh.lc[0] = sh.lc[1] = 0;
         sh.ovf[0] = sh.ovf[1] = 0;
+        sh.tl_count[0] = sh.tl_count[1] = 0;
         sh.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -607,7 +613,7 @@ __global__ void __launch_bounds__((CW + 1) * 32)
             }
             // stage item (t0, q0)
             const int32_t m0 = rec0.y, m1 = rec0.z;
-            for (int32_t mb = m0;; mb += 2 * 32) {
+            for (int32_t mb = m0;; mb += 64) {
                 const int cnt = (int)min((int64_t)64, (int64_t)m1 - mb);  // may be <= 0
                 uint32_t a[2], n[2];
 #pragma unroll
@@ -647,7 +653,6 @@ __global__ void __launch_bounds__((CW + 1) * 32)
                         StageHdr& hd = sh.hdr[s];
                         hd.n = aborted ? 0 : (int32_t)(e1 - e0);
                         hd.last = (last_chunk && k + 1 == nst) ? 1 : 0;
-                        hd.item = item;
                         hd.tile = t0;
                         hd.qi = q0;
                         hd.kp = (uint32_t)rec0.w;
@@ -709,9 +714,11 @@ __global__ void __launch_bounds__((CW + 1) * 32)
     int s = 0;
     uint32_t round = 0, par = 0;
     bool aborted = false;
+    auto csync = [] { consumer_sync<NT>(); };
+    const uint32_t ltmask = lanemask_lt();
     for (int32_t item = blockIdx.x; item < n_items; item += gridDim.x, par ^= 1u) {
         int32_t tile = 0, qi = 0;
-        uint32_t qkp = 0, post = 0, tau = 0;
+        uint32_t qkp = 1, post = 0, tau = 0;
         // ---- scatter the item's staged postings ----------------------------------
         for (;;) {
             if (!aborted && !warp_wait(&sh.full[s], round & 1u, abort_flag)) {
@@ -721,39 +728,37 @@ __global__ void __launch_bounds__((CW + 1) * 32)
                     sh.abort_flag = 1;
                 }
             }
-            const StageHdr hd = sh.hdr[s];
             // (clamped so that a header left stale by an abandoned wait
             // still indexes inside the arrays)
+            const StageHdr hd = sh.hdr[s];
             tile = min(max(hd.tile, 0), n_tiles - 1);
             qi = min(max(hd.qi, 0), nq - 1);
             qkp = min(max(hd.kp, 1u), (uint32_t)kstride);
             post = hd.post;
             tau = hd.tau;
-            const int64_t d0 = (int64_t)tile * W;
-            const uint32_t wd = (uint32_t)min((int64_t)W, n_docs - d0);
             const int32_t n_e = aborted ? 0 : min(max(hd.n, 0), kStageEntries);
+            const bool last = hd.last != 0;
+            const uint32_t d0 = (uint32_t)tile * (uint32_t)W;
+            const uint32_t wd = (uint32_t)min((int64_t)W, n_docs - (int64_t)d0);
             const uint2* sb = stage + (size_t)s * kStageEntries;
+            // chunks of 32 entries: warp w takes chunks w, w + CW, ...
             for (int32_t e0 = warp * 32; e0 < n_e; e0 += NT) {
                 const int32_t e = e0 + lane;
+                const uint2 pe = e < n_e ? sb[e] : make_uint2(kPostPad, 0u);
+                const uint32_t dl = pe.x - d0;
                 bool first = false;
-                uint32_t dl = 0;
-                if (e < n_e) {
-                    const uint2 p = sb[e];
-                    dl = p.x - (uint32_t)d0;
-                    if (dl < wd) {
-                        const float old = atomicAdd(&acc[dl], __uint_as_float(p.y));
-                        first = __float_as_uint(old) == kUntouched;
-                    }
-                }
-                const uint32_t bal = __ballot_sync(0xffffffffu, first);
-                if (bal) {
-                    const int leader = __ffs(bal) - 1;
+                if (dl < wd)
+                    first = __float_as_uint(atomicAdd(&acc[dl], __uint_as_float(pe.y))) ==
+                            kUntouched;
+                const uint32_t b = __ballot_sync(0xffffffffu, first);
+                if (b) {
+                    const int leader = __ffs(b) - 1;
                     uint32_t base = 0;
                     if (lane == leader)
-                        base = atomicAdd(&sh.tl_count[par], (uint32_t)__popc(bal));
+                        base = atomicAdd(&sh.tl_count[par], (uint32_t)__popc(b));
                     base = __shfl_sync(0xffffffffu, base, leader);
                     if (first)
-                        tl[base + __popc(bal & lanemask_lt())] = (uint16_t)dl;
+                        tl[base + __popc(b & ltmask)] = (uint16_t)dl;
                 }
             }
             __syncwarp();
@@ -763,7 +768,7 @@ __global__ void __launch_bounds__((CW + 1) * 32)
                 s = 0;
                 round++;
             }
-            if (hd.last || aborted)
+            if (last || aborted)
                 break;
         }
         consumer_sync<NT>();  // every posting added, every first touch listed
@@ -771,23 +776,21 @@ __global__ void __launch_bounds__((CW + 1) * 32)
         const int64_t d0 = (int64_t)tile * W;
         const int32_t wd = (int32_t)min((int64_t)W, n_docs - d0);
         const uint32_t n_t = sh.tl_count[par];
-        if (tid == 0) {  // counters of the next item (its scatter follows the claim barrier)
-            sh.tl_count[par ^ 1u] = 0;
+        if (tid == 0) {  // counters of the next item (used after its scatter barrier)
             sh.lc[par ^ 1u] = 0;
             sh.ovf[par ^ 1u] = 0;
+            sh.tl_count[par ^ 1u] = 0;
         }
         const uint32_t kp = min(qkp, (uint32_t)wd);
-        const bool zero_counts = tau <= kZeroKey;
-        const bool may_fill = zero_counts && (int64_t)tile * W < (int64_t)qkp + (int64_t)post;
         u64* out = cand + (int64_t)item * kstride;
         uint32_t n_emit = 0, new_tau = 0;
         bool tau_ok = false;
-        auto csync = [] { consumer_sync<NT>(); };
         auto emit = [&](u64 key, uint32_t slot) { out[slot] = key; };
+        const bool zero_counts = tau <= kZeroKey;
 
         if (!zero_counts) {
             // ---- claim: read and reset each touched document once ------------------
-            for (uint32_t b0 = warp * 32; b0 < n_t; b0 += NT) {
+            for (uint32_t b0 = warp * 32; b0 < n_t; b0 += NT) {  // warp-uniform
                 const uint32_t t = b0 + lane;
                 bool keep = false;
                 uint32_t dl = 0;
@@ -806,7 +809,7 @@ __global__ void __launch_bounds__((CW + 1) * 32)
                         base = atomicAdd(&sh.lc[par], (uint32_t)__popc(bal));
                     base = __shfl_sync(0xffffffffu, base, leader);
                     if (keep) {
-                        const uint32_t pos = base + __popc(bal & lanemask_lt());
+                        const uint32_t pos = base + __popc(bal & ltmask);
                         if (pos < (uint32_t)kCandCap) {
                             clist[pos] = make_key(v, (uint32_t)(d0 + dl));
                         } else {  // no room: the sum goes back for the general select
@@ -820,18 +823,19 @@ __global__ void __launch_bounds__((CW + 1) * 32)
             const uint32_t n_c = sh.lc[par];
             if (!sh.ovf[par]) {
                 if (n_c <= kp) {
-                    for (uint32_t i = tid; i < n_c; i += NT)
-                        out[i] = clist[i];
-                    n_emit = n_c;
-                    if (warp == 0 && n_c == qkp && n_c > 0) {
+                    if (warp == OW) {
                         uint32_t m = 0xffffffffu;
-                        for (uint32_t i = lane; i < n_c; i += 32)
-                            m = min(m, (uint32_t)(clist[i] >> 32));
+                        for (uint32_t i = lane; i < n_c; i += 32) {
+                            const u64 key = clist[i];
+                            out[i] = key;
+                            m = min(m, (uint32_t)(key >> 32));
+                        }
                         new_tau = __reduce_min_sync(0xffffffffu, m);
-                        tau_ok = true;
+                        tau_ok = n_c > 0;
                     }
+                    n_emit = n_c;
                 } else if (n_c <= 32) {
-                    if (warp == 0) {  // a few too many: sorted in registers
+                    if (warp == OW) {  // a few too many: sorted in registers
                         u64 key = (uint32_t)lane < n_c ? clist[lane] : 0ull;
                         key = warp_sort_desc(key);
                         if ((uint32_t)lane < kp)
@@ -851,17 +855,17 @@ __global__ void __launch_bounds__((CW + 1) * 32)
                 }
             } else {
                 // more candidates than the list holds: select over the list and
-                // the sums put back on the touched documents
+                // the sums put back in the tile
                 if (tid == 0)
                     st.ctr = 0;
-                select_top<true>(st, NT, csync, (uint32_t)kCandCap + n_t, n_c, kp, 0, 0ull,
+                select_top<true>(st, NT, csync, (uint32_t)kCandCap + (uint32_t)wd, n_c, kp, 0, 0ull,
                                  [&](uint32_t i) -> u64 {
                                      if (i < (uint32_t)kCandCap)
                                          return clist[i];
-                                     const uint32_t dl = tl[i - kCandCap];
-                                     const float v = acc[dl];
+                                     const uint32_t d = i - kCandCap;
+                                     const float v = acc[d];
                                      return __float_as_uint(v) != kUntouched
-                                                ? make_key(v, (uint32_t)(d0 + dl))
+                                                ? make_key(v, (uint32_t)(d0 + d))
                                                 : 0ull;
                                  },
                                  emit);
@@ -870,12 +874,12 @@ __global__ void __launch_bounds__((CW + 1) * 32)
                     new_tau = (uint32_t)(st.prefix >> 32);
                     tau_ok = true;
                 }
-                for (uint32_t t = tid; t < n_t; t += NT)
-                    acc[tl[t]] = neg0;
+                for (int32_t d = tid; d < wd; d += NT)
+                    acc[d] = neg0;
                 consumer_sync<NT>();
             }
         } else {
-            // ---- a score of 0 can still rank: count, fill, select, reset ------------
+            // ---- a score of 0 can still rank: count, fill, select over the lists -------
             uint32_t c = 0, p = 0;
             for (uint32_t t = tid; t < n_t; t += NT) {
                 const float v = acc[tl[t]];
@@ -885,24 +889,26 @@ __global__ void __launch_bounds__((CW + 1) * 32)
             uint32_t n_cand, n_pos, n_unt = 0, cut = 0;
             consumer_exclusive_sum<NT>(c, sh.scan, &n_cand);
             consumer_exclusive_sum<NT>(p, sh.scan, &n_pos);
+            const bool may_fill = (int64_t)tile * W < (int64_t)qkp + (int64_t)post;
             if (may_fill && n_pos < kp) {
                 n_unt = consumer_first_untouched<NT>(acc, wd, kp, sh.scan, &sh.cutoff);
                 cut = sh.cutoff;
             }
+            const uint32_t n_l = n_t;
             const uint32_t n_all = n_cand + n_unt;
             n_emit = min(n_all, kp);
             if (tid == 0)
                 st.ctr = 0;
             consumer_sync<NT>();
-            select_top<true>(st, NT, csync, n_t + cut, n_all, kp, 0, 0ull,
+            select_top<true>(st, NT, csync, n_l + cut, n_all, kp, 0, 0ull,
                              [&](uint32_t i) -> u64 {
-                                 if (i < n_t) {
+                                 if (i < n_l) {
                                      const uint32_t dl = tl[i];
                                      const float v = acc[dl];
                                      return order_f32(v) >= tau ? make_key(v, (uint32_t)(d0 + dl))
                                                                 : 0ull;
                                  }
-                                 const uint32_t d = i - n_t;
+                                 const uint32_t d = i - n_l;
                                  return __float_as_uint(acc[d]) == kUntouched
                                             ? make_key(0.0f, (uint32_t)(d0 + d))
                                             : 0ull;
@@ -916,7 +922,9 @@ __global__ void __launch_bounds__((CW + 1) * 32)
                 acc[tl[t]] = neg0;
             consumer_sync<NT>();
         }
-        if (tid == 0) {
+        // the output warp's first lane records the item (select paths: every
+        // thread holds the result; the others computed it in warp OW)
+        if (tid == OW * 32) {
             tcount[item] = n_emit;
             // a full set of the query's k' candidates raises its threshold to (a
             // lower bound on) the weakest of them (a tile narrower than k' never does)
@@ -1452,7 +1460,7 @@ int reserve(const bm25_index* ix, bm25_workspace* ws, const Geometry& g, int64_t
 
 int32_t tile_width(const Plan& plan, int64_t n_docs)
 {
-    int32_t W = plan.tile_docs > 0 ? plan.tile_docs : 12288;
+    int32_t W = plan.tile_docs > 0 ? plan.tile_docs : 7168;
     // multiples of 128 keep the shared-memory carve-up 16-byte aligned
     const int64_t w_need = (n_docs + 127) / 128 * 128;
     if (W > w_need)

@@ -118,7 +118,7 @@ extern "C" int bm25_autotune(bm25_index* ix, const int32_t* query_tokens, int64_
         }
     };
     // 1. the tile width, every query on the tiled path
-    for (int32_t W : {8192, 12288, 16384}) {
+    for (int32_t W : {6144, 7168, 8192, 12288}) {
         Plan p = base;
         p.accumulator = BM25_ACC_SMEM_TILED;
         p.tile_docs = W;
