@@ -36,7 +36,7 @@ L2_BYTES = 129 * 1024 * 1024
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=40)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="1m", choices=sorted(synth.WORKLOADS))
@@ -59,27 +59,65 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+# ------------------------------------------------- ranks (weak scaling) ----
+# Under torchrun every rank answers its own query batch over its own replica
+# of the index; no data crosses ranks.  Only the timing is combined.
+
+def rank_batch(w, rank: int, n_queries: int = 0):
+    """The query batch of `rank`: the workload's query law with seed 1 + rank."""
+    q = w.queries(seed=1 + rank)
+    if n_queries:
+        q = q.subset(np.arange(min(n_queries, q.n_queries)))
+    return q
+
+
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The job's time: the slowest rank's (all_reduce MAX; a no-op at N = 1)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the job's time."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 # ------------------------------------------------------------ clocks ------
 
 class ClockSampler:
-    """nvidia-smi samples every 200 ms while the timed region runs."""
+    """nvidia-smi samples (with their wall-clock timestamps) every 50 ms;
+    stop() keeps those taken inside the window set by mark_start / mark_end,
+    i.e. during the timed region."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_id: str | None):
         self.path = tempfile.mktemp(suffix=".csv")
         self.proc = None
+        self.t0 = self.t1 = None
         cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-               "-lms", "200"]
+               "-lms", "50"]
         if gpu_id:
             cmd += ["-i", gpu_id]
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)  # let it start sampling before the timed region
         except (OSError, FileNotFoundError):
             self.proc = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def stop(self) -> dict | None:
         if self.proc is None:
@@ -91,14 +129,22 @@ class ClockSampler:
             self.proc.kill()
         self.f.close()
         rows = []
+        import datetime
         with open(self.path) as f:
             for line in f:
                 parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    continue
+                if self.t0 is not None and self.t1 is not None and not (self.t0 <= ts <= self.t1):
+                    continue
+                rows.append(parts[1:])
         os.unlink(self.path)
         if not rows:
-            return None
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -214,9 +260,7 @@ def main():
     w = synth.WORKLOADS[args.workload]
     prm = w.params
     corpus = w.corpus()
-    queries = w.queries(seed=1 + rank)  # each rank answers its own batch (weak scaling)
-    if args.queries:
-        queries = queries.subset(np.arange(min(args.queries, queries.n_queries)))
+    queries = rank_batch(w, rank, args.queries)  # each rank its own batch (weak scaling)
     k = args.k
     nq = queries.n_queries
 
@@ -275,21 +319,21 @@ def main():
     barrier()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if clocks:
+        clocks.mark_start()
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize(dev)
+    if clocks:
+        clocks.mark_end()
     barrier()
     prof = bm25.profile_end()
     launches = bm25.launch_count() - launches0
     clock_info = clocks.stop() if clocks else None
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = nq * world / (ms / 1e3)
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    value = job_rate(nq, world, ms)
 
     line = {"metric": f"queries/s @k={k}", "value": value, "unit": "queries/s",
             "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
@@ -370,16 +414,21 @@ def extras(args, line, bm25, corpus, queries, tok, off, qt, qo, ids, sc, dev, pr
         avg_s = t / c / 1e3
         achieved = b / avg_s / 1e9
         traffic = None
-        tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+        # profiles/<kernel>_<workload>_traffic.md holds "key: value" lines from
+        # one ncu capture; used only while the sources match its build stamp
+        tr_path = os.path.join(ROOT, "profiles",
+                               f"{name}_{w.name.replace('-', '')}_traffic.md")
         try:
+            kv = {}
             with open(tr_path) as f:
-                tr = json.load(f)
+                for line in f:
+                    if ":" in line and not line.startswith("#"):
+                        key, _, val = line.partition(":")
+                        kv[key.strip().strip("`* ")] = val.strip().strip("`* ")
             from paper_2407_03618_gb300 import build_ext
-            ent = tr.get(name)
-            if ent and ent.get("build_stamp") == build_ext._stamp() and \
-                    ent.get("workload") == w.name:
-                traffic = ent["bytes_per_launch"]
-        except (OSError, ValueError):
+            if kv.get("build_stamp") == build_ext._stamp() and kv.get("workload") == w.name:
+                traffic = int(kv["traffic_bytes_per_launch"])
+        except (OSError, ValueError, KeyError):
             pass
         return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                 "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
