@@ -97,7 +97,7 @@ typedef struct bm25_plan {
     int32_t block_threads;      /* consumer threads per CTA of the tiled kernel: 128, 256
                                    or 512 (default 256; one producer warp is added) */
     int32_t dense_max_postings; /* dense-path bound for AUTO / L2_DENSE, in [0, 2^22]
-                                   (default 8192) */
+                                   (default 4096) */
 } bm25_plan;
 
 /* ------------------------------------------------------------------ index */
