@@ -163,9 +163,17 @@ int bm25_index_import(int64_t n_docs, int64_t n_tokens, int64_t nnz, int32_t voc
  * kernel recorded for this index since the last call (BM25_OK if none). */
 int bm25_sync_status(const bm25_index* index, void* cuda_stream);
 
-/* Releases the index, its default workspace and its device memory.  The caller
- * must make sure no work using the index is still in flight.  NULL is a no-op. */
+/* Releases the index and its device memory.  Its default workspace (the
+ * retrieval scratch of bm25_retrieve and the _host entry points) is kept, one
+ * per device, for the next index's first call, so that building and dropping
+ * indexes in a loop allocates that scratch once; bm25_release_cached() frees
+ * it.  The caller must make sure no work using the index is still in flight.
+ * NULL is a no-op. */
 void bm25_index_free(bm25_index* index);
+
+/* Frees the retrieval scratch kept from freed indexes (see bm25_index_free)
+ * on every device.  No index of this process may be running a call. */
+void bm25_release_cached(void);
 
 /* -------------------------------------------------------------- retrieval */
 

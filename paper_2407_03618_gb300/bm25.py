@@ -88,6 +88,7 @@ def load(path: str | None = None):
                                      P, P, P, P, P, P, P, P, PP]),
         "bm25_sync_status": (cint, [P, P]),
         "bm25_index_free": (None, [P]),
+        "bm25_release_cached": (None, []),
         "bm25_retrieve": (cint, [P, P, i64, P, i32, i32, P, P, P]),
         "bm25_retrieve_host": (cint, [P, P, P, i32, i32, P, P, P]),
         "bm25_retrieve_noalloc": (cint, [P, P, i64, P, i32, i32, P, P, P]),
@@ -123,6 +124,11 @@ def load(path: str | None = None):
 def _check(rc: int):
     if rc != 0:
         raise BM25Error(rc, load().bm25_last_error().decode())
+
+
+def release_cached():
+    """Free the retrieval scratch kept from freed indexes (all devices)."""
+    load().bm25_release_cached()
 
 
 def launch_count() -> int:

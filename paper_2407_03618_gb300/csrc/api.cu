@@ -103,12 +103,45 @@ Plan plan_of(const bm25_index* ix)
     return ix->plan;
 }
 
+// The default workspace of a freed index is kept (one per device) and handed
+// to the next index's first call, so that building and dropping indexes in a
+// loop allocates retrieval scratch once.  Its buffers grow on demand and the
+// dense-path vectors are left at -0.0 by every query, so nothing carries over.
+std::mutex g_ws_cache_mu;
+bm25_workspace* g_ws_cache[64] = {};
+
+bm25_workspace* take_cached_ws(int dev)
+{
+    std::lock_guard<std::mutex> g(g_ws_cache_mu);
+    if (dev < 0 || dev >= 64)
+        return nullptr;
+    bm25_workspace* ws = g_ws_cache[dev];
+    g_ws_cache[dev] = nullptr;
+    return ws;
+}
+
+void put_cached_ws(bm25_workspace* ws)
+{
+    {
+        std::lock_guard<std::mutex> g(g_ws_cache_mu);
+        if (ws->device >= 0 && ws->device < 64 && !g_ws_cache[ws->device]) {
+            g_ws_cache[ws->device] = ws;
+            return;
+        }
+    }
+    workspace_release(ws);
+    delete ws;
+}
+
 int default_ws(const bm25_index* ix, bm25_workspace** out)
 {
     bm25_index* m = const_cast<bm25_index*>(ix);
     if (!m->default_ws) {
-        bm25_workspace* ws = new bm25_workspace();
-        ws->device = ix->device;
+        bm25_workspace* ws = take_cached_ws(ix->device);
+        if (!ws) {
+            ws = new bm25_workspace();
+            ws->device = ix->device;
+        }
         m->default_ws = ws;
     }
     *out = m->default_ws;
@@ -347,13 +380,26 @@ void bm25_index_free(bm25_index* ix)
 {
     if (!ix)
         return;
-    if (ix->default_ws) {
-        workspace_release(ix->default_ws);
-        delete ix->default_ws;
-    }
+    if (ix->default_ws)
+        put_cached_ws(ix->default_ws);
     free_index_arrays(ix, 0);
     cudaStreamSynchronize(0);
     delete ix;
+}
+
+void bm25_release_cached(void)
+{
+    for (int d = 0; d < 64; d++) {
+        bm25_workspace* ws = take_cached_ws(d);
+        if (!ws)
+            continue;
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(d);
+        workspace_release(ws);
+        delete ws;
+        cudaSetDevice(cur);
+    }
 }
 
 int bm25_workspace_create(const bm25_index* ix, int32_t max_queries, int64_t max_query_tokens,

@@ -154,7 +154,7 @@ def test_retrieval_across_tiles(torch_dev, tile_docs, threads):
     ix = _build(torch_dev, c, "bm25+")
     ix.set_plan(2, tile_docs, threads)
     assert ix.get_plan() == {"accumulator": 2, "tile_docs": tile_docs, "block_threads": threads,
-                             "dense_max_postings": 8192}
+                             "dense_max_postings": 4096}
     orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.BM25PLUS)
     for k in (1, 7, 100, 1000, 2500):  # 2500: k' wider than the narrow tiles
         _check_retrieval(torch_dev, ix, orc, q, k, where=f"W={tile_docs} k={k}")
@@ -408,3 +408,27 @@ def test_cuda_graph_capture_and_replay(torch_dev, name):
     ws.close()
     small.close()
     ix.close()
+
+
+def test_default_workspace_reused_across_indexes(torch_dev):
+    """A freed index's default workspace serves the next index built on the
+    device (one kept per device): indexes of larger, smaller and equal size in
+    turn, each through bm25_retrieve and bm25_retrieve_host with dense and
+    tiled queries, all give the oracle's results; then the cache is freed."""
+    from paper_2407_03618_gb300 import bm25
+    shapes = [(3000, 2000, 1.1, ("poisson", 40)), (9000, 4000, 1.05, ("poisson", 30)),
+              (1500, 1000, 1.2, ("poisson", 50)), (3000, 2000, 1.1, ("poisson", 40))]
+    for i, (n, v, s_, L) in enumerate(shapes):
+        c = synth.make_corpus(n, v, s_, L, seed=60 + i)
+        q = synth.make_queries(48, v, s_, ("uniform", 1, 10), seed=70 + i)
+        orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.BM25PLUS)
+        ix = _build(torch_dev, c, "bm25+")
+        ix.set_plan(1, 0, 0, 600)  # short queries dense, the rest tiled
+        _check_retrieval(torch_dev, ix, orc, q, 10, where=f"index {i} device")
+        ids, sc = ix.retrieve_host(q.tokens, q.offsets, 7)
+        ix.sync_status()
+        for r in range(q.n_queries):
+            full, ab = oracle.score_all(orc, q.query(r), with_abs=True)
+            check_topk(ids[r], sc[r], full, ab, 7, where=f"index {i} host q{r}")
+        ix.close()
+    bm25.release_cached()
