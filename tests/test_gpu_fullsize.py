@@ -65,3 +65,65 @@ def test_fullsize_parity(workload, variant):
             full, ab = oracle.score_all(orc, q.query(int(i)), with_abs=True)
             check_topk(ids[i], sc[i], full, ab, k, where=f"{variant} k={k} q{i}")
     ix.close()
+
+
+# ---- the passage and long-document shapes ------------------------------------
+# passage-8.8m at full size: 8.8M documents (lognormal(56, 0.5)), vocab 1M
+# Zipf(1.0), ~433M CSC entries, 7,000 queries of geometric length (mean 6, at
+# most 32) with head terms, k = 10 / 100 / 1000 in the batched launch the
+# bench would time; structure checked in full on sampled columns, the top-k
+# of a seeded query sample against the oracle's exhaustive scores.
+# long-5m's shape (lognormal(300, 0.8) documents, vocab 2M Zipf(1.1), 20..60
+# tokens per query including head terms, BM25+, k = 100) at 1M documents:
+# 1.5 G tokens would take the oracle minutes to build.
+
+@pytest.mark.parametrize("name", ["passage", "long"])
+def test_large_shapes(name):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2407_03618_gb300 import bm25
+    w = synth.WORKLOADS[name]
+    dev = torch.device("cuda:0")
+    if name == "passage":
+        c, q, variant, ks, n_sample = w.corpus(), w.queries(), "lucene", (10, 100, 1000), 8
+    else:
+        c = synth.make_corpus(1_000_000, w.vocab, w.zipf_s, w.doc_length, seed=0)
+        q = w.queries()
+        variant, ks, n_sample = "bm25+", (100,), 8
+    prm = w.params
+    ix = bm25.Index.build(torch.from_numpy(c.tokens).to(dev),
+                          torch.from_numpy(c.doc_offsets).to(dev), c.vocab, variant,
+                          prm["k1"], prm["b"], prm["delta"])
+    orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.VARIANTS[variant], prm["k1"],
+                       prm["b"], prm["delta"])
+    info = ix.info()
+    assert info["nnz"] == orc.nnz
+    ex = ix.export()
+    # the structure in full (bit-exact), the stored scores on sampled columns
+    assert np.array_equal(ex["df"], orc.df.astype(np.int32))
+    assert np.array_equal(ex["indptr"], orc.indptr)
+    assert np.array_equal(ex["doc_len"], orc.doc_len.astype(np.int32))
+    assert np.array_equal(ex["indices"], orc.indices)
+    assert np.array_equal(ex["tf"], orc.csc_tf)
+    rng = np.random.default_rng(5)
+    cols = np.unique(np.concatenate([np.arange(20), rng.integers(0, c.vocab, 200)]))
+    for t in cols:  # the head terms and a random sample
+        a, b = orc.indptr[t], orc.indptr[t + 1]
+        full_s = orc.csc_delta[a:b] + orc.s0[t]
+        scale = np.maximum(np.abs(orc.csc_delta[a:b]), np.abs(full_s))
+        assert (np.abs(ex["data"][a:b] - orc.csc_delta[a:b]) <= 1e-5 * scale + 1e-30).all()
+    del ex
+    qt = torch.from_numpy(q.tokens).to(dev)
+    qo = torch.from_numpy(q.offsets).to(dev)
+    sample = rng.choice(q.n_queries, n_sample, replace=False)
+    rows = {}
+    for k in ks:
+        ids, sc = ix.retrieve(qt, qo, k)
+        ix.sync_status()
+        rows[k] = (ids.cpu().numpy()[sample], sc.cpu().numpy()[sample])
+    ix.close()
+    for j, i in enumerate(sample):
+        full, ab = oracle.score_all(orc, q.query(int(i)), with_abs=True)
+        for k in ks:
+            check_topk(rows[k][0][j], rows[k][1][j], full, ab, k, where=f"{name} k={k} q{i}")
