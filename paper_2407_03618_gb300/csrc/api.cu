@@ -164,9 +164,9 @@ int merge_plan(const bm25_plan* in, const Plan& base, Plan* out)
             return set_error(BM25_E_INVALID,
                              "tile_docs %d must be a multiple of 1024 in [1024, 49152]",
                              in->tile_docs);
-        if (in->block_threads != 0 && in->block_threads != 128 && in->block_threads != 256 &&
-            in->block_threads != 512)
-            return set_error(BM25_E_INVALID, "block_threads %d must be 128, 256 or 512",
+        if (in->block_threads != 0 && in->block_threads != 128 && in->block_threads != 192 &&
+            in->block_threads != 256 && in->block_threads != 512)
+            return set_error(BM25_E_INVALID, "block_threads %d must be 128, 192, 256 or 512",
                              in->block_threads);
         if (in->accumulator)
             p.accumulator = in->accumulator;

@@ -32,8 +32,9 @@ constexpr int kSortThreads = 256;
 constexpr int kSortIpt = 16;
 constexpr int kSortTile = kSortThreads * kSortIpt;  // 4096 items per tile
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kMaxDigitBits = 8;
+constexpr int kMaxDigitBits = 9;  // 18-bit vocabularies (<= 262,144 terms) sort in two passes
 constexpr int kMaxBuckets = 1 << kMaxDigitBits;
+constexpr int kSortedTileBytes = 2 * kSortTile * (int)sizeof(uint32_t);  // downsweep dynamic smem
 
 // ---- K1 -------------------------------------------------------------------
 // One warp per group of 32 documents (lane l: document g*32 + l): |D|, the
@@ -152,9 +153,10 @@ __global__ void __launch_bounds__(kSortThreads)
     __shared__ uint32_t wcnt[kSortWarps][kMaxBuckets];
     __shared__ uint32_t gbase[kMaxBuckets];
     __shared__ uint32_t dstart[kMaxBuckets];
-    __shared__ uint32_t sk[kSortTile];
-    __shared__ uint32_t sv[kSortTile];
     __shared__ uint32_t scan_buf[33];
+    extern __shared__ uint32_t sorted_tile[];  // kSortTile keys, then kSortTile doc ids
+    uint32_t* sk = sorted_tile;
+    uint32_t* sv = sorted_tile + kSortTile;
     const int nb = 1 << bits;
     const uint32_t mask = (uint32_t)nb - 1u;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -192,19 +194,27 @@ __global__ void __launch_bounds__(kSortThreads)
     __syncthreads();
     // per digit: exclusive scan over warps (warp bases) and the tile total;
     // then the digits' start offsets in the tile
-    uint32_t tot = 0;
-    if ((int)threadIdx.x < nb) {
+    // (thread t owns digits 2t and 2t + 1: up to 512 digits)
+    static_assert(kMaxBuckets <= 2 * kSortThreads, "two digits per thread");
+    uint32_t tot2[2] = {0u, 0u};
 #pragma unroll
-        for (int w = 0; w < kSortWarps; w++) {
-            uint32_t t = wcnt[w][threadIdx.x];
-            wcnt[w][threadIdx.x] = tot;
-            tot += t;
+    for (int h = 0; h < 2; h++) {
+        const int d = 2 * (int)threadIdx.x + h;
+        if (d < nb) {
+#pragma unroll
+            for (int w = 0; w < kSortWarps; w++) {
+                const uint32_t t = wcnt[w][d];
+                wcnt[w][d] = tot2[h];
+                tot2[h] += t;
+            }
         }
     }
     uint32_t all;
-    const uint32_t ds = block_exclusive_sum(tot, scan_buf, &all);
-    if ((int)threadIdx.x < nb)
-        dstart[threadIdx.x] = ds;
+    const uint32_t ds = block_exclusive_sum(tot2[0] + tot2[1], scan_buf, &all);
+    if (2 * (int)threadIdx.x < nb)
+        dstart[2 * threadIdx.x] = ds;
+    if (2 * (int)threadIdx.x + 1 < nb)
+        dstart[2 * threadIdx.x + 1] = ds + tot2[0];
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kSortIpt; r++) {
@@ -660,6 +670,10 @@ int build_index_device(const int32_t* d_tokens, int64_t n_tokens, const int64_t*
         if (r != BM25_OK)
             return fail(r);
         vb = (uint32_t*)tok_doc;  // reused once pass 0 has consumed the doc ids
+        if (cudaFuncSetAttribute(k_radix_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSortedTileBytes) != cudaSuccess)
+            return fail(set_error(BM25_E_CUDA, "cannot give the sort kernel %d bytes of shared "
+                                               "memory", kSortedTileBytes));
 
         {
 
@@ -693,7 +707,7 @@ int build_index_device(const int32_t* d_tokens, int64_t n_tokens, const int64_t*
                                             d_total, scan_tmp, s));
                 {
                     ProfileScope ps_("k_radix_downsweep", s);
-                    k_radix_downsweep<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(
+                    k_radix_downsweep<<<(unsigned)n_tiles, kSortThreads, kSortedTileBytes, s>>>(
                         kin, vin, kout, vout, T, shift, bits, counts, n_tiles);
                 }
                 count_launch();

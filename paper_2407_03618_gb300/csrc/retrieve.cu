@@ -1579,6 +1579,7 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
     const size_t smem = staged_smem_bytes(W);
     // plan.threads consumer threads (4, 8 or 16 warps) and one producer warp
     auto tile_kernel = plan.threads == 128   ? k_tile_staged<4>
+                       : plan.threads == 192 ? k_tile_staged<6>
                        : plan.threads == 256 ? k_tile_staged<8>
                                              : k_tile_staged<16>;
     const int tile_threads = plan.threads + 32;

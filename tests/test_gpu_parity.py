@@ -146,7 +146,7 @@ def test_sort_spans_many_tiles_and_passes(torch_dev):
 # --------------------------------------------------------- retrieval -----
 
 @pytest.mark.parametrize("tile_docs,threads", [(1024, 128), (2048, 256), (16384, 512),
-                                               (4096, 512), (49152, 256)])
+                                               (4096, 512), (49152, 256), (3072, 192)])
 def test_retrieval_across_tiles(torch_dev, tile_docs, threads):
     """Small doc tiles force many (query, tile) items and a ragged last tile."""
     c = synth.make_corpus(9_999, 3_000, 1.1, ("poisson", 30), seed=2)
