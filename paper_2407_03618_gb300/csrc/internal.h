@@ -120,7 +120,7 @@ struct bm25_workspace {
     int32_t max_queries = 0;         // queries per sub-batch the arrays hold
     uint32_t* ctr = nullptr;         // [4] tiled count, dense count, dense queue head
     double* shift = nullptr;         // [q]  sum_i S0(q_i)
-    int4* lrec = nullptr;            // [li] tiled-path record {q, first token, end token, k'}
+    int4* lrec = nullptr;            // [li] tiled-path record {q, first token, end token, k' and a flag}
     int32_t* qkp = nullptr;          // [q]  k' = min(k_q, N)
     uint32_t* lpost = nullptr;       // [li] postings of the query's columns
     uint32_t* thresh = nullptr;      // [li] running k'-th best score key

@@ -39,19 +39,25 @@ constexpr int kTokChunk = 64;          // query tokens staged in shared memory a
 constexpr int kMergeThreads = 256;
 constexpr int kMergeBufCap = 4096;     // candidates a merge gathers into shared memory
 constexpr uint32_t kZeroKey = 0x80000000u;  // order_f32(0.0f)
+// A tiled-path record's k field: k' in the low 16 bits, and kNegScores when
+// one of the query's columns holds negative scores (Robertson terms with
+// DF > N/2), so that its documents' sums need not grow monotonically.
+constexpr int32_t kNegScores = 1 << 30;
+constexpr int32_t kKpMask = 0xffff;
 
 // ---- R0 ---------------------------------------------------------------------
 // Per query: checks its token range (clamped where malformed), sum_i S0(q_i)
 // in FP64, k' = min(k_q, N), and the postings of its columns (an upper bound
 // on the documents it touches).  Queries with at most dense_max postings go
 // to the list of the dense path (sq, count in ctr[1]); the others get a
-// record {q, first token, end token, k'} on the list of the tiled path
+// record {q, first token, end token, k' (+ kNegScores)} on the list of the tiled path
 // (lrec / lpost / thresh, count in ctr[0]), with their running threshold
 // reset.  List order follows the atomic appends; results do not depend on it.
 __global__ void k_query_prep(const int32_t* __restrict__ q_tokens, int64_t n_tok,
                              const int64_t* __restrict__ q_off, int32_t nq, int check_first,
                              int check_last, const int32_t* __restrict__ qk, int32_t kmax,
                              int64_t n_docs, const double* __restrict__ s0,
+                             const double* __restrict__ idf,
                              const int64_t* __restrict__ indptr, int32_t vocab, int64_t dense_max,
                              double* __restrict__ shift, int32_t* __restrict__ qkp,
                              int4* __restrict__ lrec, uint32_t* __restrict__ lpost,
@@ -67,6 +73,7 @@ __global__ void k_query_prep(const int32_t* __restrict__ q_tokens, int64_t n_tok
         const bool act = q < nq;
         int64_t lo = 0, hi = 0, post = 0;
         int32_t kp = 0;
+        bool neg = false;
         if (act) {
             lo = q_off[q];
             hi = q_off[q + 1];
@@ -90,6 +97,7 @@ __global__ void k_query_prep(const int32_t* __restrict__ q_tokens, int64_t n_tok
                 }
                 sum += s0[t];
                 post += indptr[t + 1] - indptr[t];
+                neg |= idf[t] < 0.0;
             }
             shift[q] = sum;
             qkp[q] = kp;
@@ -112,7 +120,7 @@ __global__ void k_query_prep(const int32_t* __restrict__ q_tokens, int64_t n_tok
             sq[base_d + __popc(bd & lt)] = (int32_t)q;
         if (tiled) {
             const uint32_t li = base_t + __popc(bt & lt);
-            lrec[li] = make_int4((int32_t)q, (int32_t)lo, (int32_t)hi, kp);
+            lrec[li] = make_int4((int32_t)q, (int32_t)lo, (int32_t)hi, kp | (neg ? kNegScores : 0));
             lpost[li] = post > 0xffffffffll ? 0xffffffffu : (uint32_t)post;
             thresh[li] = 0u;  // below every real score key
         }
@@ -358,9 +366,13 @@ constexpr int kCandCap = 256;        // candidate keys an item collects in the c
 constexpr int kWaitPolls = 1 << 22;  // mbarrier polls before a wait gives up
 
 
+constexpr int32_t kModeList = 0;   // first touches listed, claimed after the scatter
+constexpr int32_t kModeCross = 1;  // threshold crossings listed, the tile reset in bulk
+
 struct StageHdr {
     int32_t n;       // entries in the buffer
     int32_t last;    // 1: the item's last buffer
+    int32_t mode;    // kModeList or kModeCross (the same for all buffers of an item)
     int32_t tile, qi;        // the item's doc tile and query record
     uint32_t kp, post, tau;  // the query's k', postings, threshold when staged
 };
@@ -653,9 +665,12 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
                         StageHdr& hd = sh.hdr[s];
                         hd.n = aborted ? 0 : (int32_t)(e1 - e0);
                         hd.last = (last_chunk && k + 1 == nst) ? 1 : 0;
+                        // a sum can cross the threshold only once when it only grows
+                        hd.mode = (tau0 > kZeroKey && !(rec0.w & kNegScores)) ? kModeCross
+                                                                              : kModeList;
                         hd.tile = t0;
                         hd.qi = q0;
-                        hd.kp = (uint32_t)rec0.w;
+                        hd.kp = (uint32_t)(rec0.w & kKpMask);
                         hd.post = post0;
                         hd.tau = tau0;
                         mbar_arrive_expect_tx(&sh.full[s],
@@ -717,7 +732,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
     auto csync = [] { consumer_sync<NT>(); };
     const uint32_t ltmask = lanemask_lt();
     for (int32_t item = blockIdx.x; item < n_items; item += gridDim.x, par ^= 1u) {
-        int32_t tile = 0, qi = 0;
+        int32_t tile = 0, qi = 0, mode = kModeList;
         uint32_t qkp = 1, post = 0, tau = 0;
         // ---- scatter the item's staged postings ----------------------------------
         for (;;) {
@@ -736,6 +751,9 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
             qkp = min(max(hd.kp, 1u), (uint32_t)kstride);
             post = hd.post;
             tau = hd.tau;
+            mode = hd.mode == kModeCross ? kModeCross : kModeList;
+            const bool cross = mode == kModeCross;  // warp-uniform
+            const float tau_f = unorder_f32(tau);   // (used when tau is above the key of 0)
             const int32_t n_e = aborted ? 0 : min(max(hd.n, 0), kStageEntries);
             const bool last = hd.last != 0;
             const uint32_t d0 = (uint32_t)tile * (uint32_t)W;
@@ -746,10 +764,15 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
                 const int32_t e = e0 + lane;
                 const uint2 pe = e < n_e ? sb[e] : make_uint2(kPostPad, 0u);
                 const uint32_t dl = pe.x - d0;
+                // listed: a first touch (the old value is -0.0), or in the crossing
+                // mode the posting that lifts the sum to the threshold
                 bool first = false;
-                if (dl < wd)
-                    first = __float_as_uint(atomicAdd(&acc[dl], __uint_as_float(pe.y))) ==
-                            kUntouched;
+                if (dl < wd) {
+                    const float v = __uint_as_float(pe.y);
+                    const float old = atomicAdd(&acc[dl], v);
+                    first = cross ? (old + v >= tau_f && !(old >= tau_f))
+                                  : __float_as_uint(old) == kUntouched;
+                }
                 const uint32_t b = __ballot_sync(0xffffffffu, first);
                 if (b) {
                     const int leader = __ffs(b) - 1;
@@ -771,7 +794,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
             if (last || aborted)
                 break;
         }
-        consumer_sync<NT>();  // every posting added, every first touch listed
+        consumer_sync<NT>();  // every posting added, every first touch (crossing) listed
 
         const int64_t d0 = (int64_t)tile * W;
         const int32_t wd = (int32_t)min((int64_t)W, n_docs - d0);
@@ -787,8 +810,81 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
         bool tau_ok = false;
         auto emit = [&](u64 key, uint32_t slot) { out[slot] = key; };
         const bool zero_counts = tau <= kZeroKey;
+        // the k' best of the candidate keys clist[0 .. n_c) (n_c <= kCandCap) to the
+        // item's slots; a full set raises the threshold
+        auto select_clist = [&](uint32_t n_c) {
+            if (n_c <= kp) {
+                if (warp == OW) {
+                    uint32_t m = 0xffffffffu;
+                    for (uint32_t i = lane; i < n_c; i += 32) {
+                        const u64 key = clist[i];
+                        out[i] = key;
+                        m = min(m, (uint32_t)(key >> 32));
+                    }
+                    new_tau = __reduce_min_sync(0xffffffffu, m);
+                    tau_ok = n_c > 0;
+                }
+                n_emit = n_c;
+            } else if (n_c <= 32) {
+                if (warp == OW) {  // a few too many: sorted in registers
+                    u64 key = (uint32_t)lane < n_c ? clist[lane] : 0ull;
+                    key = warp_sort_desc(key);
+                    if ((uint32_t)lane < kp)
+                        out[lane] = key;
+                    new_tau = (uint32_t)(__shfl_sync(0xffffffffu, key, kp - 1) >> 32);
+                    tau_ok = true;
+                }
+                n_emit = kp;
+            } else {
+                if (tid == 0)
+                    st.ctr = 0;
+                select_top<false>(st, NT, csync, n_c, n_c, kp, 0, 0ull,
+                                  [&](uint32_t i) -> u64 { return clist[i]; }, emit);
+                new_tau = (uint32_t)(st.prefix >> 32);
+                tau_ok = true;
+                n_emit = kp;
+            }
+        };
+        auto reset_tile = [&]() {  // every accumulator of the tile back to -0.0
+            float4* a4 = reinterpret_cast<float4*>(acc);
+            const float4 z = make_float4(neg0, neg0, neg0, neg0);
+            for (int32_t i = tid; i < (wd + 3) / 4; i += NT)
+                a4[i] = z;
+        };
 
-        if (!zero_counts) {
+        if (mode == kModeCross) {
+            // ---- the listed documents are exactly those at or above the threshold -----
+            if (n_t <= (uint32_t)kCandCap) {
+                for (uint32_t i = tid; i < n_t; i += NT) {
+                    const uint32_t dl = tl[i];
+                    clist[i] = make_key(acc[dl], (uint32_t)(d0 + dl));
+                }
+                if (n_t > 0)
+                    consumer_sync<NT>();  // every candidate's sum read before the reset
+                reset_tile();
+                select_clist(n_t);
+            } else {
+                if (tid == 0)
+                    st.ctr = 0;
+                consumer_sync<NT>();  // (with n_t <= k' the select emits at once)
+                select_top<true>(st, NT, csync, (uint32_t)wd, n_t, kp, 0, 0ull,
+                                 [&](uint32_t d) -> u64 {
+                                     const float v = acc[d];
+                                     return __float_as_uint(v) != kUntouched &&
+                                                    order_f32(v) >= tau
+                                                ? make_key(v, (uint32_t)(d0 + d))
+                                                : 0ull;
+                                 },
+                                 emit);
+                n_emit = min(n_t, kp);
+                if (n_t > kp) {
+                    new_tau = (uint32_t)(st.prefix >> 32);
+                    tau_ok = true;
+                }
+                reset_tile();
+            }
+            consumer_sync<NT>();  // the tile is clean before the next scatter
+        } else if (!zero_counts) {
             // ---- claim: read and reset each touched document once ------------------
             for (uint32_t b0 = warp * 32; b0 < n_t; b0 += NT) {  // warp-uniform
                 const uint32_t t = b0 + lane;
@@ -822,42 +918,13 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
             consumer_sync<NT>();
             const uint32_t n_c = sh.lc[par];
             if (!sh.ovf[par]) {
-                if (n_c <= kp) {
-                    if (warp == OW) {
-                        uint32_t m = 0xffffffffu;
-                        for (uint32_t i = lane; i < n_c; i += 32) {
-                            const u64 key = clist[i];
-                            out[i] = key;
-                            m = min(m, (uint32_t)(key >> 32));
-                        }
-                        new_tau = __reduce_min_sync(0xffffffffu, m);
-                        tau_ok = n_c > 0;
-                    }
-                    n_emit = n_c;
-                } else if (n_c <= 32) {
-                    if (warp == OW) {  // a few too many: sorted in registers
-                        u64 key = (uint32_t)lane < n_c ? clist[lane] : 0ull;
-                        key = warp_sort_desc(key);
-                        if ((uint32_t)lane < kp)
-                            out[lane] = key;
-                        new_tau = (uint32_t)(__shfl_sync(0xffffffffu, key, kp - 1) >> 32);
-                        tau_ok = true;
-                    }
-                    n_emit = kp;
-                } else {
-                    if (tid == 0)
-                        st.ctr = 0;
-                    select_top<false>(st, NT, csync, n_c, n_c, kp, 0, 0ull,
-                                      [&](uint32_t i) -> u64 { return clist[i]; }, emit);
-                    new_tau = (uint32_t)(st.prefix >> 32);
-                    tau_ok = true;
-                    n_emit = kp;
-                }
+                select_clist(n_c);
             } else {
                 // more candidates than the list holds: select over the list and
                 // the sums put back in the tile
                 if (tid == 0)
                     st.ctr = 0;
+                consumer_sync<NT>();  // (with n_c <= k' the select emits at once)
                 select_top<true>(st, NT, csync, (uint32_t)kCandCap + (uint32_t)wd, n_c, kp, 0, 0ull,
                                  [&](uint32_t i) -> u64 {
                                      if (i < (uint32_t)kCandCap)
@@ -996,7 +1063,7 @@ __global__ void __launch_bounds__(kMergeThreads)
         return;
     const int4 rec = lrec[b];
     const int32_t q = rec.x;
-    const uint32_t kp = (uint32_t)rec.w;
+    const uint32_t kp = (uint32_t)(rec.w & kKpMask);
     int sz_all = 1;
     while (sz_all < kstride)
         sz_all <<= 1;
@@ -1614,7 +1681,7 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
             ProfileScope ps_("k_query_prep", s);
             k_query_prep<<<std::max(g0, 1), 256, 0, s>>>(
                 q_tokens, n_tok, qo, nb, q0 == 0, q0 + nb == nq, q_k ? q_k + q0 : nullptr, kmax,
-                N, ix->s0, ix->indptr, ix->vocab, g.dense_max, ws->shift, ws->qkp, ws->lrec,
+                N, ix->s0, ix->idf, ix->indptr, ix->vocab, g.dense_max, ws->shift, ws->qkp, ws->lrec,
                 ws->lpost, ws->thresh, ws->sq, ws->ctr, ix->status);
         }
         count_launch();
