@@ -17,6 +17,7 @@
 //   K8 k_score           S(t,D) - S0(t) per CSC entry in FP32, written to the
 //                        CSC and to the packed copy that staged retrieval
 //                        reads (each column 16-byte aligned)
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -99,60 +100,94 @@ __global__ void k_doc_prep(const int64_t* __restrict__ off, int64_t n_docs, int6
 }
 
 // ---- K2: stable LSD radix sort -------------------------------------------
-// Reduce-then-scan per pass (Satish et al. 2009; Merrill and Grimshaw 2011):
-// per-tile digit counts, one exclusive scan over the digit-major count table,
-// then a scatter that ranks each tile's items stably.  No kernel waits on
-// another block.
+// Reduce-then-scan per pass (Satish et al. 2009; Merrill and Grimshaw 2011),
+// partitioned the way those papers do it for a resident grid: block b of the
+// G-block downsweep grid owns the consecutive tiles [b*nt/G, (b+1)*nt/G) of
+// the input and walks them in order, ranking each tile's items stably and
+// advancing its per-digit output bases by the tile's counts.  The upsweep
+// splits each of those ranges over S blocks (a full wave of small blocks)
+// and counts their digits; one exclusive scan over the [digit][b][s] table
+// gives every (digit, b) its first output position at s = 0.  No kernel
+// waits on another block.  The table has 2^bits * G * S words instead of
+// one column per tile, and the writes of one digit by consecutive tiles of
+// a block continue each other.
 
-// Per-tile digit histogram.  counts is digit-major: counts[d * n_tiles + tile].
-// With vocab > 0 it also checks every key against [0, vocab).
+// First and last+1 tile of downsweep block b.
+__device__ __forceinline__ void sort_block_tiles(int64_t b, int64_t G, int64_t n_tiles,
+                                                 int64_t& t0, int64_t& t1)
+{
+    t0 = b * n_tiles / G;
+    t1 = (b + 1) * n_tiles / G;
+}
+
+// Digit histogram of upsweep block (b, s) = (blockIdx.x / S, blockIdx.x % S):
+// counts[(d * G + b) * S + s].  One private histogram per warp, plain shared
+// atomics (grouping a warp's equal digits with __match_any_sync first was
+// slower).  With vocab > 0 it also checks every key against [0, vocab).
 __global__ void __launch_bounds__(kSortThreads)
     k_radix_upsweep(const uint32_t* __restrict__ keys, int64_t n, int shift, int bits,
-                    uint32_t* __restrict__ counts, int64_t n_tiles, uint32_t vocab, int* status)
+                    uint32_t* __restrict__ counts, int64_t n_tiles, int S, uint32_t vocab,
+                    int* status)
 {
-    __shared__ uint32_t hist[kMaxBuckets];
+    __shared__ uint32_t whist[kSortWarps][kMaxBuckets];
     const int nb = 1 << bits;
     const uint32_t mask = (uint32_t)nb - 1u;
-    for (int d = threadIdx.x; d < nb; d += kSortThreads)
-        hist[d] = 0;
+    const int warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kSortWarps * kMaxBuckets; i += kSortThreads)
+        (&whist[0][0])[i] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    const int64_t G = gridDim.x / S, b = blockIdx.x / S, sub = blockIdx.x % S;
+    int64_t t0, t1;
+    sort_block_tiles(b, G, n_tiles, t0, t1);
+    const int64_t lo = (t0 + sub * (t1 - t0) / S) * kSortTile;
+    const int64_t hi = min((t0 + (sub + 1) * (t1 - t0) / S) * kSortTile, n);
     bool bad = false;
-#pragma unroll 4
-    for (int i = 0; i < kSortIpt; i++) {
-        int64_t p = base + (int64_t)i * kSortThreads + threadIdx.x;
-        uint32_t dg = 0xffffffffu;
-        if (p < n) {
-            uint32_t k = keys[p];
-            bad |= (vocab != 0u && k >= vocab);
-            dg = (k >> shift) & mask;
+    // rounds of 4 x 256 items, the loads of a round issued together
+    for (int64_t p0 = lo; p0 < hi; p0 += 4 * kSortThreads) {
+        uint32_t k[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int64_t p = p0 + i * kSortThreads + threadIdx.x;
+            k[i] = p < hi ? keys[p] : 0u;
         }
-        uint32_t peers = __match_any_sync(0xffffffffu, dg);
-        if (dg != 0xffffffffu && (peers & lanemask_lt()) == 0)
-            atomicAdd(&hist[dg], (uint32_t)__popc(peers));
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            if (p0 + i * kSortThreads + threadIdx.x < hi) {
+                bad |= (vocab != 0u && k[i] >= vocab);
+                atomicAdd(&whist[warp][(k[i] >> shift) & mask], 1u);
+            }
+        }
     }
     if (bad)
         set_status(status, BM25_E_TOKEN_RANGE);
     __syncthreads();
-    for (int d = threadIdx.x; d < nb; d += kSortThreads)
-        counts[(int64_t)d * n_tiles + blockIdx.x] = hist[d];
+    for (int d = threadIdx.x; d < nb; d += kSortThreads) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; w++)
+            c += whist[w][d];
+        counts[((int64_t)d * G + b) * S + sub] = c;
+    }
 }
 
-// Stable scatter.  Warp w owns items [w*512, w*512+512) of the tile and
-// walks them in 16 rounds of 32 consecutive items; __match_any_sync groups a
-// round's lanes by digit, so each item's rank among equal digits follows its
-// position.  Per-warp counters are then turned into per-warp bases by an
-// exclusive scan over warps, which keeps warp order = item order.  The items
-// are reordered in shared memory into the tile's digit order first, so that
+// Stable scatter of the block's tiles, in order.  Per tile: warp w owns
+// items [w*512, w*512+512) and walks them in 16 rounds of 32 consecutive
+// items; __match_any_sync groups a round's lanes by digit, so each item's
+// rank among equal digits follows its position.  Per-warp counters become
+// per-warp bases by an exclusive scan over warps (warp order = item order),
+// the items are reordered in shared memory into the tile's digit order, and
 // consecutive threads write consecutive global positions of one digit.
-__global__ void __launch_bounds__(kSortThreads)
+// Thread t keeps the block's running global base of digits 2t and 2t+1 in
+// registers.  The next tile's keys and doc ids are loaded while the current
+// tile is written out.
+__global__ void __launch_bounds__(kSortThreads, 2)
     k_radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                       uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n,
-                      int shift, int bits, const uint32_t* __restrict__ offsets, int64_t n_tiles)
+                      int shift, int bits, const uint32_t* __restrict__ offsets, int64_t n_tiles,
+                      int S)
 {
-    __shared__ uint32_t wcnt[kSortWarps][kMaxBuckets];
-    __shared__ uint32_t gbase[kMaxBuckets];
-    __shared__ uint32_t dstart[kMaxBuckets];
+    __shared__ uint32_t wcnt[kSortWarps][kMaxBuckets];  // per-warp counts, then tile positions
+    __shared__ uint32_t gofs[kMaxBuckets];  // global position - position in the sorted tile
     __shared__ uint32_t scan_buf[33];
     extern __shared__ uint32_t sorted_tile[];  // kSortTile keys, then kSortTile doc ids
     uint32_t* sk = sorted_tile;
@@ -160,79 +195,101 @@ __global__ void __launch_bounds__(kSortThreads)
     const int nb = 1 << bits;
     const uint32_t mask = (uint32_t)nb - 1u;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < kSortWarps * kMaxBuckets; i += kSortThreads)
-        (&wcnt[0][0])[i] = 0;
-    for (int d = threadIdx.x; d < nb; d += kSortThreads)
-        gbase[d] = offsets[(int64_t)d * n_tiles + blockIdx.x];
-    __syncthreads();
-
-    const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
-    const int tile_n = (int)min((int64_t)kSortTile, n - tile0);
-    const int64_t base = tile0 + warp * (kSortIpt * 32);
     const uint32_t lt = lanemask_lt();
-    uint32_t k[kSortIpt], v[kSortIpt], rank[kSortIpt];
-#pragma unroll
-    for (int r = 0; r < kSortIpt; r++) {
-        int64_t p = base + r * 32 + lane;
-        bool ok = p < n;
-        k[r] = ok ? keys_in[p] : 0u;
-        v[r] = ok ? vals_in[p] : 0u;
-    }
-#pragma unroll
-    for (int r = 0; r < kSortIpt; r++) {
-        int64_t p = base + r * 32 + lane;
-        bool ok = p < n;
-        uint32_t dg = ok ? ((k[r] >> shift) & mask) : 0xffffffffu;
-        uint32_t peers = __match_any_sync(0xffffffffu, dg);
-        uint32_t before = ok ? wcnt[warp][dg] : 0u;
-        __syncwarp();
-        if (ok && (peers & lt) == 0)
-            wcnt[warp][dg] = before + (uint32_t)__popc(peers);
-        __syncwarp();
-        rank[r] = before + (uint32_t)__popc(peers & lt);
-    }
-    __syncthreads();
-    // per digit: exclusive scan over warps (warp bases) and the tile total;
-    // then the digits' start offsets in the tile
-    // (thread t owns digits 2t and 2t + 1: up to 512 digits)
     static_assert(kMaxBuckets <= 2 * kSortThreads, "two digits per thread");
-    uint32_t tot2[2] = {0u, 0u};
+    uint32_t run[2];
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         const int d = 2 * (int)threadIdx.x + h;
-        if (d < nb) {
+        run[h] = d < nb ? offsets[((int64_t)d * gridDim.x + blockIdx.x) * S] : 0u;
+    }
+    int64_t t0, t1;
+    sort_block_tiles(blockIdx.x, gridDim.x, n_tiles, t0, t1);
+    uint32_t k[kSortIpt], v[kSortIpt];
+    const int wbase = warp * (kSortIpt * 32) + lane;  // item index in the tile, round 0
+    auto load_tile = [&](int64_t tile) {
+        const int64_t first = tile * kSortTile + wbase;
+        const uint32_t* kp = keys_in + first;
+        const uint32_t* vp = vals_in + first;
+        const int rem = (int)min((int64_t)kSortTile, n - first);  // may be <= 0
 #pragma unroll
-            for (int w = 0; w < kSortWarps; w++) {
-                const uint32_t t = wcnt[w][d];
-                wcnt[w][d] = tot2[h];
-                tot2[h] += t;
+        for (int r = 0; r < kSortIpt; r++) {
+            const bool ok = r * 32 < rem;
+            k[r] = ok ? kp[r * 32] : 0u;
+            v[r] = ok ? vp[r * 32] : 0u;
+        }
+    };
+    if (t0 < t1)
+        load_tile(t0);
+    for (int64_t tile = t0; tile < t1; tile++) {
+        const int64_t tile0 = tile * kSortTile;
+        const int tile_n = (int)min((int64_t)kSortTile, n - tile0);
+        for (int i = threadIdx.x; i < kSortWarps * kMaxBuckets; i += kSortThreads)
+            (&wcnt[0][0])[i] = 0;
+        __syncthreads();
+        uint32_t rank[kSortIpt];
+#pragma unroll
+        for (int r = 0; r < kSortIpt; r++) {
+            const bool ok = wbase + r * 32 < tile_n;
+            const uint32_t dg = ok ? ((k[r] >> shift) & mask) : 0xffffffffu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+            const uint32_t before = ok ? wcnt[warp][dg] : 0u;
+            __syncwarp();
+            if (ok && (peers & lt) == 0)
+                wcnt[warp][dg] = before + (uint32_t)__popc(peers);
+            __syncwarp();
+            rank[r] = before + (uint32_t)__popc(peers & lt);
+        }
+        __syncthreads();
+        // per digit: the tile total and the exclusive scan over warps; then
+        // the digit's start in the tile, folded into the warp bases
+        uint32_t tot2[2] = {0u, 0u};
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int d = 2 * (int)threadIdx.x + h;
+            if (d < nb) {
+#pragma unroll
+                for (int w = 0; w < kSortWarps; w++)
+                    tot2[h] += wcnt[w][d];
             }
         }
-    }
-    uint32_t all;
-    const uint32_t ds = block_exclusive_sum(tot2[0] + tot2[1], scan_buf, &all);
-    if (2 * (int)threadIdx.x < nb)
-        dstart[2 * threadIdx.x] = ds;
-    if (2 * (int)threadIdx.x + 1 < nb)
-        dstart[2 * threadIdx.x + 1] = ds + tot2[0];
-    __syncthreads();
+        uint32_t all;
+        const uint32_t ds = block_exclusive_sum(tot2[0] + tot2[1], scan_buf, &all);
 #pragma unroll
-    for (int r = 0; r < kSortIpt; r++) {
-        int64_t p = base + r * 32 + lane;
-        if (p < n) {
-            uint32_t dg = (k[r] >> shift) & mask;
-            uint32_t local = dstart[dg] + wcnt[warp][dg] + rank[r];
-            sk[local] = k[r];
-            sv[local] = v[r];
+        for (int h = 0; h < 2; h++) {
+            const int d = 2 * (int)threadIdx.x + h;
+            if (d < nb) {
+                uint32_t c = ds + (h ? tot2[0] : 0u);  // the digit's start in the tile
+                gofs[d] = run[h] - c;
+                run[h] += tot2[h];
+#pragma unroll
+                for (int w = 0; w < kSortWarps; w++) {
+                    const uint32_t t = wcnt[w][d];
+                    wcnt[w][d] = c;
+                    c += t;
+                }
+            }
         }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < tile_n; i += kSortThreads) {
-        const uint32_t kk = sk[i];
-        const uint32_t dg = (kk >> shift) & mask;
-        const uint32_t pos = gbase[dg] + ((uint32_t)i - dstart[dg]);
-        keys_out[pos] = kk;
-        vals_out[pos] = sv[i];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kSortIpt; r++) {
+            if (wbase + r * 32 < tile_n) {
+                const uint32_t local = wcnt[warp][(k[r] >> shift) & mask] + rank[r];
+                sk[local] = k[r];
+                sv[local] = v[r];
+            }
+        }
+        __syncthreads();
+        if (tile + 1 < t1)
+            load_tile(tile + 1);
+        for (int i = threadIdx.x; i < tile_n; i += kSortThreads) {
+            const uint32_t kk = sk[i];
+            const uint32_t pos = gofs[(kk >> shift) & mask] + (uint32_t)i;
+            keys_out[pos] = kk;
+            vals_out[pos] = sv[i];
+        }
+        // (the next tile's first barrier orders these reads of sk, sv and
+        // gofs before their next writes)
     }
 }
 
@@ -242,13 +299,18 @@ __global__ void __launch_bounds__(kSortThreads)
 // (a distinct (term, doc) pair) when its pair differs from the previous
 // position's.  Runs are numbered in position order, i.e. by (round, warp,
 // lane), so the writes of one warp-round are consecutive.
+// All four loads are unconditional (clamped at the ends), so that a thread's
+// loads for several positions are in flight together.
 __device__ __forceinline__ bool is_head(const uint32_t* __restrict__ keys,
-                                        const uint32_t* __restrict__ vals, int64_t p,
+                                        const uint32_t* __restrict__ vals, int64_t p, int64_t n,
                                         uint32_t& kk, uint32_t& vv)
 {
-    kk = keys[p];
-    vv = vals[p];
-    return p == 0 || kk != keys[p - 1] || vv != vals[p - 1];
+    const int64_t pc = p < n ? p : n - 1;
+    const int64_t pp = pc > 0 ? pc - 1 : 0;
+    kk = keys[pc];
+    vv = vals[pc];
+    const uint32_t kp = keys[pp], vp = vals[pp];
+    return p < n && (p == 0 || kk != kp || vv != vp);
 }
 
 __global__ void __launch_bounds__(kSortThreads)
@@ -263,7 +325,7 @@ __global__ void __launch_bounds__(kSortThreads)
     for (int i = 0; i < kSortIpt; i++) {
         const int64_t p = base + i * kSortThreads + threadIdx.x;
         uint32_t kk, vv;
-        const bool h = p < n && is_head(keys, vals, p, kk, vv);
+        const bool h = is_head(keys, vals, p, n, kk, vv);
         const uint32_t bal = __ballot_sync(0xffffffffu, h);
         if (lane == 0)
             c += __popc(bal);
@@ -290,7 +352,7 @@ __global__ void __launch_bounds__(kSortThreads)
 #pragma unroll
     for (int i = 0; i < kSortIpt; i++) {
         const int64_t p = base + i * kSortThreads + threadIdx.x;
-        const bool h = p < n && is_head(keys, vals, p, kk[i], vv[i]);
+        const bool h = is_head(keys, vals, p, n, kk[i], vv[i]);
         bals[i] = __ballot_sync(0xffffffffu, h);
         if (lane == 0)
             seg_cnt[i * kSortWarps + warp] = __popc(bals[i]);
@@ -655,7 +717,24 @@ int build_index_device(const int32_t* d_tokens, int64_t n_tokens, const int64_t*
             nbits++;
         const int passes = (nbits + kMaxDigitBits - 1) / kMaxDigitBits;
         const int dbits = (nbits + passes - 1) / passes;
-        const int64_t ncounts = ((int64_t)1 << dbits) * n_tiles;
+        // the sort's grid: one wave of resident downsweep blocks (both sort
+        // kernels of a pass use it: it fixes which tiles each block owns)
+        if (cudaFuncSetAttribute(k_radix_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSortedTileBytes) != cudaSuccess)
+            return fail(set_error(BM25_E_CUDA, "cannot give the sort kernel %d bytes of shared "
+                                               "memory", kSortedTileBytes));
+        int sort_bps = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sort_bps, k_radix_downsweep, kSortThreads,
+                                                          kSortedTileBytes) != cudaSuccess)
+            sort_bps = 1;
+        const int64_t sort_grid = std::max<int64_t>(
+            1, std::min<int64_t>(n_tiles, (int64_t)std::max(sort_bps, 1) * di.sm_count));
+        // upsweep blocks per downsweep block: about 8 resident 256-thread
+        // blocks per SM in all
+        const int sort_split = (int)std::max<int64_t>(
+            1, std::min<int64_t>((8LL * di.sm_count + sort_grid - 1) / sort_grid,
+                                 n_tiles / sort_grid));
+        const int64_t ncounts = ((int64_t)1 << dbits) * sort_grid * sort_split;
         int r = BM25_OK;
         if (r == BM25_OK) r = tmp.alloc(&tok_doc, T, pool);
         if (r == BM25_OK) r = tmp.alloc(&len_factor, n_docs, pool);
@@ -670,10 +749,6 @@ int build_index_device(const int32_t* d_tokens, int64_t n_tokens, const int64_t*
         if (r != BM25_OK)
             return fail(r);
         vb = (uint32_t*)tok_doc;  // reused once pass 0 has consumed the doc ids
-        if (cudaFuncSetAttribute(k_radix_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kSortedTileBytes) != cudaSuccess)
-            return fail(set_error(BM25_E_CUDA, "cannot give the sort kernel %d bytes of shared "
-                                               "memory", kSortedTileBytes));
 
         {
 
@@ -697,18 +772,19 @@ int build_index_device(const int32_t* d_tokens, int64_t n_tokens, const int64_t*
                 const int bits = (nbits - shift < dbits) ? nbits - shift : dbits;
                 {
                     ProfileScope ps_("k_radix_upsweep", s);
-                    k_radix_upsweep<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(
-                        kin, T, shift, bits, counts, n_tiles, pass == 0 ? (uint32_t)vocab : 0u,
-                        ix->status);
+                    k_radix_upsweep<<<(unsigned)(sort_grid * sort_split), kSortThreads, 0, s>>>(
+                        kin, T, shift, bits, counts, n_tiles, sort_split,
+                        pass == 0 ? (uint32_t)vocab : 0u, ix->status);
                 }
                 count_launch();
                 BM25_LAUNCH_CHECK();
-                BM25_TRY(exclusive_scan_u32(counts, counts, ((int64_t)1 << bits) * n_tiles,
+                BM25_TRY(exclusive_scan_u32(counts, counts,
+                                            ((int64_t)1 << bits) * sort_grid * sort_split,
                                             d_total, scan_tmp, s));
                 {
                     ProfileScope ps_("k_radix_downsweep", s);
-                    k_radix_downsweep<<<(unsigned)n_tiles, kSortThreads, kSortedTileBytes, s>>>(
-                        kin, vin, kout, vout, T, shift, bits, counts, n_tiles);
+                    k_radix_downsweep<<<(unsigned)sort_grid, kSortThreads, kSortedTileBytes, s>>>(
+                        kin, vin, kout, vout, T, shift, bits, counts, n_tiles, sort_split);
                 }
                 count_launch();
                 BM25_LAUNCH_CHECK();
