@@ -82,16 +82,22 @@ __global__ void k_doc_prep(const int64_t* __restrict__ off, int64_t n_docs, int6
             last = 31 - __clz(has_mask);
         }
         const int64_t end = __shfl_sync(0xffffffffu, hi, last);
-        // warp-uniform loop: every lane runs every step's shuffles
+        // warp-uniform loop over windows of 32 positions.  Position p belongs
+        // to the last lane whose document starts at or before p: the lanes
+        // started by the window's first position are counted by one ballot,
+        // and the few documents starting inside the window (a window holds
+        // ~32 / mean length of them) are added one by one.  Lanes past the
+        // last document start at n_tokens and never count.
+        const uint32_t live = (last == 31) ? 0xffffffffu : ((2u << last) - 1u);
         for (int64_t pb = start; pb < end; pb += 32) {
             const int64_t p = pb + lane;
-            // the last lane whose document starts at or before p
-            int idx = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int64_t s_lo = __shfl_sync(0xffffffffu, lo, (idx + step) & 31);
-                if (idx + step <= last && s_lo <= p)
-                    idx += step;
+            const uint32_t before = __ballot_sync(0xffffffffu, lo <= pb) & live;
+            uint32_t inside = __ballot_sync(0xffffffffu, lo > pb && lo <= pb + 31) & live;
+            int idx = __popc(before) - 1;  // >= 0: lane 0 starts at `start` <= pb
+            while (inside) {               // warp-uniform
+                const int l = __ffs(inside) - 1;
+                inside &= inside - 1u;
+                idx += (__shfl_sync(0xffffffffu, lo, l) <= p) ? 1 : 0;
             }
             if (p < end)
                 tok_doc[p] = (int32_t)((g << 5) + idx);
@@ -179,7 +185,9 @@ __global__ void __launch_bounds__(kSortThreads)
 // consecutive threads write consecutive global positions of one digit.
 // Thread t keeps the block's running global base of digits 2t and 2t+1 in
 // registers.  The next tile's keys and doc ids are loaded while the current
-// tile is written out.
+// tile is written out; the doc ids wait in shared memory in tile order
+// during the ranking, which keeps the kernel within the registers of three
+// resident blocks per SM.
 __global__ void __launch_bounds__(kSortThreads, 2)
     k_radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                       uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n,
@@ -189,7 +197,8 @@ __global__ void __launch_bounds__(kSortThreads, 2)
     __shared__ uint32_t wcnt[kSortWarps][kMaxBuckets];  // per-warp counts, then tile positions
     __shared__ uint32_t gofs[kMaxBuckets];  // global position - position in the sorted tile
     __shared__ uint32_t scan_buf[33];
-    extern __shared__ uint32_t sorted_tile[];  // kSortTile keys, then kSortTile doc ids
+    // kSortTile sorted keys, kSortTile sorted doc ids, kSortTile doc ids in tile order
+    extern __shared__ uint32_t sorted_tile[];
     uint32_t* sk = sorted_tile;
     uint32_t* sv = sorted_tile + kSortTile;
     const int nb = 1 << bits;
@@ -460,26 +469,46 @@ __global__ void k_score(const int32_t* __restrict__ run_pos, const int32_t* __re
                         uint2* __restrict__ posts)
 {
     const int64_t nnz = *d_nnz;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        int32_t tf = run_pos[j + 1] - run_pos[j];
-        float f = (float)tf;
-        const int32_t doc = indices[j];
-        const int32_t term = run_term[j];
-        float a = len_factor[doc];
-        float c = coef[term];
-        float s;
-        if (variant == BM25_L) {
-            float cc = f * a;
-            s = c * cc / (k1_plus_delta + cc);
-        } else {
-            s = c * f / (f + a);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    constexpr int U = 4;  // entries per thread and iteration, their loads issued together
+    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j0 < nnz; j0 += U * stride) {
+        int32_t tf[U], doc[U], term[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int64_t j = j0 + u * stride;
+            const bool ok = j < nnz;
+            tf[u] = ok ? run_pos[j + 1] - run_pos[j] : 0;
+            doc[u] = ok ? indices[j] : 0;
+            term[u] = ok ? run_term[j] : 0;
         }
-        s = (s == 0.0f) ? 0.0f : s;  // never -0.0: retrieval uses -0.0 as "untouched"
-        tf_out[j] = tf;
-        data[j] = s;
-        const int64_t c0 = indptr[term];
-        posts[post_start(c0, term) + (j - c0)] = make_uint2((uint32_t)doc, __float_as_uint(s));
+        float a[U], c[U];
+        int64_t c0[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const bool ok = j0 + u * stride < nnz;
+            a[u] = ok ? len_factor[doc[u]] : 1.0f;
+            c[u] = ok ? coef[term[u]] : 0.0f;
+            c0[u] = ok ? indptr[term[u]] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int64_t j = j0 + u * stride;
+            if (j >= nnz)
+                break;
+            const float f = (float)tf[u];
+            float sc;
+            if (variant == BM25_L) {
+                const float cc = f * a[u];
+                sc = c[u] * cc / (k1_plus_delta + cc);
+            } else {
+                sc = c[u] * f / (f + a[u]);
+            }
+            sc = (sc == 0.0f) ? 0.0f : sc;  // never -0.0: retrieval uses -0.0 as "untouched"
+            tf_out[j] = tf[u];
+            data[j] = sc;
+            posts[post_start(c0[u], term[u]) + (j - c0[u])] =
+                make_uint2((uint32_t)doc[u], __float_as_uint(sc));
+        }
     }
 }
 
