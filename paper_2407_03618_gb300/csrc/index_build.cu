@@ -185,9 +185,7 @@ __global__ void __launch_bounds__(kSortThreads)
 // consecutive threads write consecutive global positions of one digit.
 // Thread t keeps the block's running global base of digits 2t and 2t+1 in
 // registers.  The next tile's keys and doc ids are loaded while the current
-// tile is written out; the doc ids wait in shared memory in tile order
-// during the ranking, which keeps the kernel within the registers of three
-// resident blocks per SM.
+// tile is written out.
 __global__ void __launch_bounds__(kSortThreads, 2)
     k_radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                       uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n,

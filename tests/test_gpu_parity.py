@@ -134,9 +134,11 @@ def test_tiny_workload_build_and_retrieve(torch_dev, variant):
 
 
 def test_sort_spans_many_tiles_and_passes(torch_dev):
-    """Enough tokens for thousands of sort tiles, a vocabulary needing three
-    radix passes, and a ragged last tile."""
-    c = synth.make_corpus(40_001, 150_000, 1.05, ("lognormal", 60, 0.6), seed=5)
+    """About 5.4M tokens = ~1,300 sort tiles of 4,096: more tiles than one wave
+    of sort blocks, so each block walks several tiles in order and its range
+    is counted by several upsweep blocks; a 300k vocabulary (19 bits) needing
+    three radix passes; a ragged last tile."""
+    c = synth.make_corpus(90_001, 300_000, 1.05, ("lognormal", 60, 0.6), seed=5)
     ix = _build(torch_dev, c, "lucene")
     orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, 0)
     _check_structure(ix, orc)
