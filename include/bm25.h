@@ -95,7 +95,7 @@ typedef struct bm25_plan {
     int32_t tile_docs;          /* doc-tile width: a multiple of 1024 in [1024, 49152]
                                    (default 7168) */
     int32_t block_threads;      /* consumer threads per CTA of the tiled kernel: 128, 192,
-                                   256 or 512 (default 256; one producer warp is added) */
+                                   256 or 512 (default 192; one producer warp is added) */
     int32_t dense_max_postings; /* dense-path bound for AUTO / L2_DENSE, in [0, 2^22]
                                    (default 4096) */
 } bm25_plan;
@@ -291,9 +291,11 @@ int bm25_index_get_plan(const bm25_index* index, bm25_plan* plan);
 
 /* Times retrieval of a sample batch (device arrays, as in bm25_retrieve,
  * with one k for all queries) under candidate plans and makes the fastest
- * the index's plan.  Candidates: tile widths 6144, 7168, 8192 and 12288 with
- * every query tiled, then, with the best width, dense-path bounds of 2048 ..
- * 32768 postings (the accumulator per query-length bucket).  Each candidate
+ * the index's plan.  Candidates: tile widths 6144, 7168, 8192, 10240 and
+ * 12288 with every query tiled and 192 consumer threads, then 128 and 256
+ * consumer threads at the best width, then, with the best of those,
+ * dense-path bounds of 2048 .. 32768 postings (the accumulator per
+ * query-length bucket).  Each candidate
  * runs once untimed and twice timed (CUDA events on `cuda_stream`); the best
  * of the two counts.  Synchronous; allocates its own scratch.  Results of
  * retrieval do not depend on the plan.

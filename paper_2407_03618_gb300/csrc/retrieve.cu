@@ -369,7 +369,7 @@ constexpr int kWaitPolls = 1 << 22;  // mbarrier polls before a wait gives up
 constexpr int32_t kModeList = 0;   // first touches listed, claimed after the scatter
 constexpr int32_t kModeCross = 1;  // threshold crossings listed, the tile reset in bulk
 
-struct StageHdr {
+struct __align__(16) StageHdr {
     int32_t n;       // entries in the buffer
     int32_t last;    // 1: the item's last buffer
     int32_t mode;    // kModeList or kModeCross (the same for all buffers of an item)
@@ -526,7 +526,8 @@ size_t staged_smem_bytes(int32_t W)
 // token's packed column at or past document j * W (j = n_tiles: the column
 // end), from k_seg_bounds<true>.
 // Four CTAs per SM at the default tile width (shared memory allows it; the
-// register bound, 56 per thread at 8 consumer warps, makes it so).
+// register bound makes it so: 67 per thread at 6 consumer warps, the
+// default, 56 at 8).
 template <int CW>
 __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
     k_tile_staged(int64_t n_docs, const uint2* __restrict__ posts, const uint32_t* __restrict__ seg,
@@ -848,6 +849,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
         auto reset_tile = [&]() {  // every accumulator of the tile back to -0.0
             float4* a4 = reinterpret_cast<float4*>(acc);
             const float4 z = make_float4(neg0, neg0, neg0, neg0);
+#pragma unroll 8
             for (int32_t i = tid; i < (wd + 3) / 4; i += NT)
                 a4[i] = z;
         };

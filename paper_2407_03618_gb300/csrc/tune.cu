@@ -4,6 +4,8 @@
 // sum per query batch); the choices tuned are the ones this library adds:
 //   - the doc-tile width W of the shared-memory path (smaller tiles: more
 //     CTAs per SM but more (tile, query) items per query);
+//   - the consumer warps per CTA of that path (fewer: less per-item work
+//     spread over fewer warps, more issue slots per warp);
 //   - the accumulator per query-length bucket: queries whose columns hold at
 //     most dense_max postings take the dense path, the rest the tiled path.
 // The top-k radix width is fixed at 8-bit digits (one 256-bin histogram per
@@ -118,11 +120,18 @@ extern "C" int bm25_autotune(bm25_index* ix, const int32_t* query_tokens, int64_
         }
     };
     // 1. the tile width, every query on the tiled path
-    for (int32_t W : {6144, 7168, 8192, 12288}) {
+    for (int32_t W : {6144, 7168, 8192, 10240, 12288}) {
         Plan p = base;
         p.accumulator = BM25_ACC_SMEM_TILED;
         p.tile_docs = W;
-        p.threads = 256;
+        p.threads = 192;
+        trial(p);
+    }
+    // 1b. the consumer threads per CTA at that width
+    const Plan width = cur;
+    for (int32_t th : {128, 256}) {
+        Plan p = width;
+        p.threads = th;
         trial(p);
     }
     // 2. the dense-path bound with that tile width
