@@ -416,6 +416,7 @@ def extras(args, line, bm25, corpus, queries, tok, off, qt, qo, ids, sc, dev, pr
         traffic = None
         # profiles/<kernel>_<workload>_traffic.md holds "key: value" lines from
         # one ncu capture; used only while the sources match its build stamp
+        # and the plan timed here is the one captured
         tr_path = os.path.join(ROOT, "profiles",
                                f"{name}_{w.name.replace('-', '')}_traffic.md")
         try:
@@ -426,7 +427,10 @@ def extras(args, line, bm25, corpus, queries, tok, off, qt, qo, ids, sc, dev, pr
                         key, _, val = line.partition(":")
                         kv[key.strip().strip("`* ")] = val.strip().strip("`* ")
             from paper_2407_03618_gb300 import build_ext
-            if kv.get("build_stamp") == build_ext._stamp() and kv.get("workload") == w.name:
+            plan_here = ",".join(str(used[f]) for f in ("accumulator", "tile_docs", "block_threads",
+                                                         "dense_max_postings"))
+            if (kv.get("build_stamp") == build_ext._stamp() and kv.get("workload") == w.name
+                    and kv.get("plan", plan_here) == plan_here):
                 traffic = int(kv["traffic_bytes_per_launch"])
         except (OSError, ValueError, KeyError):
             pass

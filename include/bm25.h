@@ -93,7 +93,7 @@ enum bm25_accumulator {
 typedef struct bm25_plan {
     int32_t accumulator;        /* enum bm25_accumulator */
     int32_t tile_docs;          /* doc-tile width: a multiple of 1024 in [1024, 49152]
-                                   (default 7168) */
+                                   (default 10240) */
     int32_t block_threads;      /* consumer threads per CTA of the tiled kernel: 128, 192,
                                    256 or 512 (default 192; one producer warp is added) */
     int32_t dense_max_postings; /* dense-path bound for AUTO / L2_DENSE, in [0, 2^22]

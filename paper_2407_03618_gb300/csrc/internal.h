@@ -74,7 +74,7 @@ constexpr uint32_t kPostPad = 0xffffffffu;  // doc id of a padding slot (beyond 
 
 struct Plan {
     int accumulator = BM25_ACC_AUTO;
-    int32_t tile_docs = 7168;
+    int32_t tile_docs = 10240;
     int32_t threads = 192;
     int32_t dense_max = 4096;   // postings bound of the dense path (AUTO, L2_DENSE)
 };

@@ -1529,7 +1529,7 @@ int reserve(const bm25_index* ix, bm25_workspace* ws, const Geometry& g, int64_t
 
 int32_t tile_width(const Plan& plan, int64_t n_docs)
 {
-    int32_t W = plan.tile_docs > 0 ? plan.tile_docs : 7168;
+    int32_t W = plan.tile_docs > 0 ? plan.tile_docs : Plan().tile_docs;
     // multiples of 128 keep the shared-memory carve-up 16-byte aligned
     const int64_t w_need = (n_docs + 127) / 128 * 128;
     if (W > w_need)
