@@ -295,7 +295,9 @@ int bm25_index_get_plan(const bm25_index* index, bm25_plan* plan);
  * 12288 with every query tiled and 192 consumer threads, then 128 and 256
  * consumer threads at the best width, then, with the best of those,
  * dense-path bounds of 2048 .. 32768 postings (the accumulator per
- * query-length bucket).  Each candidate
+ * query-length bucket).  Each step tries the library's default first, and a
+ * later candidate replaces the best so far only when more than 1 % faster, so
+ * that timing noise does not move the plan between runs.  Each candidate
  * runs once untimed and twice timed (CUDA events on `cuda_stream`); the best
  * of the two counts.  Synchronous; allocates its own scratch.  Results of
  * retrieval do not depend on the plan.

@@ -98,6 +98,7 @@ extern "C" int bm25_autotune(bm25_index* ix, const int32_t* query_tokens, int64_
     std::vector<std::pair<Plan, double>> log;
     Plan cur = base;
     double cur_ms = DBL_MAX;
+    constexpr double kMinGain = 0.01;
     int rc = BM25_OK;
     auto trial = [&](const Plan& p) {
         if (rc != BM25_OK)
@@ -114,29 +115,39 @@ extern "C" int bm25_autotune(bm25_index* ix, const int32_t* query_tokens, int64_
             return;
         }
         log.emplace_back(p, ms);
-        if (ms < cur_ms) {
+        // a later candidate must be faster by more than kMinGain: timing
+        // noise then leaves the plan where it is (each step tries the
+        // library's default first)
+        if (ms < cur_ms * (1.0 - kMinGain)) {
             cur_ms = ms;
             cur = p;
         }
     };
+    const Plan def;  // the library's defaults
+    auto default_first = [](std::vector<int32_t> v, int32_t d) {
+        std::stable_partition(v.begin(), v.end(), [d](int32_t x) { return x == d; });
+        return v;
+    };
     // 1. the tile width, every query on the tiled path
-    for (int32_t W : {6144, 7168, 8192, 10240, 12288}) {
+    for (int32_t W : default_first({6144, 7168, 8192, 10240, 12288}, def.tile_docs)) {
         Plan p = base;
         p.accumulator = BM25_ACC_SMEM_TILED;
         p.tile_docs = W;
-        p.threads = 192;
+        p.threads = def.threads;
         trial(p);
     }
     // 1b. the consumer threads per CTA at that width
     const Plan width = cur;
-    for (int32_t th : {128, 256}) {
+    for (int32_t th : {128, 192, 256}) {
+        if (th == def.threads)
+            continue;  // tried in step 1
         Plan p = width;
         p.threads = th;
         trial(p);
     }
     // 2. the dense-path bound with that tile width
     const Plan tiled = cur;
-    for (int32_t dmax : {2048, 4096, 8192, 16384, 32768}) {
+    for (int32_t dmax : default_first({2048, 4096, 8192, 16384, 32768}, def.dense_max)) {
         Plan p = tiled;
         p.accumulator = BM25_ACC_AUTO;
         p.dense_max = dmax;

@@ -153,7 +153,10 @@ def test_autotune_picks_a_plan_and_keeps_results(env):
     best, ms, log = ix.autotune(qt, qo, 10)
     assert ms > 0 and len(log) >= 4
     assert best == ix.get_plan()
-    assert min(m for _, m in log) == ms
+    # a later candidate replaces the best only when more than 1 % faster, so
+    # the chosen time is one of those logged and within 1 % of the fastest
+    assert ms in [m for _, m in log]
+    assert ms <= min(m for _, m in log) / 0.99 + 1e-9
     assert best["accumulator"] in (bm25.ACC_SMEM_TILED, bm25.ACC_AUTO)
     orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.BM25L)
     ids, sc = ix.retrieve(qt, qo, 10)
