@@ -226,6 +226,32 @@ def reference_arm(args):
 
 # ------------------------------------------------------------ GPU arm -----
 
+def plan_key(plan):
+    """A plan dict as the "plan:" line of a traffic file writes it."""
+    return ",".join(str(plan[f]) for f in ("accumulator", "tile_docs", "block_threads",
+                                           "dense_max_postings"))
+
+
+def read_traffic(path, stamp, workload, plan):
+    """DRAM bytes per launch from a profiles/<kernel>_<workload>_traffic.md
+    file ("key: value" lines from one ncu capture), or None.  The figure holds
+    only for the sources it was taken on (build_stamp), its workload and, when
+    the file names one, its plan."""
+    kv = {}
+    try:
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    key, _, val = line.partition(":")
+                    kv[key.strip().strip("`* ")] = val.strip().strip("`* ")
+        if (kv.get("build_stamp") == stamp and kv.get("workload") == workload
+                and kv.get("plan", plan) == plan):
+            return int(kv["traffic_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
 def kernel_bytes(name, ctx):
     """Algorithmic bytes per launch of the kernels a roofline is quoted for."""
     if name == "k_tile_staged":
@@ -413,27 +439,10 @@ def extras(args, line, bm25, corpus, queries, tok, off, qt, qo, ids, sc, dev, pr
             return None
         avg_s = t / c / 1e3
         achieved = b / avg_s / 1e9
-        traffic = None
-        # profiles/<kernel>_<workload>_traffic.md holds "key: value" lines from
-        # one ncu capture; used only while the sources match its build stamp
-        # and the plan timed here is the one captured
-        tr_path = os.path.join(ROOT, "profiles",
-                               f"{name}_{w.name.replace('-', '')}_traffic.md")
-        try:
-            kv = {}
-            with open(tr_path) as f:
-                for line in f:
-                    if ":" in line and not line.startswith("#"):
-                        key, _, val = line.partition(":")
-                        kv[key.strip().strip("`* ")] = val.strip().strip("`* ")
-            from paper_2407_03618_gb300 import build_ext
-            plan_here = ",".join(str(used[f]) for f in ("accumulator", "tile_docs", "block_threads",
-                                                         "dense_max_postings"))
-            if (kv.get("build_stamp") == build_ext._stamp() and kv.get("workload") == w.name
-                    and kv.get("plan", plan_here) == plan_here):
-                traffic = int(kv["traffic_bytes_per_launch"])
-        except (OSError, ValueError, KeyError):
-            pass
+        from paper_2407_03618_gb300 import build_ext
+        traffic = read_traffic(os.path.join(ROOT, "profiles",
+                                            f"{name}_{w.name.replace('-', '')}_traffic.md"),
+                               build_ext._stamp(), w.name, plan_key(used))
         return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                 "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                 "algorithmic_bytes_per_launch": b, "ms_per_launch": t / c,
