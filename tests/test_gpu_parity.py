@@ -219,6 +219,47 @@ def test_edge_cases(torch_dev):
     ix.close()
 
 
+def test_exact_ties_at_the_threshold_across_tiles(torch_dev):
+    """30,011 documents in two classes of identical documents ([0, 1], and
+    [0, 0, 2] for every fifth): every score ties exactly with its whole class,
+    and the classes lie >= 8 % apart.  The top k is then unique — the class
+    order, lowest doc ids first — and must come back exactly, across many doc
+    tiles (a ragged last one) where the running threshold sits on the tied
+    score: the crossing mode (Lucene, BM25+ with its shift) and the list mode
+    with untouched documents ranking (Robertson, negative IDF of term 0)."""
+    n = 30_011
+    toks, offs = [], [0]
+    for i in range(n):
+        toks += [0, 0, 2] if i % 5 == 3 else [0, 1]
+        offs.append(len(toks))
+    c = synth.Corpus(np.array(toks, np.int32), np.array(offs, np.int64), 3)
+    qlist = [[0], [1], [2], [0, 1], [1, 2], [0, 2], [2, 2, 1]]
+    q = synth.Queries(np.array(sum(qlist, []), np.int32),
+                      np.concatenate([[0], np.cumsum([len(x) for x in qlist])]).astype(np.int64))
+    plans = {"tiled W=1024": (2, 1024, 0), "tiled": (2, 0, 0), "dense": (3, 0, 0),
+             "mixed": (1, 0, 20_000)}
+    for variant in ("lucene", "bm25+", "robertson"):
+        ix = _build(torch_dev, c, variant)
+        orc = oracle.build(c.tokens, c.doc_offsets, 3, oracle.VARIANTS[variant], 1.5, 0.75, 0.5)
+        want = []
+        for i in range(q.n_queries):
+            full = oracle.score_all(orc, q.query(i))
+            want.append((np.lexsort((np.arange(n), -full)), full))
+        for name, (acc, w, dmax) in plans.items():
+            ix.set_plan(acc, w, 0, dmax)
+            for k in (1, 10, 100, 1000, 4096):
+                ids, sc = ix.retrieve(_to(torch_dev, q.tokens), _to(torch_dev, q.offsets), k)
+                ix.sync_status()
+                ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+                for i in range(q.n_queries):
+                    order, full = want[i]
+                    where = f"{variant} {name} k={k} q{qlist[i]}"
+                    assert np.array_equal(ids[i], order[:k]), where
+                    np.testing.assert_allclose(sc[i], full[order[:k]], rtol=1e-5, atol=0.0,
+                                               err_msg=where)
+        ix.close()
+
+
 def test_out_of_range_tokens_are_reported(torch_dev):
     from paper_2407_03618_gb300 import bm25
     c = synth.Corpus(np.array([0, 1, 2, 1], np.int32), np.array([0, 2, 4], np.int64), 3)
