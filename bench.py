@@ -232,24 +232,33 @@ def plan_key(plan):
                                            "dense_max_postings"))
 
 
-def read_traffic(path, stamp, workload, plan):
-    """DRAM bytes per launch from a profiles/<kernel>_<workload>_traffic.md
-    file ("key: value" lines from one ncu capture), or None.  The figure holds
-    only for the sources it was taken on (build_stamp), its workload and, when
-    the file names one, its plan."""
+def parse_traffic(text, stamp, workload, plan):
+    """DRAM bytes per launch from the "key: value" lines of a traffic profile
+    (one ncu capture), or None.  The figure holds only for the code it was
+    taken on (code_stamp: build_ext.code_stamp()), its workload and, when the
+    profile names one, its plan."""
     kv = {}
+    for line in text.splitlines():
+        if ":" in line and not line.startswith("#"):
+            key, _, val = line.partition(":")
+            kv[key.strip().strip("`* ")] = val.strip().strip("`* ")
     try:
-        with open(path) as f:
-            for line in f:
-                if ":" in line and not line.startswith("#"):
-                    key, _, val = line.partition(":")
-                    kv[key.strip().strip("`* ")] = val.strip().strip("`* ")
-        if (kv.get("build_stamp") == stamp and kv.get("workload") == workload
+        if (kv.get("code_stamp") == stamp and kv.get("workload") == workload
                 and kv.get("plan", plan) == plan):
             return int(kv["traffic_bytes_per_launch"])
-    except (OSError, ValueError, KeyError):
+    except (ValueError, KeyError):
         pass
     return None
+
+
+def read_traffic(path, stamp, workload, plan):
+    """parse_traffic of the file profiles/<kernel>_<workload>_traffic.md;
+    None when there is no such file."""
+    try:
+        with open(path) as f:
+            return parse_traffic(f.read(), stamp, workload, plan)
+    except OSError:
+        return None
 
 
 def kernel_bytes(name, ctx):
@@ -442,7 +451,7 @@ def extras(args, line, bm25, corpus, queries, tok, off, qt, qo, ids, sc, dev, pr
         from paper_2407_03618_gb300 import build_ext
         traffic = read_traffic(os.path.join(ROOT, "profiles",
                                             f"{name}_{w.name.replace('-', '')}_traffic.md"),
-                               build_ext._stamp(), w.name, plan_key(used))
+                               build_ext.code_stamp(), w.name, plan_key(used))
         return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                 "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                 "algorithmic_bytes_per_launch": b, "ms_per_launch": t / c,

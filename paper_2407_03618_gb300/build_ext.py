@@ -42,6 +42,51 @@ def _stamp() -> str:
     return h.hexdigest()
 
 
+def strip_c_comments(src: str) -> str:
+    """C/C++/CUDA source with its comments removed and every run of whitespace
+    collapsed to one space; string and character literals are kept."""
+    out = []
+    i, n = 0, len(src)
+    while i < n:
+        c = src[i]
+        if c == "/" and src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+            out.append(" ")
+        elif c == "/" and src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
+def code_stamp(csrc: str = CSRC, include: str = INCLUDE) -> str:
+    """Hash of what the compiled code depends on: the arch, the flags other
+    than include paths, the translation units, and every source and header
+    with comments and whitespace removed.  Independent of where the
+    repository lives and of comment edits; counters a profile took stay valid
+    while it is unchanged."""
+    h = hashlib.sha256()
+    flags = [f for f in NVCC_FLAGS if not f.startswith("-I")]
+    h.update(" ".join(ARCH + flags + SOURCES).encode())
+    for d in (csrc, include):
+        for name in sorted(os.listdir(d)):
+            if name.endswith((".cu", ".cuh", ".h")):
+                with open(os.path.join(d, name), encoding="utf-8") as f:
+                    h.update(name.encode() + b"\0")
+                    h.update(strip_c_comments(f.read()).encode() + b"\0")
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     stamp = _stamp()
     stamp_path = os.path.join(OBJ_DIR, "stamp")

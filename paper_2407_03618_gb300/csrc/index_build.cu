@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kSortThreads, 2)
     __shared__ uint32_t wcnt[kSortWarps][kMaxBuckets];  // per-warp counts, then tile positions
     __shared__ uint32_t gofs[kMaxBuckets];  // global position - position in the sorted tile
     __shared__ uint32_t scan_buf[33];
-    // kSortTile sorted keys, kSortTile sorted doc ids, kSortTile doc ids in tile order
+    // kSortTile sorted keys, then kSortTile sorted doc ids
     extern __shared__ uint32_t sorted_tile[];
     uint32_t* sk = sorted_tile;
     uint32_t* sv = sorted_tile + kSortTile;

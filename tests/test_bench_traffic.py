@@ -1,14 +1,15 @@
 """bench.py's roofline `traffic`: read from a profile's "key: value" lines only
-for the sources, workload and plan the counters were taken on."""
+for the code, workload and plan the counters were taken on; the code stamp
+ignores comments, whitespace and where the repository lives."""
+import os
+
 import bench
+from paper_2407_03618_gb300 import build_ext
 
 
-def _write(tmp_path, **kv):
-    p = tmp_path / "k_traffic.md"
+def _profile(**kv):
     body = "# k — DRAM traffic\n\nCommand: ncu ... (a prose line with a colon)\n\n"
-    body += "".join(f"{k}: {v}\n" for k, v in kv.items())
-    p.write_text(body)
-    return str(p)
+    return body + "".join(f"{k}: {v}\n" for k, v in kv.items())
 
 
 def test_plan_key_order():
@@ -17,40 +18,61 @@ def test_plan_key_order():
     assert bench.plan_key(plan) == "1,10240,192,4096"
 
 
-def test_matching_stamp_workload_and_plan(tmp_path):
-    p = _write(tmp_path, build_stamp="abc", workload="zipf-1m", plan="1,10240,192,4096",
-               traffic_bytes_per_launch=300100000)
-    assert bench.read_traffic(p, "abc", "zipf-1m", "1,10240,192,4096") == 300100000
+def test_matching_stamp_workload_and_plan():
+    t = _profile(code_stamp="abc", workload="zipf-1m", plan="1,10240,192,4096",
+                 traffic_bytes_per_launch=300100000)
+    assert bench.parse_traffic(t, "abc", "zipf-1m", "1,10240,192,4096") == 300100000
 
 
-def test_any_mismatch_gives_none(tmp_path):
-    p = _write(tmp_path, build_stamp="abc", workload="zipf-1m", plan="1,10240,192,4096",
-               traffic_bytes_per_launch=300100000)
-    assert bench.read_traffic(p, "abd", "zipf-1m", "1,10240,192,4096") is None
-    assert bench.read_traffic(p, "abc", "tiny-2k", "1,10240,192,4096") is None
-    assert bench.read_traffic(p, "abc", "zipf-1m", "1,10240,192,2048") is None
+def test_any_mismatch_gives_none():
+    t = _profile(code_stamp="abc", workload="zipf-1m", plan="1,10240,192,4096",
+                 traffic_bytes_per_launch=300100000)
+    assert bench.parse_traffic(t, "abd", "zipf-1m", "1,10240,192,4096") is None
+    assert bench.parse_traffic(t, "abc", "tiny-2k", "1,10240,192,4096") is None
+    assert bench.parse_traffic(t, "abc", "zipf-1m", "1,10240,192,2048") is None
 
 
-def test_file_without_a_plan_holds_for_any_plan(tmp_path):
-    p = _write(tmp_path, build_stamp="abc", workload="zipf-1m", traffic_bytes_per_launch=7)
-    assert bench.read_traffic(p, "abc", "zipf-1m", "2,7168,256,0") == 7
+def test_profile_without_a_plan_holds_for_any_plan():
+    t = _profile(code_stamp="abc", workload="zipf-1m", traffic_bytes_per_launch=7)
+    assert bench.parse_traffic(t, "abc", "zipf-1m", "2,7168,256,0") == 7
 
 
-def test_missing_or_malformed_gives_none(tmp_path):
-    assert bench.read_traffic(str(tmp_path / "absent.md"), "abc", "zipf-1m", "x") is None
-    p = _write(tmp_path, build_stamp="abc", workload="zipf-1m", traffic_bytes_per_launch="n/a")
-    assert bench.read_traffic(p, "abc", "zipf-1m", "x") is None
+def test_missing_or_malformed_gives_none():
+    assert bench.read_traffic(os.path.join(bench.ROOT, "profiles", "absent.md"), "abc",
+                              "zipf-1m", "x") is None
+    t = _profile(code_stamp="abc", workload="zipf-1m", traffic_bytes_per_launch="n/a")
+    assert bench.parse_traffic(t, "abc", "zipf-1m", "x") is None
 
 
-def test_committed_profile_parses():
-    # the committed file names a stamp, the bench workload and a plan
-    import os
+def test_committed_profile_matches_the_code():
     path = os.path.join(bench.ROOT, "profiles", "k_tile_staged_zipf1m_traffic.md")
+    text = open(path).read()
+    keys = ("code_stamp", "plan", "workload", "traffic_bytes_per_launch")
     kv = {}
-    for line in open(path):
-        if ":" in line and not line.startswith("#"):
-            k, _, v = line.partition(":")
-            kv[k.strip()] = v.strip()
-    assert kv["workload"] == "zipf-1m" and len(kv["build_stamp"]) == 64
-    assert bench.read_traffic(path, kv["build_stamp"], "zipf-1m", kv["plan"]) == \
+    for line in text.splitlines():
+        key, sep, val = line.partition(":")
+        if sep and key in keys:
+            kv[key] = val.strip()
+    assert set(kv) == set(keys)
+    assert kv["workload"] == "zipf-1m"
+    assert kv["code_stamp"] == build_ext.code_stamp()
+    assert bench.read_traffic(path, build_ext.code_stamp(), "zipf-1m", kv["plan"]) == \
         int(kv["traffic_bytes_per_launch"])
+
+
+def test_strip_c_comments():
+    src = ('int a = 1; // c\'mon "x"\n'
+           'const char* p = "// not a comment"; /* block\n comment */ char q = \'\\\'\';\n'
+           "char r = '\"';   int  b=2;\n")
+    assert build_ext.strip_c_comments(src) == \
+        "int a = 1; const char* p = \"// not a comment\"; char q = '\\''; char r = '\"'; int b=2;"
+    assert build_ext.strip_c_comments("x /* a */ y\n\n  // b\nz") == "x y z"
+
+
+def test_code_stamp_ignores_include_paths(monkeypatch):
+    s0 = build_ext.code_stamp()
+    flags = [f if not f.startswith("-I") else "-I/elsewhere" + f[2:] for f in build_ext.NVCC_FLAGS]
+    monkeypatch.setattr(build_ext, "NVCC_FLAGS", flags)
+    assert build_ext.code_stamp() == s0
+    monkeypatch.setattr(build_ext, "NVCC_FLAGS", flags + ["-DX=1"])
+    assert build_ext.code_stamp() != s0
