@@ -2,6 +2,7 @@
 include/bm25.h declares, and rejects bad arguments on the host before any
 CUDA call."""
 import ctypes
+import os
 
 import pytest
 
@@ -54,3 +55,15 @@ def test_null_handles_are_rejected(lib):
     lib.bm25_workspace_free(None)
     assert lib.bm25_index_set_plan(None, None) == -1
     assert lib.bm25_index_get_plan(None, None) == -1
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    # no fallback of any kind: without the built library the binding raises
+    monkeypatch.setattr(bm25, "_lib", None)
+    missing = os.path.join(build_ext.PKG, "_missing", "libbm25gpu.so")
+    assert not os.path.exists(missing)
+    with pytest.raises(RuntimeError, match="not built"):
+        bm25.load(missing)
+    monkeypatch.setattr(build_ext, "LIB_PATH", missing)
+    with pytest.raises(RuntimeError, match="not built"):
+        bm25.load()
