@@ -525,9 +525,9 @@ size_t staged_smem_bytes(int32_t W)
 // seg (packed): for query token m and tile boundary j, the first slot of the
 // token's packed column at or past document j * W (j = n_tiles: the column
 // end), from k_seg_bounds<true>.
-// Four CTAs per SM at the default tile width (shared memory allows it; the
-// register bound makes it so: 67 per thread at 6 consumer warps, the
-// default, 56 at 8).
+// Up to four CTAs per SM: the register bound allows four (67 registers per
+// thread at 6 consumer warps, the default, 56 at 8); shared memory allows
+// four up to W = 7168 and three at the default W = 10240 (73 KB).
 template <int CW>
 __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
     k_tile_staged(int64_t n_docs, const uint2* __restrict__ posts, const uint32_t* __restrict__ seg,
