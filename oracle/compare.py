@@ -2,18 +2,26 @@
 
 TEST INFRASTRUCTURE ONLY (used by tests/, smoke() and bench.py's oracle leg).
 
-Tolerance: |s - B(Q,D)| <= rtol * max(|B(Q,D)|, sum_i |S(q_i, D)|), rtol 1e-5.
+The rule (Sec. 2 "Top-k selection": the k highest-scoring documents, ties
+broken by the lower doc id; tolerance 1e-5 relative):
+
+  tol(D) = rtol * max(|B(Q,D)|, sum_i |S(q_i, D)|)          rtol = 1e-5
+
 The second term keeps terms of opposite sign (Robertson's negative IDF) from
-making a relative bound meaningless.  Ids must equal the oracle's ranking
-except where oracle scores are within that tolerance of each other, so only
-what is unique is compared exactly:
-  * every returned document's oracle score is at least the k-th best oracle
-    score minus the tolerance;
-  * every document whose oracle score beats the k-th by more than the
-    tolerance is returned;
-  * the returned list holds no duplicate and is ordered by its own scores
-    (descending, then doc id ascending);
-  * slots past min(k, N) hold id -1 and score -inf.
+making a relative bound meaningless.  With k' = min(k, N), `order` the
+oracle's ranking (score descending, doc id ascending) and B_k the oracle
+score of order[k'-1] (the k-th best), tol_k = tol(order[k'-1]):
+
+  * every returned score is within tol(D) of the oracle's B(Q,D);
+  * ids may differ from the oracle's top k' only among documents whose
+    oracle score lies within tol_k of B_k: every oracle top-k' document
+    scoring more than B_k + tol_k is returned, and every returned document
+    scores at least B_k - tol_k;
+  * the returned ids are in [0, N) and distinct, and the row is ordered by
+    its own scores (descending; equal scores by ascending doc id);
+  * slots past k' hold id -1 and score -inf.
+
+check_topk raises AssertionError with a message naming the first violation.
 """
 from __future__ import annotations
 
@@ -22,34 +30,47 @@ import numpy as np
 RTOL = 1e-5
 
 
+def tolerance(full, abs_full, rtol: float = RTOL):
+    """Per-document tolerance rtol * max(|B|, sum |S|)."""
+    return rtol * np.maximum(np.abs(full), abs_full)
+
+
 def check_topk(ids, scores, full, abs_full, k: int, rtol: float = RTOL, where: str = ""):
     ids = np.asarray(ids)
     scores = np.asarray(scores, dtype=np.float64)
+    full = np.asarray(full, dtype=np.float64)
+    abs_full = np.asarray(abs_full, dtype=np.float64)
     n = full.shape[0]
     kp = min(k, n)
-    assert ids.shape[0] == k, f"{where}: expected {k} slots"
+    assert ids.shape[0] == k and scores.shape[0] == k, f"{where}: expected {k} slots"
     if kp < k:
-        assert (ids[kp:] == -1).all(), f"{where}: padding ids must be -1"
-        assert np.isneginf(scores[kp:]).all(), f"{where}: padding scores must be -inf"
+        assert (ids[kp:] == -1).all(), f"{where}: padding ids must be -1, got {ids[kp:][:5]}"
+        assert np.isneginf(scores[kp:]).all(), \
+            f"{where}: padding scores must be -inf, got {scores[kp:][:5]}"
     got = ids[:kp].astype(np.int64)
     sc = scores[:kp]
-    assert ((got >= 0) & (got < n)).all(), f"{where}: id out of range {got}"
+    assert ((got >= 0) & (got < n)).all(), f"{where}: id out of range {got[(got < 0) | (got >= n)][:5]}"
     assert np.unique(got).shape[0] == kp, f"{where}: duplicate ids {got}"
-    tol_doc = rtol * np.maximum(np.abs(full), abs_full)
+    assert np.isfinite(sc).all(), f"{where}: non-finite score among the first {kp} slots"
+    tol = tolerance(full, abs_full, rtol)
     err = np.abs(sc - full[got])
-    bad = err > tol_doc[got] + 1e-300
+    bad = err > tol[got]
     assert not bad.any(), (f"{where}: score mismatch at ranks {np.nonzero(bad)[0][:5]}: "
                            f"got {sc[bad][:5]} want {full[got][bad][:5]}")
     order = np.lexsort((np.arange(n), -full))
-    kth = full[order[kp - 1]]
-    tol_k = rtol * max(abs(kth), float(abs_full[order[kp - 1]]))
-    lo = full[got] < kth - 2 * tol_k - tol_doc[got]
-    assert not lo.any(), f"{where}: returned ids {got[lo][:5]} are not in the top {kp}"
-    must = order[:kp][full[order[:kp]] > kth + 2 * tol_k + tol_doc[order[:kp]]]
+    kth_doc = order[kp - 1]
+    kth = full[kth_doc]
+    tol_k = tol[kth_doc]
+    lo = full[got] < kth - tol_k
+    assert not lo.any(), (f"{where}: returned ids {got[lo][:5]} (oracle {full[got][lo][:5]}) "
+                          f"are below the k-th score {kth} by more than {tol_k}")
+    top = order[:kp]
+    must = top[full[top] > kth + tol_k]
     missing = np.setdiff1d(must, got)
-    assert missing.shape[0] == 0, f"{where}: top ids {missing[:5]} missing"
-    # own order: scores non-increasing; equal scores by ascending id
+    assert missing.shape[0] == 0, (f"{where}: top ids {missing[:5]} "
+                                   f"(oracle {full[missing][:5]}) missing")
+    # the row's own order: scores non-increasing, equal scores by ascending id
     ds = np.diff(sc)
-    assert (ds <= 0).all(), f"{where}: scores not sorted"
+    assert (ds <= 0).all(), f"{where}: scores not sorted descending at {np.nonzero(ds > 0)[0][:5]}"
     eq = ds == 0
     assert (np.diff(got)[eq] > 0).all(), f"{where}: equal scores not ordered by doc id"
