@@ -98,6 +98,9 @@ typedef struct bm25_plan {
                                    256 or 512 (default 192; one producer warp is added) */
     int32_t dense_max_postings; /* dense-path bound for AUTO / L2_DENSE, in [0, 2^22]
                                    (default 4096) */
+    int32_t stage_entries;      /* packed postings per shared-memory staging buffer of the
+                                   tiled kernel: a multiple of 64 in [128, 8192] (default 512) */
+    int32_t stages;             /* staging buffers in its ring, in [2, 8] (default 2) */
 } bm25_plan;
 
 /* ------------------------------------------------------------------ index */
@@ -338,6 +341,8 @@ typedef struct bm25_server_stats {
     int64_t batches, batched_queries;
     double p50_us, p99_us, max_us;  /* submit-to-result latency of completed requests */
     int64_t bytes_held;         /* device scratch the server holds now */
+    double span_us;             /* first submit to last completion (the results ready on the
+                                   host), so that completed / span is the served rate */
 } bm25_server_stats;
 
 /* Starts the worker thread.  indexes[n_indexes] live on the current device;
@@ -388,6 +393,25 @@ int bm25_profile_begin(void);
 int bm25_profile_end(void);
 int bm25_profile_count(void);
 int bm25_profile_get(int i, char* name, int name_cap, int64_t* launches, double* total_ms);
+
+/* ------------------------------------------------------------ test hooks */
+
+/* Failure injection for tests of the error paths (the paper has no
+ * counterpart).  Both settings are process-wide and apply to every device.
+ *
+ * bm25_debug_set_handshake_polls: the number of polls after which a
+ * producer/consumer wait of the doc-tiled retrieval kernel gives up
+ * (default 2^22; polls < 0 restores it; 0 makes every such wait give up at
+ * once).  A kernel that gives up records BM25_E_TIMEOUT in the index's
+ * status word (read and cleared by bm25_sync_status), leaves its rows
+ * undefined, waits for its own copies in flight and returns; the index and
+ * the workspace stay usable.
+ *
+ * bm25_debug_fail_allocs: the next n device allocations the library makes
+ * (index arrays, build scratch, workspace growth, host-path staging) fail
+ * with BM25_E_OOM as if the device were out of memory (n <= 0 cancels). */
+int bm25_debug_set_handshake_polls(int32_t polls);
+int bm25_debug_fail_allocs(int32_t n);
 
 #ifdef __cplusplus
 }

@@ -27,12 +27,14 @@ MAX_K = 4096
 class Plan(ctypes.Structure):
     """bm25_plan: how retrieval runs (zero fields = library defaults)."""
     _fields_ = [("accumulator", ctypes.c_int32), ("tile_docs", ctypes.c_int32),
-                ("block_threads", ctypes.c_int32), ("dense_max_postings", ctypes.c_int32)]
+                ("block_threads", ctypes.c_int32), ("dense_max_postings", ctypes.c_int32),
+                ("stage_entries", ctypes.c_int32), ("stages", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {"accumulator": self.accumulator, "tile_docs": self.tile_docs,
                 "block_threads": self.block_threads,
-                "dense_max_postings": self.dense_max_postings}
+                "dense_max_postings": self.dense_max_postings,
+                "stage_entries": self.stage_entries, "stages": self.stages}
 
 
 class ServerConfig(ctypes.Structure):
@@ -46,7 +48,8 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("batched_queries", ctypes.c_int64),
                 ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
-                ("max_us", ctypes.c_double), ("bytes_held", ctypes.c_int64)]
+                ("max_us", ctypes.c_double), ("bytes_held", ctypes.c_int64),
+                ("span_us", ctypes.c_double)]
 
 
 class BM25Error(RuntimeError):
@@ -112,6 +115,8 @@ def load(path: str | None = None):
         "bm25_profile_end": (cint, []),
         "bm25_profile_count": (cint, []),
         "bm25_profile_get": (cint, [cint, ctypes.c_char_p, cint, P, P]),
+        "bm25_debug_set_handshake_polls": (cint, [i32]),
+        "bm25_debug_fail_allocs": (cint, [i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -124,6 +129,16 @@ def load(path: str | None = None):
 def _check(rc: int):
     if rc != 0:
         raise BM25Error(rc, load().bm25_last_error().decode())
+
+
+def debug_set_handshake_polls(polls: int):
+    """Test hook: polls after which a wait of the tiled kernel gives up (< 0: default)."""
+    _check(load().bm25_debug_set_handshake_polls(polls))
+
+
+def debug_fail_allocs(n: int):
+    """Test hook: the next n device allocations of the library fail with BM25_E_OOM."""
+    _check(load().bm25_debug_fail_allocs(n))
 
 
 def release_cached():
@@ -284,8 +299,8 @@ class Index:
         return out
 
     def set_plan(self, accumulator: int = ACC_UNSET, tile_docs: int = 0, block_threads: int = 0,
-                 dense_max_postings: int = 0):
-        p = Plan(accumulator, tile_docs, block_threads, dense_max_postings)
+                 dense_max_postings: int = 0, stage_entries: int = 0, stages: int = 0):
+        p = Plan(accumulator, tile_docs, block_threads, dense_max_postings, stage_entries, stages)
         _check(load().bm25_index_set_plan(self.handle, ctypes.byref(p)))
 
     def autotune(self, q_tokens, q_offsets, k: int, stream=None):

@@ -31,6 +31,23 @@ int set_error(int code, const char* fmt, ...)
 
 void clear_error() { g_err[0] = 0; }
 
+namespace {
+std::atomic<int> g_handshake_polls{kHandshakePolls};
+std::atomic<int> g_fail_allocs{0};
+}  // namespace
+
+int handshake_polls() { return g_handshake_polls.load(std::memory_order_relaxed); }
+
+bool forced_alloc_failure()
+{
+    int n = g_fail_allocs.load(std::memory_order_relaxed);
+    while (n > 0) {
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1, std::memory_order_relaxed))
+            return true;
+    }
+    return false;
+}
+
 int device_info(DeviceInfo* out)
 {
     int dev = 0;
@@ -168,6 +185,17 @@ int merge_plan(const bm25_plan* in, const Plan& base, Plan* out)
             in->block_threads != 256 && in->block_threads != 512)
             return set_error(BM25_E_INVALID, "block_threads %d must be 128, 192, 256 or 512",
                              in->block_threads);
+        if (in->stage_entries != 0 &&
+            (in->stage_entries < 128 || in->stage_entries > 8192 || in->stage_entries % 64))
+            return set_error(BM25_E_INVALID,
+                             "stage_entries %d must be a multiple of 64 in [128, 8192]",
+                             in->stage_entries);
+        if (in->stages != 0 && (in->stages < 2 || in->stages > 8))
+            return set_error(BM25_E_INVALID, "stages %d must be in [2, 8]", in->stages);
+        if (in->stage_entries)
+            p.stage_entries = in->stage_entries;
+        if (in->stages)
+            p.stages = in->stages;
         if (in->accumulator)
             p.accumulator = in->accumulator;
         if (in->tile_docs)
@@ -525,6 +553,9 @@ int bm25_retrieve_host(const bm25_index* ix, const int32_t* query_tokens,
             cudaFree(*p);
         *p = nullptr;
         *cap = 0;
+        if (forced_alloc_failure())
+            return set_error(BM25_E_OOM, "device allocation of %zu bytes failed (forced by "
+                             "bm25_debug_fail_allocs)", bytes);
         BM25_CUDA_TRY(cudaMalloc(p, bytes ? bytes : 1));
         *cap = bytes;
         return BM25_OK;
@@ -553,6 +584,20 @@ int bm25_retrieve_host(const bm25_index* ix, const int32_t* query_tokens,
     return BM25_OK;
 }
 
+int bm25_debug_set_handshake_polls(int32_t polls)
+{
+    clear_error();
+    g_handshake_polls.store(polls < 0 ? kHandshakePolls : polls, std::memory_order_relaxed);
+    return BM25_OK;
+}
+
+int bm25_debug_fail_allocs(int32_t n)
+{
+    clear_error();
+    g_fail_allocs.store(n > 0 ? n : 0, std::memory_order_relaxed);
+    return BM25_OK;
+}
+
 int bm25_index_set_plan(bm25_index* ix, const bm25_plan* plan)
 {
     clear_error();
@@ -575,6 +620,8 @@ int bm25_index_get_plan(const bm25_index* ix, bm25_plan* plan)
     plan->tile_docs = p.tile_docs;
     plan->block_threads = p.threads;
     plan->dense_max_postings = p.dense_max;
+    plan->stage_entries = p.stage_entries;
+    plan->stages = p.stages;
     return BM25_OK;
 }
 

@@ -581,6 +581,11 @@ template <typename T>
 int pool_alloc(T** p, int64_t count, cudaMemPool_t pool, cudaStream_t s)
 {
     size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+    if (forced_alloc_failure()) {
+        *p = nullptr;
+        return set_error(BM25_E_OOM, "device allocation of %zu bytes failed (forced by "
+                         "bm25_debug_fail_allocs)", bytes);
+    }
     cudaError_t e = cudaMallocFromPoolAsync((void**)p, bytes, pool, s);
     if (e != cudaSuccess) {
         *p = nullptr;

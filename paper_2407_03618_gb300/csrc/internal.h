@@ -34,6 +34,14 @@ void clear_error();
             return r_;          \
     } while (0)
 
+// Test hooks (bm25_debug_*).  handshake_polls(): the poll limit of the tile
+// kernel's producer/consumer waits (kHandshakePolls unless a test lowered
+// it).  forced_alloc_failure(): true when a test asked for this device
+// allocation to fail (consumes one of the failures it asked for).
+constexpr int kHandshakePolls = 1 << 22;
+int handshake_polls();
+bool forced_alloc_failure();
+
 // Kernel launch accounting (bm25_launch_count).
 extern std::atomic<int64_t> g_launches;
 inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -77,6 +85,8 @@ struct Plan {
     int32_t tile_docs = 10240;
     int32_t threads = 192;
     int32_t dense_max = 4096;   // postings bound of the dense path (AUTO, L2_DENSE)
+    int32_t stage_entries = 512; // packed postings per staging buffer of the tiled kernel
+    int32_t stages = 2;          // staging buffers in its ring
 };
 // Fills zero fields of `in` from `base`; BM25_E_INVALID (nothing changed) if
 // a field is out of range.

@@ -341,7 +341,7 @@ __device__ __forceinline__ u64 warp_sort_desc(u64 key)
 // mbarrier).  Segments start on 16-byte boundaries, so each copy is
 // widened to whole pairs: the extra slots hold postings of the same column
 // outside the tile, or padding, and are dropped by the doc-range test.
-// Staging buffers form a ring of kNumStages; an item larger than one buffer
+// Staging buffers form a ring of plan.stages; an item larger than one buffer
 // spans several.  The consumer warps (named barrier 1):
 //   scatter  every staged posting in the tile is added to the tile's FP32
 //            accumulator in shared memory (Sec. 2 "Assigning Query Scores":
@@ -360,10 +360,11 @@ __device__ __forceinline__ u64 warp_sort_desc(u64 key)
 // untouched documents when fewer than k' touched ones score above 0,
 // selects over both, and resets through the list.  Candidates beyond
 // kCandCap in a claim are put back and selected by a scan of the tile.
-constexpr int kStageEntries = 512;   // packed postings per staging buffer (4 KB)
-constexpr int kNumStages = 2;
+constexpr int kMaxStages = 8;        // staging buffers in the ring at most
 constexpr int kCandCap = 256;        // candidate keys an item collects in the common case
-constexpr int kWaitPolls = 1 << 22;  // mbarrier polls before a wait gives up
+constexpr uint32_t kTouchCap = 2048; // touched-list entries kept (an item touching more
+                                     // documents walks its whole tile instead)
+constexpr int kWaitPolls = kHandshakePolls;  // mbarrier polls before a copy wait gives up
 
 
 constexpr int32_t kModeList = 0;   // first touches listed, claimed after the scatter
@@ -378,9 +379,9 @@ struct __align__(16) StageHdr {
 };
 
 struct StagedFront {
-    unsigned long long full[kNumStages];   // producer -> consumers (bytes landed)
-    unsigned long long empty[kNumStages];  // consumers -> producer (buffer free)
-    StageHdr hdr[kNumStages];
+    unsigned long long full[kMaxStages];   // producer -> consumers (bytes landed)
+    unsigned long long empty[kMaxStages];  // consumers -> producer (buffer free)
+    StageHdr hdr[kMaxStages];
     uint32_t lc[2], ovf[2];                // candidate count / overflow, per item parity
     uint32_t tl_count[2];                  // touched-list length, per item parity
     uint32_t abort_flag;
@@ -438,17 +439,29 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
         : "memory");
 }
 
-// Warp-uniform bounded wait for the phase of `bar` with the given parity.
-// Gives up (false) after kWaitPolls polls or once another warp has given up.
+// Warp-uniform bounded wait for the phase of `bar` with the given parity (a
+// producer/consumer handshake).  Gives up (false) after `polls` polls or once
+// another warp has given up.
 __device__ __forceinline__ bool warp_wait(unsigned long long* bar, uint32_t parity,
-                                          const volatile uint32_t* abort_flag)
+                                          const volatile uint32_t* abort_flag, int polls)
 {
-    for (int i = 0; i < kWaitPolls; i++) {
+    for (int i = 0; i < polls; i++) {
         if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity)))
             return true;
-        if (*abort_flag)
+        if (__any_sync(0xffffffffu, *abort_flag != 0u))
             return false;
     }
+    return false;
+}
+
+// Warp-uniform wait for the bulk copies of one fill to land, bounded by
+// kWaitPolls whatever the other warps do: a copy completes in bounded time,
+// and a CTA must not exit while one still writes its shared memory.
+__device__ __forceinline__ bool warp_drain(unsigned long long* bar, uint32_t parity)
+{
+    for (int i = 0; i < kWaitPolls; i++)
+        if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity)))
+            return true;
     return false;
 }
 
@@ -456,6 +469,23 @@ template <int NT>
 __device__ __forceinline__ void consumer_sync()
 {
     asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
+
+// consumer_sync that also returns, to every consumer thread, whether any of
+// them passed v = true (barrier reduction).
+template <int NT>
+__device__ __forceinline__ bool consumer_sync_any(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, 1, %2, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(NT)
+        : "memory");
+    return r != 0u;
 }
 
 // Exclusive scan across the NT consumer threads (see block_exclusive_sum).
@@ -516,10 +546,13 @@ __device__ uint32_t consumer_first_untouched(const float* acc, int32_t wd, uint3
     return carry < k ? carry : k;
 }
 
-size_t staged_smem_bytes(int32_t W)
+// Shared memory of k_tile_staged: the front, W accumulators, the candidate
+// list, `stages` staging buffers of `entries` packed postings, the touched
+// list (tl_cap 16-bit entries, rounded to 16 bytes).
+size_t staged_smem_bytes(int32_t W, int stages, int entries, uint32_t tl_cap)
 {
-    return kStagedFront + (size_t)W * (sizeof(float) + sizeof(uint16_t)) +
-           (size_t)kCandCap * sizeof(u64) + (size_t)kNumStages * kStageEntries * sizeof(uint2);
+    return kStagedFront + (size_t)W * sizeof(float) + (size_t)kCandCap * sizeof(u64) +
+           (size_t)stages * entries * sizeof(uint2) + ((size_t)tl_cap * sizeof(uint16_t) + 15) / 16 * 16;
 }
 
 // seg (packed): for query token m and tile boundary j, the first slot of the
@@ -534,7 +567,8 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
                   int32_t W, int32_t n_tiles, int32_t kstride, const int4* __restrict__ lrec,
                   const uint32_t* __restrict__ lpost, const uint32_t* __restrict__ ctr,
                   uint32_t* __restrict__ thresh, uint32_t* __restrict__ tcount,
-                  u64* __restrict__ cand, int* __restrict__ status)
+                  u64* __restrict__ cand, int* __restrict__ status, int wait_polls,
+                  int n_stages, int stage_entries, uint32_t tl_cap)
 {
     constexpr int NT = CW * 32;  // consumer threads
     constexpr int OW = CW - 1;   // the output warp (the fewest postings per item)
@@ -543,7 +577,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
     float* acc = reinterpret_cast<float*>(smem + kStagedFront);
     u64* clist = reinterpret_cast<u64*>(acc + W);
     uint2* stage = reinterpret_cast<uint2*>(clist + kCandCap);
-    uint16_t* tl = reinterpret_cast<uint16_t*>(stage + (size_t)kNumStages * kStageEntries);
+    uint16_t* tl = reinterpret_cast<uint16_t*>(stage + (size_t)n_stages * stage_entries);
     SelectState& st = sh.st;
 
     const int32_t nq = (int32_t)ctr[0];
@@ -555,7 +589,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
     for (int i = tid; i < W; i += blockDim.x)
         acc[i] = neg0;
     if (tid == 0) {
-        for (int s = 0; s < kNumStages; s++) {
+        for (int s = 0; s < n_stages; s++) {
             mbar_init(&sh.full[s], 1);
             mbar_init(&sh.empty[s], CW);
         }
@@ -651,20 +685,24 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
                 const bool last_chunk = (int64_t)mb + 64 >= (int64_t)m1;
                 if (total == 0u && !last_chunk)
                     continue;
-                const uint32_t nst = total == 0u ? 1u : (total + kStageEntries - 1) / kStageEntries;
+                const uint32_t se = (uint32_t)stage_entries;
+                const uint32_t nst = total == 0u ? 1u : (total + se - 1) / se;
                 for (uint32_t k = 0; k < nst; k++) {
-                    const uint32_t e0 = k * kStageEntries;
-                    const uint32_t e1 = min(total, e0 + (uint32_t)kStageEntries);
-                    if (!aborted && !warp_wait(&sh.empty[s], (round & 1u) ^ 1u, abort_flag)) {
+                    const uint32_t e0 = k * se;
+                    const uint32_t e1 = min(total, e0 + se);
+                    // After giving up, nothing more is staged: a buffer whose
+                    // consumers gave up may still be receiving its copies.
+                    if (!warp_wait(&sh.empty[s], (round & 1u) ^ 1u, abort_flag, wait_polls)) {
                         aborted = true;
                         if (lane == 0) {
                             set_status(status, BM25_E_TIMEOUT);
-                            sh.abort_flag = 1;
+                            *(volatile uint32_t*)&sh.abort_flag = 1u;
                         }
+                        break;
                     }
                     if (lane == 0) {
                         StageHdr& hd = sh.hdr[s];
-                        hd.n = aborted ? 0 : (int32_t)(e1 - e0);
+                        hd.n = (int32_t)(e1 - e0);
                         hd.last = (last_chunk && k + 1 == nst) ? 1 : 0;
                         // a sum can cross the threshold only once when it only grows
                         hd.mode = (tau0 > kZeroKey && !(rec0.w & kNegScores)) ? kModeCross
@@ -674,29 +712,28 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
                         hd.kp = (uint32_t)(rec0.w & kKpMask);
                         hd.post = post0;
                         hd.tau = tau0;
-                        mbar_arrive_expect_tx(&sh.full[s],
-                                              aborted ? 0u : (e1 - e0) * (uint32_t)sizeof(uint2));
+                        mbar_arrive_expect_tx(&sh.full[s], (e1 - e0) * (uint32_t)sizeof(uint2));
                     }
                     __syncwarp();
-                    if (!aborted) {
 #pragma unroll
-                        for (int h = 0; h < 2; h++) {
-                            const uint32_t lo_e = max(off[h], e0);
-                            const uint32_t hi_e = min(off[h] + n[h], e1);
-                            if (lo_e < hi_e)
-                                bulk_copy_g2s(stage + (size_t)s * kStageEntries + (lo_e - e0),
-                                              posts + a[h] + (lo_e - off[h]),
-                                              (hi_e - lo_e) * (uint32_t)sizeof(uint2), &sh.full[s]);
-                        }
+                    for (int h = 0; h < 2; h++) {
+                        const uint32_t lo_e = max(off[h], e0);
+                        const uint32_t hi_e = min(off[h] + n[h], e1);
+                        if (lo_e < hi_e)
+                            bulk_copy_g2s(stage + (size_t)s * stage_entries + (lo_e - e0),
+                                          posts + a[h] + (lo_e - off[h]),
+                                          (hi_e - lo_e) * (uint32_t)sizeof(uint2), &sh.full[s]);
                     }
-                    if (++s == kNumStages) {
+                    if (++s == n_stages) {
                         s = 0;
                         round++;
                     }
                 }
-                if (last_chunk)
+                if (last_chunk || aborted)
                     break;
             }
+            if (aborted)
+                break;
             // shift the pipeline
             rec0 = rec1;
             rec1 = rec2;
@@ -712,16 +749,18 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
             q1 = q2;
             advance(t2, q2);
         }
-        // the copies of the last fills have landed before the warp leaves
-        for (int k = 0; k < kNumStages; k++) {
+        // The copies of the last fill of every stage have landed before the
+        // warp leaves, also after giving up (an earlier fill of a stage
+        // completed before its buffer was released for the next one).
+        for (int k = 0; k < n_stages; k++) {
             if (s == 0) {
-                s = kNumStages;
+                s = n_stages;
                 if (round == 0)
                     break;
                 round--;
             }
             s--;
-            warp_wait(&sh.full[s], round & 1u, abort_flag);
+            warp_drain(&sh.full[s], round & 1u);
         }
         return;
     }
@@ -737,15 +776,17 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
         uint32_t qkp = 1, post = 0, tau = 0;
         // ---- scatter the item's staged postings ----------------------------------
         for (;;) {
-            if (!aborted && !warp_wait(&sh.full[s], round & 1u, abort_flag)) {
+            if (!warp_wait(&sh.full[s], round & 1u, abort_flag, wait_polls)) {
+                // give up without releasing the buffer (its copies may still
+                // be landing; the producer waits for them before it leaves)
                 aborted = true;
                 if (lane == 0) {
                     set_status(status, BM25_E_TIMEOUT);
-                    sh.abort_flag = 1;
+                    *(volatile uint32_t*)&sh.abort_flag = 1u;
                 }
+                break;
             }
-            // (clamped so that a header left stale by an abandoned wait
-            // still indexes inside the arrays)
+            // (clamped, as a defence: the header indexes the arrays)
             const StageHdr hd = sh.hdr[s];
             tile = min(max(hd.tile, 0), n_tiles - 1);
             qi = min(max(hd.qi, 0), nq - 1);
@@ -755,11 +796,11 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
             mode = hd.mode == kModeCross ? kModeCross : kModeList;
             const bool cross = mode == kModeCross;  // warp-uniform
             const float tau_f = unorder_f32(tau);   // (used when tau is above the key of 0)
-            const int32_t n_e = aborted ? 0 : min(max(hd.n, 0), kStageEntries);
+            const int32_t n_e = min(max(hd.n, 0), stage_entries);
             const bool last = hd.last != 0;
             const uint32_t d0 = (uint32_t)tile * (uint32_t)W;
             const uint32_t wd = (uint32_t)min((int64_t)W, n_docs - (int64_t)d0);
-            const uint2* sb = stage + (size_t)s * kStageEntries;
+            const uint2* sb = stage + (size_t)s * stage_entries;
             // chunks of 32 entries: warp w takes chunks w, w + CW, ...
             for (int32_t e0 = warp * 32; e0 < n_e; e0 += NT) {
                 const int32_t e = e0 + lane;
@@ -781,21 +822,26 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
                     if (lane == leader)
                         base = atomicAdd(&sh.tl_count[par], (uint32_t)__popc(b));
                     base = __shfl_sync(0xffffffffu, base, leader);
-                    if (first)
-                        tl[base + __popc(b & ltmask)] = (uint16_t)dl;
+                    const uint32_t pos = base + __popc(b & ltmask);
+                    if (first && pos < tl_cap)  // beyond the cap only counted
+                        tl[pos] = (uint16_t)dl;
                 }
             }
             __syncwarp();
             if (lane == 0)
                 mbar_arrive(&sh.empty[s]);
-            if (++s == kNumStages) {
+            if (++s == n_stages) {
                 s = 0;
                 round++;
             }
-            if (last || aborted)
+            if (last)
                 break;
         }
-        consumer_sync<NT>();  // every posting added, every first touch (crossing) listed
+        // every posting added, every first touch (crossing) listed; if any
+        // consumer warp gave up, all of them leave here together, so that no
+        // warp waits at a later barrier for one that left
+        if (consumer_sync_any<NT>(aborted))
+            return;
 
         const int64_t d0 = (int64_t)tile * W;
         const int32_t wd = (int32_t)min((int64_t)W, n_docs - d0);
@@ -888,16 +934,22 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
             consumer_sync<NT>();  // the tile is clean before the next scatter
         } else if (!zero_counts) {
             // ---- claim: read and reset each touched document once ------------------
-            for (uint32_t b0 = warp * 32; b0 < n_t; b0 += NT) {  // warp-uniform
+            // (through the touched list, or over the whole tile when the list
+            // overflowed; a touched sum is never -0.0)
+            const bool walk = n_t > tl_cap;
+            const uint32_t n_w = walk ? (uint32_t)wd : n_t;
+            for (uint32_t b0 = warp * 32; b0 < n_w; b0 += NT) {  // warp-uniform
                 const uint32_t t = b0 + lane;
                 bool keep = false;
                 uint32_t dl = 0;
                 float v = 0.0f;
-                if (t < n_t) {
-                    dl = tl[t];
+                if (t < n_w) {
+                    dl = walk ? t : tl[t];
                     v = acc[dl];
-                    acc[dl] = neg0;
-                    keep = order_f32(v) >= tau;
+                    if (__float_as_uint(v) != kUntouched) {
+                        acc[dl] = neg0;
+                        keep = order_f32(v) >= tau;
+                    }
                 }
                 const uint32_t bal = __ballot_sync(0xffffffffu, keep);
                 if (bal) {
@@ -949,10 +1001,12 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
             }
         } else {
             // ---- a score of 0 can still rank: count, fill, select over the lists -------
+            // (through the touched list, or over the whole tile when it overflowed)
+            const bool walk = n_t > tl_cap;
             uint32_t c = 0, p = 0;
-            for (uint32_t t = tid; t < n_t; t += NT) {
-                const float v = acc[tl[t]];
-                c += order_f32(v) >= tau;
+            for (uint32_t t = tid; t < (walk ? (uint32_t)wd : n_t); t += NT) {
+                const float v = acc[walk ? t : tl[t]];
+                c += __float_as_uint(v) != kUntouched && order_f32(v) >= tau;
                 p += v > 0.0f;
             }
             uint32_t n_cand, n_pos, n_unt = 0, cut = 0;
@@ -963,14 +1017,24 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
                 n_unt = consumer_first_untouched<NT>(acc, wd, kp, sh.scan, &sh.cutoff);
                 cut = sh.cutoff;
             }
-            const uint32_t n_l = n_t;
+            // indexes: the listed documents, then the tile's first `cut`
+            // documents (untouched ones score 0); walking, the tile itself
+            const uint32_t n_l = walk ? 0u : n_t;
             const uint32_t n_all = n_cand + n_unt;
             n_emit = min(n_all, kp);
             if (tid == 0)
                 st.ctr = 0;
             consumer_sync<NT>();
-            select_top<true>(st, NT, csync, n_l + cut, n_all, kp, 0, 0ull,
+            select_top<true>(st, NT, csync, walk ? (uint32_t)wd : n_l + cut, n_all, kp, 0, 0ull,
                              [&](uint32_t i) -> u64 {
+                                 if (walk) {
+                                     const float v = acc[i];
+                                     if (__float_as_uint(v) != kUntouched)
+                                         return order_f32(v) >= tau
+                                                    ? make_key(v, (uint32_t)(d0 + i))
+                                                    : 0ull;
+                                     return i < cut ? make_key(0.0f, (uint32_t)(d0 + i)) : 0ull;
+                                 }
                                  if (i < n_l) {
                                      const uint32_t dl = tl[i];
                                      const float v = acc[dl];
@@ -987,8 +1051,12 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
                 new_tau = (uint32_t)(st.prefix >> 32);
                 tau_ok = true;
             }
-            for (uint32_t t = tid; t < n_t; t += NT)
-                acc[tl[t]] = neg0;
+            if (walk) {
+                reset_tile();
+            } else {
+                for (uint32_t t = tid; t < n_t; t += NT)
+                    acc[tl[t]] = neg0;
+            }
             consumer_sync<NT>();
         }
         // the output warp's first lane records the item (select paths: every
@@ -1081,7 +1149,9 @@ __global__ void __launch_bounds__(kMergeThreads)
     uint32_t carry = 0;
     for (int t0 = 0; t0 < n_tiles; t0 += kMergeThreads) {
         const int t = t0 + tid;
-        const uint32_t c = t < n_tiles ? tcount[(int64_t)t * nl + b] : 0u;
+        // (at most kstride: a count left unwritten by a tile kernel that gave
+        // up must not send the gather past the item's slots)
+        const uint32_t c = t < n_tiles ? min(tcount[(int64_t)t * nl + b], (uint32_t)kstride) : 0u;
         uint32_t tot;
         const uint32_t ex = block_exclusive_sum(c, st.red, &tot);
         if (t < n_tiles)
@@ -1479,6 +1549,9 @@ int grow(T** p, size_t* cap, size_t need, bool capturing)
     *p = nullptr;
     *cap = 0;
     size_t n = need > 0 ? need : 1;
+    if (forced_alloc_failure())
+        return set_error(BM25_E_OOM, "device allocation of %zu bytes failed (forced by "
+                         "bm25_debug_fail_allocs)", n * sizeof(T));
     BM25_CUDA_TRY(cudaMalloc((void**)p, n * sizeof(T)));
     *cap = n;
     return BM25_OK;
@@ -1645,7 +1718,8 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
     }
 
     // launch shapes that do not depend on the sub-batch
-    const size_t smem = staged_smem_bytes(W);
+    const uint32_t tl_cap = std::min<uint32_t>((uint32_t)W, kTouchCap);
+    const size_t smem = staged_smem_bytes(W, plan.stages, plan.stage_entries, tl_cap);
     // plan.threads consumer threads (4, 8 or 16 warps) and one producer warp
     auto tile_kernel = plan.threads == 128   ? k_tile_staged<4>
                        : plan.threads == 192 ? k_tile_staged<6>
@@ -1694,7 +1768,8 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
             ProfileScope ps_("k_tile_staged", s);
             tile_kernel<<<g2, tile_threads, smem, s>>>(
                 N, ix->posts, reinterpret_cast<const uint32_t*>(ws->seg), W, n_tiles, kstride,
-                ws->lrec, ws->lpost, ws->ctr, ws->thresh, ws->tcount, ws->cand, ix->status);
+                ws->lrec, ws->lpost, ws->ctr, ws->thresh, ws->tcount, ws->cand, ix->status,
+                handshake_polls(), plan.stages, plan.stage_entries, tl_cap);
         }
         count_launch();
         BM25_LAUNCH_CHECK();

@@ -82,6 +82,8 @@ struct bm25_server {
     // statistics since the last reset
     int64_t completed = 0, failed = 0, batches = 0, batched_queries = 0;
     std::vector<double> latency_us;
+    bool any_submit = false, any_done = false;
+    Clock::time_point first_submit, last_done;
 };
 
 using namespace bm25;
@@ -167,6 +169,8 @@ void complete(bm25_server* sv, Slot& s, int rc)
             sv->completed++;
             sv->latency_us.push_back(
                 std::chrono::duration<double, std::micro>(now - r.t_submit).count());
+            sv->any_done = true;
+            sv->last_done = now;
         } else {
             r.status = rc;
             sv->failed++;
@@ -444,6 +448,10 @@ int bm25_server_submit(bm25_server* sv, int32_t index_id, const int32_t* tokens,
             return set_error(BM25_E_INVALID, "server is shutting down");
         r->ticket = sv->next_ticket++;
         r->t_submit = Clock::now();
+        if (!sv->any_submit) {
+            sv->any_submit = true;
+            sv->first_submit = r->t_submit;
+        }
         sv->tickets[r->ticket] = r;
         sv->queues[index_id].push_back(r);
         *ticket = r->ticket;
@@ -504,9 +512,14 @@ int bm25_server_stats_get(bm25_server* sv, int reset, bm25_server_stats* out)
     for (const Slot& s : sv->slots)
         held += slot_bytes(s);
     out->bytes_held = (int64_t)held;
+    out->span_us = (sv->any_submit && sv->any_done && sv->last_done > sv->first_submit)
+                       ? std::chrono::duration<double, std::micro>(sv->last_done -
+                                                                   sv->first_submit).count()
+                       : 0.0;
     if (reset) {
         sv->completed = sv->failed = sv->batches = sv->batched_queries = 0;
         sv->latency_us.clear();
+        sv->any_submit = sv->any_done = false;
     }
     return BM25_OK;
 }

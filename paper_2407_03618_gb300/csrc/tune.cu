@@ -169,6 +169,8 @@ extern "C" int bm25_autotune(bm25_index* ix, const int32_t* query_tokens, int64_
         o->tile_docs = p.tile_docs;
         o->block_threads = p.threads;
         o->dense_max_postings = p.dense_max;
+        o->stage_entries = p.stage_entries;
+        o->stages = p.stages;
     };
     to_c(cur, best);
     if (best_ms)

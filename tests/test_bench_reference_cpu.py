@@ -12,7 +12,7 @@ import bench
 def _run(rank, world):
     env = dict(os.environ, RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
     cmd = [sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
-           "--workload", "tiny", "--steps", "2", "--warmup", "1", "--cpu-sample-queries", "4"]
+           "--workload", "tiny", "--steps", "2", "--warmup", "1", "--ref-sample-queries", "4"]
     return subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=300,
                           cwd=bench.ROOT)
 
@@ -30,6 +30,12 @@ def test_rank0_prints_the_reference_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
     assert cb["sample"]
+    # the same config dict the GPU arm prints (bench_config), so the two lines compare
+    import argparse
+    from paper_2407_03618_gb300 import synth
+    args = argparse.Namespace(variant="lucene", k=10)
+    w = synth.WORKLOADS["tiny"]
+    assert d["config"] == json.loads(json.dumps(bench.bench_config(args, w, w.n_queries, 2)))
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0

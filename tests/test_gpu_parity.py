@@ -147,16 +147,21 @@ def test_sort_spans_many_tiles_and_passes(torch_dev):
 
 # --------------------------------------------------------- retrieval -----
 
-@pytest.mark.parametrize("tile_docs,threads", [(1024, 128), (2048, 256), (16384, 512),
-                                               (4096, 512), (49152, 256), (3072, 192)])
-def test_retrieval_across_tiles(torch_dev, tile_docs, threads):
-    """Small doc tiles force many (query, tile) items and a ragged last tile."""
+@pytest.mark.parametrize("tile_docs,threads,stage_entries,stages",
+                         [(1024, 128, 512, 2), (2048, 256, 128, 8), (16384, 512, 4096, 3),
+                          (4096, 512, 512, 2), (49152, 256, 256, 2), (3072, 192, 8192, 2),
+                          (10240, 192, 1024, 4), (8192, 256, 2048, 3)])
+def test_retrieval_across_tiles(torch_dev, tile_docs, threads, stage_entries, stages):
+    """Small doc tiles force many (query, tile) items and a ragged last tile;
+    staging rings from eight 1 KB buffers (an item spans many) to two 64 KB
+    ones (a buffer holds several items' worth)."""
     c = synth.make_corpus(9_999, 3_000, 1.1, ("poisson", 30), seed=2)
     q = synth.make_queries(64, 3_000, 1.1, ("uniform", 0, 12), seed=3)
     ix = _build(torch_dev, c, "bm25+")
-    ix.set_plan(2, tile_docs, threads)
+    ix.set_plan(2, tile_docs, threads, 0, stage_entries, stages)
     assert ix.get_plan() == {"accumulator": 2, "tile_docs": tile_docs, "block_threads": threads,
-                             "dense_max_postings": 4096}
+                             "dense_max_postings": 4096, "stage_entries": stage_entries,
+                             "stages": stages}
     orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.BM25PLUS)
     for k in (1, 7, 100, 1000, 2500):  # 2500: k' wider than the narrow tiles
         _check_retrieval(torch_dev, ix, orc, q, k, where=f"W={tile_docs} k={k}")
