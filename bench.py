@@ -40,7 +40,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="passage", choices=sorted(synth.WORKLOADS))
-    p.add_argument("--variant", default="lucene", choices=list(synth.ALL_VARIANTS))
+    p.add_argument("--variant", default="lucene", choices=list(synth.ALL_VARIANTS) + ["tfldp"])
     p.add_argument("--k", type=int, default=10)
     p.add_argument("--plain-queries", type=int, default=1000)
     p.add_argument("--cpu-sample-queries", type=int, default=32,

@@ -30,9 +30,13 @@
  *   ATIRE      IDF = ln(N / DF),                         S = IDF (k1+1) TF/(TF + k1 K_D)
  *   BM25L      IDF = ln((N + 1)/(DF + 0.5)), c = TF/K_D, S = IDF (k1+1)(c + delta)/(k1 + c + delta)
  *   BM25PLUS   IDF = ln((N + 1)/DF),                     S = IDF ((k1+1) TF/(k1 K_D + TF) + delta)
- * (the last four as the paper adopts them from Kamphuis et al. 2020,
- * Sec. 2 "Alternative BM25 implementations").  A term with DF = 0 has
- * IDF = 0 and S0 = 0.
+ *   TFLDP      IDF = ln((N + 1)/DF), p = TF/K_D,         S = IDF (1 + ln(1 + ln(p + delta)))
+ * (Robertson .. BM25PLUS as the paper adopts them from Kamphuis et al. 2020,
+ * Sec. 2 "Alternative BM25 implementations"; TFLDP is TF_{l o delta o p} x
+ * IDF of Rousseau and Vazirgiannis 2013, which Sec. 2.1 names among the
+ * models with a non-zero score at TF = 0: pivoted normalisation, lower
+ * bound delta, double logarithm; k1 is unused, delta > 1/e).  A term with
+ * DF = 0 has IDF = 0 and S0 = 0.
  */
 #ifndef BM25_GPU_H
 #define BM25_GPU_H
@@ -51,7 +55,8 @@ enum bm25_variant {
     BM25_ROBERTSON = 1,
     BM25_ATIRE = 2,
     BM25_L = 3,
-    BM25_PLUS = 4
+    BM25_PLUS = 4,
+    BM25_TFLDP = 5   /* TF_{l o delta o p} x IDF */
 };
 
 enum bm25_status {
@@ -95,12 +100,12 @@ typedef struct bm25_plan {
     int32_t tile_docs;          /* doc-tile width: a multiple of 1024 in [1024, 49152]
                                    (default 10240) */
     int32_t block_threads;      /* consumer threads per CTA of the tiled kernel: 128, 192,
-                                   256 or 512 (default 192; one producer warp is added) */
+                                   256 or 512 (default 256; one producer warp is added) */
     int32_t dense_max_postings; /* dense-path bound for AUTO / L2_DENSE, in [0, 2^22]
                                    (default 4096) */
     int32_t stage_entries;      /* packed postings per shared-memory staging buffer of the
-                                   tiled kernel: a multiple of 64 in [128, 8192] (default 512) */
-    int32_t stages;             /* staging buffers in its ring, in [2, 8] (default 2) */
+                                   tiled kernel: a multiple of 64 in [128, 8192] (default 1024) */
+    int32_t stages;             /* staging buffers in its ring, in [2, 8] (default 3) */
 } bm25_plan;
 
 /* ------------------------------------------------------------------ index */
@@ -115,8 +120,9 @@ typedef struct bm25_plan {
  *                          are allowed and count in N.
  *   vocab                  number of term ids; every token must be in [0, vocab).
  *   variant                enum bm25_variant.
- *   k1 >= 0, 0 <= b <= 1, delta >= 0 (delta is used by BM25L and BM25PLUS;
- *                          BM25L also needs k1 + delta > 0).
+ *   k1 >= 0, 0 <= b <= 1, delta >= 0 (delta is used by BM25L, BM25PLUS and
+ *                          TFLDP; BM25L also needs k1 + delta > 0, TFLDP
+ *                          delta > 1/e).
  *   n_docs in [1, 2^31 - 2], n_tokens in [0, 2^31 - 2].
  *
  * Computes |D|, Lavg (FP64), TF per distinct (term, doc) pair, DF, IDF and
@@ -295,10 +301,11 @@ int bm25_index_get_plan(const bm25_index* index, bm25_plan* plan);
 /* Times retrieval of a sample batch (device arrays, as in bm25_retrieve,
  * with one k for all queries) under candidate plans and makes the fastest
  * the index's plan.  Candidates: tile widths 6144, 7168, 8192, 10240 and
- * 12288 with every query tiled and 192 consumer threads, then 128 and 256
- * consumer threads at the best width, then, with the best of those,
- * dense-path bounds of 2048 .. 32768 postings (the accumulator per
- * query-length bucket).  Each step tries the library's default first, and a
+ * 12288 with every query tiled and the default threads and staging ring,
+ * then 128, 192, 256 and 512 consumer threads at the best width, then
+ * staging rings of 2 x 512, 2 x 1024, 3 x 1024 and 2 x 2048 postings with
+ * the best of those, then dense-path bounds of 2048 .. 32768 postings (the
+ * accumulator per query-length bucket).  Each step tries the library's default first, and a
  * later candidate replaces the best so far only when more than 1 % faster, so
  * that timing noise does not move the plan between runs.  Each candidate
  * runs once untimed and twice timed (CUDA events on `cuda_stream`); the best
@@ -311,6 +318,54 @@ int bm25_autotune(bm25_index* index, const int32_t* query_tokens, int64_t n_quer
                   const int64_t* query_offsets, int32_t n_queries, int32_t k,
                   void* cuda_stream, bm25_plan* best, double* best_ms, bm25_plan* tried,
                   double* tried_ms, int32_t tried_cap, int32_t* n_tried);
+
+/* ------------------------------------------------------- doc-range shards */
+
+/* A collection too large for one index is split into contiguous document
+ * ranges, one index per range (one per GPU; the paper's Sec. 2.1 footnote
+ * puts a dense 2M x 200K matrix at 1.6 TB, and the sparse one grows with the
+ * collection too).  Every score must still use the WHOLE collection's DF, N
+ * and Lavg, so building a shard takes two steps around one exchange:
+ *   1. bm25_index_build over the range's documents (local ids 0 .. n-1);
+ *      bm25_index_df_device gives its DF, bm25_index_info its N and tokens;
+ *   2. the caller sums DF[vocab], N and the token count over the shards
+ *      (an all-reduce), then bm25_index_rescore applies them.
+ * A rescored shard's stored scores, IDF, S0 and Lavg equal those of one
+ * index over the whole collection bit for bit (same arithmetic, same
+ * inputs), and its retrieval returns global doc ids (local + doc_id_offset).
+ * A query's top k over the collection is then the merge of every shard's
+ * top k (an all-gather of the rows, then bm25_merge_topk). */
+
+/* Copies the index's DF (its column lengths, int32 [vocab]) to df_out
+ * (device).  Asynchronous on cuda_stream. */
+int bm25_index_df_device(const bm25_index* index, int32_t* df_out, void* cuda_stream);
+
+/* Recomputes IDF, S0, Lavg and every stored score from the collection's
+ * statistics: global_df[vocab] (device int32, the sum of every shard's DF;
+ * NULL = this index's own), global_n_docs (N of the collection, >= this
+ * index's n_docs) and global_n_tokens (>= its n_tokens); Lavg =
+ * global_n_tokens / global_n_docs.  doc_id_offset: the global id of this
+ * index's document 0 (doc_id_offset + n_docs <= global_n_docs), added to
+ * every id retrieval returns.  The structure (TF, DF, |D|, indptr, indices)
+ * is unchanged.  Stream-ordered on cuda_stream; no retrieval on the index
+ * may run meanwhile. */
+int bm25_index_rescore(bm25_index* index, const int32_t* global_df, int64_t global_n_docs,
+                       int64_t global_n_tokens, int64_t doc_id_offset, void* cuda_stream);
+
+/* The shard parameters of an index (0, its own N and tokens unless
+ * rescored).  Any pointer may be NULL.  Host memory. */
+int bm25_index_shard_info(const bm25_index* index, int64_t* doc_id_offset,
+                          int64_t* global_n_docs, int64_t* global_n_tokens);
+
+/* Merges the top-k rows of n_shards shards: cand_ids / cand_scores are
+ * [n_shards][n_queries][k] (device; id -1 marks an empty slot, as the
+ * retrieval of a shard with fewer than k documents leaves them).  Row q of
+ * out_ids / out_scores ([n_queries][k], device) gets the min(k, valid slots)
+ * best by score descending, doc id ascending among equal scores, then -1 /
+ * -inf.  1 <= k <= BM25_MAX_K.  Asynchronous on cuda_stream. */
+int bm25_merge_topk(const int32_t* cand_ids, const float* cand_scores, int32_t n_shards,
+                    int32_t n_queries, int32_t k, int32_t* out_ids, float* out_scores,
+                    void* cuda_stream);
 
 /* ---------------------------------------------------------------- serving */
 

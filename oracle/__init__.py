@@ -24,9 +24,9 @@ from dataclasses import dataclass
 
 import numpy as np
 
-LUCENE, ROBERTSON, ATIRE, BM25L, BM25PLUS = 0, 1, 2, 3, 4
+LUCENE, ROBERTSON, ATIRE, BM25L, BM25PLUS, TFLDP = 0, 1, 2, 3, 4, 5
 VARIANTS = {"lucene": LUCENE, "robertson": ROBERTSON, "atire": ATIRE,
-            "bm25l": BM25L, "bm25+": BM25PLUS}
+            "bm25l": BM25L, "bm25+": BM25PLUS, "tfldp": TFLDP}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bm25_oracle.c")

@@ -17,6 +17,13 @@
  *   - the other four variants (Robertson, ATIRE, BM25L, BM25+) follow the
  *     definitions the paper adopts from Kamphuis et al. 2020 (Sec. 2,
  *     "Alternative BM25 implementations"); the paper prints only Lucene's.
+ *   - TF_{l o delta o p} x IDF, which Sec. 2.1 names as the third model whose
+ *     non-occurrence score is not zero (Rousseau and Vazirgiannis 2013):
+ *     the pivoted length normalisation p (TF / (1 - b + b |D| / Lavg)), then
+ *     the lower bound delta (+ delta), then the double logarithm l
+ *     (x -> 1 + ln(1 + ln x)), times IDF = ln((|C| + 1) / DF).  Read, as
+ *     Sec. 2.1 does, at TF = 0 too: S0 = IDF (1 + ln(1 + ln delta)), defined
+ *     for delta > 1/e.
  *   - the non-occurrence score S0(t) = S(t, empty doc) and the shifted
  *     matrix S - S0, with B = sum S_delta + sum S0       Sec. 2.1
  *   - top-k over ALL documents, ties broken by lower doc id
@@ -46,6 +53,7 @@
 #define ORC_ATIRE 2
 #define ORC_BM25L 3
 #define ORC_BM25PLUS 4
+#define ORC_TFLDP 5
 
 /* ---- per-variant formulas (FP64) ------------------------------------- */
 
@@ -66,6 +74,7 @@ double oracle_idf(int variant, double n, double df)
     case ORC_BM25L:
         return log((n + 1.0) / (df + 0.5));
     case ORC_BM25PLUS:
+    case ORC_TFLDP:
         return log((n + 1.0) / df);
     }
     return NAN;
@@ -96,6 +105,12 @@ double oracle_term_score(int variant, double idf, double tf, double len,
     }
     case ORC_BM25PLUS:
         return idf * (((tf > 0.0) ? (k1 + 1.0) * tf / (k1 * norm + tf) : 0.0) + delta);
+    case ORC_TFLDP: {
+        /* p: pivoted normalisation, delta: lower bound, l: 1 + ln(1 + ln x) */
+        double p = (tf > 0.0) ? tf / norm : 0.0;
+        double x = p + delta;
+        return idf * (1.0 + log(1.0 + log(x)));
+    }
     }
     return NAN;
 }

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build_ext
 
-VARIANTS = {"lucene": 0, "robertson": 1, "atire": 2, "bm25l": 3, "bm25+": 4}
+VARIANTS = {"lucene": 0, "robertson": 1, "atire": 2, "bm25l": 3, "bm25+": 4, "tfldp": 5}
 ACC_UNSET, ACC_AUTO, ACC_SMEM_TILED, ACC_L2_DENSE = 0, 1, 2, 3
 STATUS = {0: "BM25_OK", -1: "BM25_E_INVALID", -2: "BM25_E_TOKEN_RANGE", -3: "BM25_E_OOM",
           -4: "BM25_E_CUDA", -5: "BM25_E_TIMEOUT", 1: "BM25_PENDING"}
@@ -115,6 +115,10 @@ def load(path: str | None = None):
         "bm25_profile_end": (cint, []),
         "bm25_profile_count": (cint, []),
         "bm25_profile_get": (cint, [cint, ctypes.c_char_p, cint, P, P]),
+        "bm25_index_df_device": (cint, [P, P, P]),
+        "bm25_index_rescore": (cint, [P, P, i64, i64, i64, P]),
+        "bm25_index_shard_info": (cint, [P, P, P, P]),
+        "bm25_merge_topk": (cint, [P, P, i32, i32, i32, P, P, P]),
         "bm25_debug_set_handshake_polls": (cint, [i32]),
         "bm25_debug_fail_allocs": (cint, [i32]),
     }
@@ -139,6 +143,23 @@ def debug_set_handshake_polls(polls: int):
 def debug_fail_allocs(n: int):
     """Test hook: the next n device allocations of the library fail with BM25_E_OOM."""
     _check(load().bm25_debug_fail_allocs(n))
+
+
+def merge_topk(cand_ids, cand_scores, k: int, out=None, stream=None):
+    """Merge shard rows: cand_ids int32 / cand_scores float32 CUDA tensors
+    [n_shards, n_queries, k] -> (ids, scores) [n_queries, k]."""
+    import torch
+    ci = _dev_tensor(cand_ids, torch.int32)
+    cs = _dev_tensor(cand_scores, torch.float32)
+    g, nq = int(ci.shape[0]), int(ci.shape[1])
+    if out is None:
+        ids = torch.empty((nq, k), dtype=torch.int32, device=ci.device)
+        sc = torch.empty((nq, k), dtype=torch.float32, device=ci.device)
+    else:
+        ids, sc = out
+    _check(load().bm25_merge_topk(ci.data_ptr(), cs.data_ptr(), g, nq, k, ids.data_ptr(),
+                                  sc.data_ptr(), _stream(stream)))
+    return ids, sc
 
 
 def release_cached():
@@ -325,6 +346,35 @@ class Index:
         p = Plan()
         _check(load().bm25_index_get_plan(self.handle, ctypes.byref(p)))
         return p.as_dict()
+
+    def df_device(self, out=None, stream=None):
+        """The index's DF as a CUDA int32 tensor [vocab]."""
+        import torch
+        v = self.info()["vocab"]
+        if out is None:
+            out = torch.empty(v, dtype=torch.int32, device=torch.device("cuda",
+                                                                          torch.cuda.current_device()))
+        _check(load().bm25_index_df_device(self.handle, out.data_ptr(), _stream(stream)))
+        return out
+
+    def rescore(self, global_df, global_n_docs: int, global_n_tokens: int, doc_id_offset: int,
+                stream=None):
+        """Apply a collection's statistics to this doc-range shard (global_df:
+        CUDA int32 [vocab] or None) and set its global doc-id offset."""
+        import torch
+        p = None
+        if global_df is not None:
+            global_df = _dev_tensor(global_df, torch.int32)
+            p = global_df.data_ptr()
+        _check(load().bm25_index_rescore(self.handle, p, int(global_n_docs), int(global_n_tokens),
+                                         int(doc_id_offset), _stream(stream)))
+
+    def shard_info(self) -> dict:
+        off, nd, nt = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().bm25_index_shard_info(self.handle, ctypes.byref(off), ctypes.byref(nd),
+                                            ctypes.byref(nt)))
+        return {"doc_id_offset": off.value, "global_n_docs": nd.value,
+                "global_n_tokens": nt.value}
 
     def sync_status(self, stream=None):
         _check(load().bm25_sync_status(self.handle, _stream(stream)))

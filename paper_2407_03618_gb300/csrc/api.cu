@@ -1,6 +1,7 @@
 // The C ABI of libbm25gpu (declared in include/bm25.h): argument checks,
 // host-buffer variants, checkpoint export/import, status and error reporting.
 // All compute is in index_build.cu, retrieve.cu and scan.cu.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -76,7 +77,7 @@ int check_build_args(int64_t n_tokens, int64_t n_docs, int32_t vocab, int varian
     if (!out)
         return set_error(BM25_E_INVALID, "out is NULL");
     *out = nullptr;
-    if (variant < BM25_LUCENE || variant > BM25_PLUS)
+    if (variant < BM25_LUCENE || variant > BM25_TFLDP)
         return set_error(BM25_E_INVALID, "unknown variant %d", variant);
     if (n_docs < 1 || n_docs > (int64_t)INT32_MAX - 1)
         return set_error(BM25_E_INVALID, "n_docs = %lld outside [1, 2^31 - 2]", (long long)n_docs);
@@ -90,6 +91,8 @@ int check_build_args(int64_t n_tokens, int64_t n_docs, int32_t vocab, int varian
                          k1, b, delta);
     if (variant == BM25_L && !(k1 + delta > 0.0))
         return set_error(BM25_E_INVALID, "BM25L needs k1 + delta > 0");
+    if (variant == BM25_TFLDP && !(1.0 + log(delta) > 0.0))
+        return set_error(BM25_E_INVALID, "TFLDP needs delta > 1/e (got %g)", delta);
     return BM25_OK;
 }
 
@@ -349,6 +352,8 @@ int bm25_index_import(int64_t n_docs, int64_t n_tokens, int64_t nnz, int32_t voc
     ix->b = b;
     ix->delta = delta;
     ix->lavg = lavg;
+    ix->stat_docs = n_docs;
+    ix->stat_tokens = n_tokens;
     int rc = alloc_index_arrays(ix, 0, true, true);
     auto cp = [&](void* dst, const void* src, size_t bytes) -> int {
         if (bytes)
@@ -582,6 +587,71 @@ int bm25_retrieve_host(const bm25_index* ix, const int32_t* query_tokens,
                                   s));
     BM25_CUDA_TRY(cudaStreamSynchronize(s));
     return BM25_OK;
+}
+
+int bm25_index_df_device(const bm25_index* ix, int32_t* df_out, void* cuda_stream)
+{
+    clear_error();
+    if (!ix || !df_out)
+        return set_error(BM25_E_INVALID, "NULL argument");
+    BM25_CUDA_TRY(cudaMemcpyAsync(df_out, ix->df, sizeof(int32_t) * (size_t)ix->vocab,
+                                  cudaMemcpyDeviceToDevice, (cudaStream_t)cuda_stream));
+    return BM25_OK;
+}
+
+int bm25_index_rescore(bm25_index* ix, const int32_t* global_df, int64_t global_n_docs,
+                       int64_t global_n_tokens, int64_t doc_id_offset, void* cuda_stream)
+{
+    clear_error();
+    if (!ix)
+        return set_error(BM25_E_INVALID, "index is NULL");
+    if (global_n_docs < ix->n_docs || global_n_docs > (int64_t)INT32_MAX - 1)
+        return set_error(BM25_E_INVALID, "global_n_docs %lld outside [n_docs %lld, 2^31 - 2]",
+                         (long long)global_n_docs, (long long)ix->n_docs);
+    if (global_n_tokens < ix->n_tokens)
+        return set_error(BM25_E_INVALID, "global_n_tokens %lld is below the index's %lld",
+                         (long long)global_n_tokens, (long long)ix->n_tokens);
+    if (doc_id_offset < 0 || doc_id_offset + ix->n_docs > global_n_docs)
+        return set_error(BM25_E_INVALID, "doc range [%lld, %lld) outside [0, %lld)",
+                         (long long)doc_id_offset, (long long)(doc_id_offset + ix->n_docs),
+                         (long long)global_n_docs);
+    int dev = 0;
+    BM25_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != ix->device)
+        return set_error(BM25_E_INVALID, "current device %d is not the index's device %d", dev,
+                         ix->device);
+    std::lock_guard<std::mutex> g(ix->mu);
+    BM25_TRY(rescore_index(ix, global_df, global_n_docs, global_n_tokens,
+                           (cudaStream_t)cuda_stream));
+    ix->doc_offset = doc_id_offset;
+    return BM25_OK;
+}
+
+int bm25_index_shard_info(const bm25_index* ix, int64_t* doc_id_offset, int64_t* global_n_docs,
+                          int64_t* global_n_tokens)
+{
+    clear_error();
+    if (!ix)
+        return set_error(BM25_E_INVALID, "index is NULL");
+    if (doc_id_offset) *doc_id_offset = ix->doc_offset;
+    if (global_n_docs) *global_n_docs = ix->stat_docs;
+    if (global_n_tokens) *global_n_tokens = ix->stat_tokens;
+    return BM25_OK;
+}
+
+int bm25_merge_topk(const int32_t* cand_ids, const float* cand_scores, int32_t n_shards,
+                    int32_t n_queries, int32_t k, int32_t* out_ids, float* out_scores,
+                    void* cuda_stream)
+{
+    clear_error();
+    if (n_shards < 1 || n_queries < 0 || k < 1 || k > BM25_MAX_K ||
+        (int64_t)n_shards * k > (int64_t)INT32_MAX)
+        return set_error(BM25_E_INVALID, "need n_shards >= 1, n_queries >= 0, 1 <= k <= %d "
+                         "(got %d, %d, %d)", BM25_MAX_K, n_shards, n_queries, k);
+    if (n_queries > 0 && (!cand_ids || !cand_scores || !out_ids || !out_scores))
+        return set_error(BM25_E_INVALID, "NULL argument");
+    return merge_topk_device(cand_ids, cand_scores, n_shards, n_queries, k, out_ids, out_scores,
+                             (cudaStream_t)cuda_stream);
 }
 
 int bm25_debug_set_handshake_polls(int32_t polls)

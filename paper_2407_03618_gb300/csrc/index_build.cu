@@ -67,7 +67,8 @@ __global__ void k_doc_prep(const int64_t* __restrict__ off, int64_t n_docs, int6
             const int64_t len = bad ? 0 : hi - lo;
             doc_len[d] = (int32_t)len;
             const double kd = 1.0 - b + b * (double)len / lavg;
-            len_factor[d] = (variant == BM25_L) ? (float)(1.0 / kd) : (float)(k1 * kd);
+            len_factor[d] =
+                (variant == BM25_L || variant == BM25_TFLDP) ? (float)(1.0 / kd) : (float)(k1 * kd);
         }
         if (__any_sync(0xffffffffu, bad))
             continue;  // the build fails; only in-range writes happen above
@@ -424,19 +425,23 @@ __device__ double idf_of(int variant, double n, double df)
         return log((n - df + 0.5) / (df + 0.5));
     case BM25_ATIRE:
         return log(n / df);
-    default:  // BM25_PLUS
+    default:  // BM25_PLUS, BM25_TFLDP
         return log((n + 1.0) / df);
     }
 }
 
+// df_out gets the index's own DF (its column lengths); IDF is taken from
+// df_global[t] and n_docs when df_global is given (a doc-range shard scored
+// with the whole collection's statistics), else from the own DF.
 __global__ void k_idf(const int64_t* __restrict__ indptr, int32_t vocab, int64_t n_docs,
-                      int variant, double k1, double delta, int32_t* __restrict__ df_out,
-                      double* __restrict__ idf_out, double* __restrict__ s0_out,
-                      float* __restrict__ coef)
+                      int variant, double k1, double delta, const int32_t* __restrict__ df_global,
+                      int32_t* __restrict__ df_out, double* __restrict__ idf_out,
+                      double* __restrict__ s0_out, float* __restrict__ coef)
 {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < vocab;
          t += (int64_t)gridDim.x * blockDim.x) {
-        int64_t df = indptr[t + 1] - indptr[t];
+        const int64_t df_own = indptr[t + 1] - indptr[t];
+        const int64_t df = df_global ? (int64_t)df_global[t] : df_own;
         double w = idf_of(variant, (double)n_docs, (double)df);
         double s0 = 0.0, c = w;
         if (variant == BM25_ATIRE || variant == BM25_PLUS)
@@ -446,8 +451,10 @@ __global__ void k_idf(const int64_t* __restrict__ indptr, int32_t vocab, int64_t
             c = w * (k1 + 1.0) * k1 / (k1 + delta);
         } else if (variant == BM25_PLUS) {
             s0 = w * delta;
+        } else if (variant == BM25_TFLDP) {
+            s0 = w * (1.0 + log(1.0 + log(delta)));
         }
-        df_out[t] = (int32_t)df;
+        df_out[t] = (int32_t)df_own;
         idf_out[t] = w;
         s0_out[t] = s0;
         coef[t] = (float)c;
@@ -459,10 +466,37 @@ __global__ void k_idf(const int64_t* __restrict__ indptr, int32_t vocab, int64_t
 //   Lucene, Robertson:  coef TF / (TF + k1 K_D)                  coef = IDF
 //   ATIRE, BM25+:       coef TF / (TF + k1 K_D)                  coef = IDF (k1+1)
 //   BM25L:              coef c / (k1 + delta + c), c = TF / K_D  coef = IDF (k1+1) k1/(k1+delta)
+//   TF_ldp:             coef log1p(log1p(c / delta) / (1 + ln delta)), c = TF / K_D,
+//                       coef = IDF  (= IDF [ln(1 + ln(c + delta)) - ln(1 + ln delta)])
+struct ScoreConsts {
+    float k1_plus_delta;  // BM25L
+    float inv_delta;      // TF_ldp: 1 / delta
+    float inv_l0;         // TF_ldp: 1 / (1 + ln delta)
+};
+
+// S(t,D) - S0(t) of one entry: TF f, length factor a (k1 K_D, or 1 / K_D for
+// BM25L and TF_ldp), term coefficient c.  Never -0.0 (retrieval uses -0.0
+// as "untouched").
+__device__ __forceinline__ float entry_score(int variant, float f, float a, float c,
+                                             const ScoreConsts& k)
+{
+    float sc;
+    if (variant == BM25_L) {
+        const float cc = f * a;
+        sc = c * cc / (k.k1_plus_delta + cc);
+    } else if (variant == BM25_TFLDP) {
+        const float cc = f * a;
+        sc = c * log1pf(log1pf(cc * k.inv_delta) * k.inv_l0);
+    } else {
+        sc = c * f / (f + a);
+    }
+    return (sc == 0.0f) ? 0.0f : sc;
+}
+
 __global__ void k_score(const int32_t* __restrict__ run_pos, const int32_t* __restrict__ run_term,
                         const int32_t* __restrict__ indices, const uint32_t* __restrict__ d_nnz,
                         const float* __restrict__ coef, const float* __restrict__ len_factor,
-                        int variant, float k1_plus_delta, const int64_t* __restrict__ indptr,
+                        int variant, ScoreConsts kc, const int64_t* __restrict__ indptr,
                         int32_t* __restrict__ tf_out, float* __restrict__ data,
                         uint2* __restrict__ posts)
 {
@@ -493,19 +527,77 @@ __global__ void k_score(const int32_t* __restrict__ run_pos, const int32_t* __re
             const int64_t j = j0 + u * stride;
             if (j >= nnz)
                 break;
-            const float f = (float)tf[u];
-            float sc;
-            if (variant == BM25_L) {
-                const float cc = f * a[u];
-                sc = c[u] * cc / (k1_plus_delta + cc);
-            } else {
-                sc = c[u] * f / (f + a[u]);
-            }
-            sc = (sc == 0.0f) ? 0.0f : sc;  // never -0.0: retrieval uses -0.0 as "untouched"
+            const float sc = entry_score(variant, (float)tf[u], a[u], c[u], kc);
             tf_out[j] = tf[u];
             data[j] = sc;
             posts[post_start(c0[u], term[u]) + (j - c0[u])] =
                 make_uint2((uint32_t)doc[u], __float_as_uint(sc));
+        }
+    }
+}
+
+ScoreConsts score_consts(double k1, double delta)
+{
+    ScoreConsts k;
+    k.k1_plus_delta = (float)(k1 + delta);
+    k.inv_delta = delta > 0.0 ? (float)(1.0 / delta) : 0.0f;
+    k.inv_l0 = (1.0 + log(delta) > 0.0) ? (float)(1.0 / (1.0 + log(delta))) : 0.0f;
+    return k;
+}
+
+// The length factor of every document from |D| and a given Lavg (as
+// k_doc_prep computes it).
+__global__ void k_len_factor(const int32_t* __restrict__ doc_len, int64_t n_docs, int variant,
+                             double k1, double b, double lavg, float* __restrict__ len_factor)
+{
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < n_docs;
+         d += (int64_t)gridDim.x * blockDim.x) {
+        const double kd = 1.0 - b + b * (double)doc_len[d] / lavg;
+        len_factor[d] =
+            (variant == BM25_L || variant == BM25_TFLDP) ? (float)(1.0 / kd) : (float)(k1 * kd);
+    }
+}
+
+// Scores of the stored entries from their TF, |D| and the term coefficients
+// (a doc-range shard after the collection's statistics are known): the same
+// arithmetic as k_score.  Each block takes a contiguous range of entries and
+// finds the terms that range spans once; each entry then finds its term
+// inside that span.
+constexpr int kRescoreItems = 2048;  // entries per block
+__global__ void k_rescore(const int64_t* __restrict__ indptr, int32_t vocab, int64_t nnz,
+                          const int32_t* __restrict__ indices, const int32_t* __restrict__ tf,
+                          const float* __restrict__ coef, const float* __restrict__ len_factor,
+                          int variant, ScoreConsts kc, float* __restrict__ data,
+                          uint2* __restrict__ posts)
+{
+    __shared__ int32_t span[2];
+    auto term_of = [&](int64_t j, int32_t lo, int32_t hi) {  // last t in [lo, hi) with indptr[t] <= j
+        while (hi - lo > 1) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (indptr[mid] <= j)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        return lo;
+    };
+    for (int64_t j0 = (int64_t)blockIdx.x * kRescoreItems; j0 < nnz;
+         j0 += (int64_t)gridDim.x * kRescoreItems) {
+        const int64_t j1 = min(nnz, j0 + kRescoreItems);
+        __syncthreads();  // the previous range's readers of span are done
+        if (threadIdx.x == 0)
+            span[0] = term_of(j0, 0, vocab);
+        if (threadIdx.x == 32)
+            span[1] = term_of(j1 - 1, 0, vocab) + 1;
+        __syncthreads();
+        const int32_t t_lo = span[0], t_hi = span[1];
+        for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+            const int32_t t = term_of(j, t_lo, t_hi);
+            const int32_t d = indices[j];
+            const float sc = entry_score(variant, (float)tf[j], len_factor[d], coef[t], kc);
+            data[j] = sc;
+            const int64_t c0 = indptr[t];
+            posts[post_start(c0, t) + (j - c0)] = make_uint2((uint32_t)d, __float_as_uint(sc));
         }
     }
 }
@@ -680,6 +772,54 @@ int pack_posts(bm25_index* ix, cudaStream_t s)
     return BM25_OK;
 }
 
+// Rescores a built index with statistics of a larger collection (a doc-range
+// shard): IDF and S0 from df_global (device, [vocab]; NULL = the index's own
+// DF) and n_docs_global, Lavg = n_tokens_global / n_docs_global, then every
+// stored S(t,D) - S0(t) and its packed copy with the arithmetic of the build.
+int rescore_index(bm25_index* ix, const int32_t* df_global, int64_t n_docs_global,
+                  int64_t n_tokens_global, cudaStream_t s)
+{
+    DeviceInfo di;
+    BM25_TRY(device_info(&di));
+    cudaMemPool_t pool;
+    BM25_TRY(pool_for_device(di.device, &pool));
+    const int max_blocks = di.sm_count * 16;
+    const double lavg = (double)n_tokens_global / (double)n_docs_global;
+    TempSet tmp(s);
+    float* len_factor = nullptr;
+    float* coef = nullptr;
+    BM25_TRY(tmp.alloc(&len_factor, ix->n_docs, pool));
+    BM25_TRY(tmp.alloc(&coef, ix->vocab, pool));
+    {
+        ProfileScope ps_("k_len_factor", s);
+        k_len_factor<<<grid_for(ix->n_docs, 256, max_blocks), 256, 0, s>>>(
+            ix->doc_len, ix->n_docs, ix->variant, ix->k1, ix->b, lavg, len_factor);
+    }
+    count_launch();
+    BM25_LAUNCH_CHECK();
+    {
+        ProfileScope ps_("k_idf", s);
+        k_idf<<<grid_for(ix->vocab, 256, max_blocks), 256, 0, s>>>(
+            ix->indptr, ix->vocab, n_docs_global, ix->variant, ix->k1, ix->delta, df_global,
+            ix->df, ix->idf, ix->s0, coef);
+    }
+    count_launch();
+    BM25_LAUNCH_CHECK();
+    if (ix->nnz > 0) {
+        const int64_t blocks = (ix->nnz + kRescoreItems - 1) / kRescoreItems;
+        ProfileScope ps_("k_rescore", s);
+        k_rescore<<<(unsigned)std::min<int64_t>(blocks, max_blocks), 256, 0, s>>>(
+            ix->indptr, ix->vocab, ix->nnz, ix->indices, ix->tf, coef, len_factor, ix->variant,
+            score_consts(ix->k1, ix->delta), ix->data, ix->posts);
+        count_launch();
+        BM25_LAUNCH_CHECK();
+    }
+    ix->lavg = lavg;
+    ix->stat_docs = n_docs_global;
+    ix->stat_tokens = n_tokens_global;
+    return BM25_OK;
+}
+
 void free_index_arrays(bm25_index* ix, cudaStream_t s)
 {
     void* ps[] = {ix->indptr, ix->indices, ix->data, ix->tf, ix->df,
@@ -722,6 +862,8 @@ int build_index_device(const int32_t* d_tokens, int64_t n_tokens, const int64_t*
     ix->b = b;
     ix->delta = delta;
     ix->lavg = lavg;
+    ix->stat_docs = n_docs;
+    ix->stat_tokens = n_tokens;
     auto fail = [&](int code) {
         free_index_arrays(ix, s);
         delete ix;
@@ -864,7 +1006,8 @@ int build_index_device(const int32_t* d_tokens, int64_t n_tokens, const int64_t*
             {
                 ProfileScope ps_("k_idf", s);
                 k_idf<<<grid_for(vocab, 256, max_blocks), 256, 0, s>>>(
-                    ix->indptr, vocab, n_docs, variant, k1, delta, ix->df, ix->idf, ix->s0, coef);
+                    ix->indptr, vocab, n_docs, variant, k1, delta, nullptr, ix->df, ix->idf,
+                    ix->s0, coef);
             }
             {
                 ProfileScope ps_("k_pad_posts", s);
@@ -878,7 +1021,7 @@ int build_index_device(const int32_t* d_tokens, int64_t n_tokens, const int64_t*
                     ProfileScope ps_("k_score", s);
                     k_score<<<grid_for(nnz, 256, max_blocks), 256, 0, s>>>(
                         run_pos, run_term, ix->indices, d_total, coef, len_factor, variant,
-                        (float)(k1 + delta), ix->indptr, ix->tf, ix->data, ix->posts);
+                        score_consts(k1, delta), ix->indptr, ix->tf, ix->data, ix->posts);
                 }
                 count_launch();
                 BM25_LAUNCH_CHECK();

@@ -83,10 +83,10 @@ constexpr uint32_t kPostPad = 0xffffffffu;  // doc id of a padding slot (beyond 
 struct Plan {
     int accumulator = BM25_ACC_AUTO;
     int32_t tile_docs = 10240;
-    int32_t threads = 192;
+    int32_t threads = 256;
     int32_t dense_max = 4096;   // postings bound of the dense path (AUTO, L2_DENSE)
-    int32_t stage_entries = 512; // packed postings per staging buffer of the tiled kernel
-    int32_t stages = 2;          // staging buffers in its ring
+    int32_t stage_entries = 1024; // packed postings per staging buffer of the tiled kernel
+    int32_t stages = 3;           // staging buffers in its ring
 };
 // Fills zero fields of `in` from `base`; BM25_E_INVALID (nothing changed) if
 // a field is out of range.
@@ -116,6 +116,11 @@ struct bm25_index {
     uint2* posts = nullptr;      // [n_posts]
     int64_t n_posts = 0;         // nnz + vocab + 3
     int* status = nullptr;       // device status word (first error code)
+    // doc-range sharding: returned doc ids are local ids + doc_offset; IDF,
+    // S0 and Lavg come from a collection of stat_docs documents and
+    // stat_tokens tokens (this index's own counts unless rescored)
+    int64_t doc_offset = 0;
+    int64_t stat_docs = 0, stat_tokens = 0;
     bm25::Plan plan;
     bm25_workspace* default_ws = nullptr;
     std::mutex mu;
@@ -168,6 +173,8 @@ void free_index_arrays(bm25_index* ix, cudaStream_t s);
 // Fills ix->posts from indptr / indices / data (used after an import; the
 // build writes the packed entries as it scores them).  Stream-ordered.
 int pack_posts(bm25_index* ix, cudaStream_t s);
+int rescore_index(bm25_index* ix, const int32_t* df_global, int64_t n_docs_global,
+                  int64_t n_tokens_global, cudaStream_t s);
 int pool_for_current_device(cudaMemPool_t* out);
 
 // ---- retrieval (retrieve.cu) -------------------------------------------
@@ -184,6 +191,11 @@ int workspace_reserve_for(const bm25_index* ix, bm25_workspace* ws, int32_t n_qu
                           int64_t n_query_tokens, int32_t k_max, const Plan& plan,
                           cudaStream_t stream);
 void workspace_release(bm25_workspace* ws);
+// Merge of n_shards top-k rows per query ([n_shards][n_queries][k] device
+// arrays, ids -1 for empty slots) into [n_queries][k] by (score desc, id asc).
+int merge_topk_device(const int32_t* cand_ids, const float* cand_scores, int32_t n_shards,
+                      int32_t n_queries, int32_t k, int32_t* out_ids, float* out_scores,
+                      cudaStream_t s);
 // Device bytes a workspace needs for such a call (from scratch), and the
 // bytes a workspace holds now.
 int workspace_bytes_for(const bm25_index* ix, int32_t n_queries, int64_t n_query_tokens,

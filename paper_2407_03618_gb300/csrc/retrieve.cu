@@ -465,6 +465,22 @@ __device__ __forceinline__ bool warp_drain(unsigned long long* bar, uint32_t par
     return false;
 }
 
+// acc[dl] += v in shared memory when dl < wd, returning the old value;
+// -0.0 (the untouched mark) when nothing is added.  A predicated atomic, so
+// that lanes outside the tile do not split the warp.
+__device__ __forceinline__ float atom_add_if(float* acc, uint32_t dl, uint32_t wd, float v)
+{
+    float old = __uint_as_float(0x80000000u);
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.lt.u32 p, %1, %2;\n\t"
+        "@p atom.shared.add.f32 %0, [%3], %4;\n\t}"
+        : "+f"(old)
+        : "r"(dl), "r"(wd), "r"(smem_addr(acc) + dl * 4u), "f"(v)
+        : "memory");
+    return old;
+}
+
 template <int NT>
 __device__ __forceinline__ void consumer_sync()
 {
@@ -774,6 +790,9 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
     for (int32_t item = blockIdx.x; item < n_items; item += gridDim.x, par ^= 1u) {
         int32_t tile = 0, qi = 0, mode = kModeList;
         uint32_t qkp = 1, post = 0, tau = 0;
+        uint32_t d0u = 0, wdu = 0;
+        float tau_f = 0.0f;
+        bool cross = false, first_fill = true;
         // ---- scatter the item's staged postings ----------------------------------
         for (;;) {
             if (!warp_wait(&sh.full[s], round & 1u, abort_flag, wait_polls)) {
@@ -786,45 +805,59 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
                 }
                 break;
             }
-            // (clamped, as a defence: the header indexes the arrays)
-            const StageHdr hd = sh.hdr[s];
-            tile = min(max(hd.tile, 0), n_tiles - 1);
-            qi = min(max(hd.qi, 0), nq - 1);
-            qkp = min(max(hd.kp, 1u), (uint32_t)kstride);
-            post = hd.post;
-            tau = hd.tau;
-            mode = hd.mode == kModeCross ? kModeCross : kModeList;
-            const bool cross = mode == kModeCross;  // warp-uniform
-            const float tau_f = unorder_f32(tau);   // (used when tau is above the key of 0)
-            const int32_t n_e = min(max(hd.n, 0), stage_entries);
-            const bool last = hd.last != 0;
-            const uint32_t d0 = (uint32_t)tile * (uint32_t)W;
-            const uint32_t wd = (uint32_t)min((int64_t)W, n_docs - (int64_t)d0);
-            const uint2* sb = stage + (size_t)s * stage_entries;
-            // chunks of 32 entries: warp w takes chunks w, w + CW, ...
-            for (int32_t e0 = warp * 32; e0 < n_e; e0 += NT) {
-                const int32_t e = e0 + lane;
-                const uint2 pe = e < n_e ? sb[e] : make_uint2(kPostPad, 0u);
-                const uint32_t dl = pe.x - d0;
+            const StageHdr& hd = sh.hdr[s];
+            const int2 nl = *reinterpret_cast<const int2*>(&hd.n);  // entries, last fill
+            if (first_fill) {  // the item's fields, the same in all its fills
+                first_fill = false;
+                tile = hd.tile;
+                qi = hd.qi;
+                qkp = hd.kp;
+                post = hd.post;
+                tau = hd.tau;
+                mode = hd.mode;
+                cross = mode == kModeCross;  // warp-uniform
+                tau_f = unorder_f32(tau);    // (used when tau is above the key of 0)
+                d0u = (uint32_t)tile * (uint32_t)W;
+                wdu = (uint32_t)min((int64_t)W, n_docs - (int64_t)d0u);
+            }
+            // Entries come in pairs of one column (segments start on even slots
+            // and span an even number of them), so one 16-byte load gives a lane
+            // two postings of distinct documents.  Pair i is taken by lane
+            // i % 32 of warp (i / 32) % CW.
+            const int32_t n_pairs = min(max(nl.x, 0), stage_entries) >> 1;
+            const uint4* sb4 = reinterpret_cast<const uint4*>(stage + (size_t)s * stage_entries);
+            for (int32_t i0 = warp * 32; i0 < n_pairs; i0 += NT) {
+                const int32_t i = i0 + lane;
+                const uint4 pe = i < n_pairs ? sb4[i] : make_uint4(kPostPad, 0u, kPostPad, 0u);
+                const uint32_t dl0 = pe.x - d0u, dl1 = pe.z - d0u;
+                const float v0 = __uint_as_float(pe.y), v1 = __uint_as_float(pe.w);
+                // the sums before the adds (-0.0 where nothing was added)
+                const float o0 = atom_add_if(acc, dl0, wdu, v0);
+                const float o1 = atom_add_if(acc, dl1, wdu, v1);
                 // listed: a first touch (the old value is -0.0), or in the crossing
                 // mode the posting that lifts the sum to the threshold
-                bool first = false;
-                if (dl < wd) {
-                    const float v = __uint_as_float(pe.y);
-                    const float old = atomicAdd(&acc[dl], v);
-                    first = cross ? (old + v >= tau_f && !(old >= tau_f))
-                                  : __float_as_uint(old) == kUntouched;
+                bool f0, f1;
+                if (cross) {
+                    f0 = dl0 < wdu && o0 + v0 >= tau_f && !(o0 >= tau_f);
+                    f1 = dl1 < wdu && o1 + v1 >= tau_f && !(o1 >= tau_f);
+                } else {
+                    f0 = dl0 < wdu && __float_as_uint(o0) == kUntouched;
+                    f1 = dl1 < wdu && __float_as_uint(o1) == kUntouched;
                 }
-                const uint32_t b = __ballot_sync(0xffffffffu, first);
-                if (b) {
-                    const int leader = __ffs(b) - 1;
+                const uint32_t b0 = __ballot_sync(0xffffffffu, f0);
+                const uint32_t b1 = __ballot_sync(0xffffffffu, f1);
+                if (b0 | b1) {
+                    const uint32_t n0 = __popc(b0);
                     uint32_t base = 0;
-                    if (lane == leader)
-                        base = atomicAdd(&sh.tl_count[par], (uint32_t)__popc(b));
-                    base = __shfl_sync(0xffffffffu, base, leader);
-                    const uint32_t pos = base + __popc(b & ltmask);
-                    if (first && pos < tl_cap)  // beyond the cap only counted
-                        tl[pos] = (uint16_t)dl;
+                    if (lane == 0)
+                        base = atomicAdd(&sh.tl_count[par], n0 + (uint32_t)__popc(b1));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    const uint32_t p0 = base + __popc(b0 & ltmask);
+                    const uint32_t p1 = base + n0 + __popc(b1 & ltmask);
+                    if (f0 && p0 < tl_cap)  // beyond the cap only counted
+                        tl[p0] = (uint16_t)dl0;
+                    if (f1 && p1 < tl_cap)
+                        tl[p1] = (uint16_t)dl1;
                 }
             }
             __syncwarp();
@@ -834,7 +867,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
                 s = 0;
                 round++;
             }
-            if (last)
+            if (nl.y != 0)
                 break;
         }
         // every posting added, every first touch (crossing) listed; if any
@@ -1078,7 +1111,8 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
 // sorts them descending (bitonic) and writes row slots 0 .. kout-1: ids and
 // scores, -1 / -inf past the k' documents.  All threads of the block call it.
 __device__ void finish_row(u64* sel, int sz, uint32_t kp, int32_t kout, double sh,
-                           int32_t* __restrict__ ids, float* __restrict__ scores)
+                           int32_t* __restrict__ ids, float* __restrict__ scores,
+                           int32_t id_base)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int i = tid; i < sz; i += nt) {
@@ -1105,7 +1139,7 @@ __device__ void finish_row(u64* sel, int sz, uint32_t kp, int32_t kout, double s
     for (int r = tid; r < kout; r += nt) {
         const u64 key = (uint32_t)r < kp ? sel[r] : 0ull;
         if (key != 0ull) {
-            ids[r] = (int32_t)key_doc(key);
+            ids[r] = (int32_t)key_doc(key) + id_base;
             scores[r] = key_score(key);
         } else {
             ids[r] = -1;
@@ -1123,7 +1157,8 @@ __global__ void __launch_bounds__(kMergeThreads)
     k_merge(const u64* __restrict__ cand, const uint32_t* __restrict__ tcount,
             const int4* __restrict__ lrec, const uint32_t* __restrict__ ctr, int32_t n_tiles,
             int32_t kstride, int32_t kout, const double* __restrict__ shift,
-            int32_t* __restrict__ out_ids, float* __restrict__ out_scores, int32_t buf_cap)
+            int32_t* __restrict__ out_ids, float* __restrict__ out_scores, int32_t buf_cap,
+            int32_t id_base)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SelectState st;
@@ -1194,7 +1229,7 @@ __global__ void __launch_bounds__(kMergeThreads)
             sel[slot] = key;
     });
     finish_row(sel, sz, kp, kout, shift[q], out_ids + (int64_t)q * kout,
-               out_scores + (int64_t)q * kout);
+               out_scores + (int64_t)q * kout, id_base);
 }
 
 // ---- R4 -----------------------------------------------------------------------
@@ -1278,7 +1313,7 @@ __global__ void __launch_bounds__(kDenseThreads)
                  int32_t vocab, int64_t n_docs, const int32_t* __restrict__ sq,
                  uint32_t* __restrict__ ctr, float* __restrict__ slots, u64* __restrict__ lists,
                  int64_t list_cap, int32_t kstride, int32_t kout, int32_t* __restrict__ out_ids,
-                 float* __restrict__ out_scores)
+                 float* __restrict__ out_scores, int32_t id_base)
 {
     constexpr int WARPS = kDenseThreads / 32;
     constexpr int U = 8;
@@ -1450,7 +1485,7 @@ __global__ void __launch_bounds__(kDenseThreads)
                 sel[slot] = key;
         });
         finish_row(sel, sz, kp, kout, shift[q], out_ids + (int64_t)q * kout,
-                   out_scores + (int64_t)q * kout);
+                   out_scores + (int64_t)q * kout, id_base);
         // finish_row ends with global writes only; the next query's first
         // barrier orders the reuse of sel and the stage
     }
@@ -1462,6 +1497,50 @@ __global__ void k_fill_u32(uint32_t* __restrict__ p, int64_t n, uint32_t v)
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         p[i] = v;
+}
+
+// ---- merge of doc-range shards --------------------------------------------
+// Per query (block q): the shards' rows, n_shards * k slots of (global id,
+// final score), empty slots id -1; selects the k' = min(k, valid slots) best
+// by (score desc, id asc) and writes the sorted row (then -1 / -inf).  The
+// scores are final (shift included), so no shift is added.
+__global__ void __launch_bounds__(kMergeThreads)
+    k_merge_shards(const int32_t* __restrict__ cand_ids, const float* __restrict__ cand_scores,
+                   int32_t n_shards, int32_t nq, int32_t k, int32_t* __restrict__ out_ids,
+                   float* __restrict__ out_scores)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SelectState st;
+    const int q = blockIdx.x;
+    const uint32_t n_index = (uint32_t)n_shards * (uint32_t)k;
+    auto slot = [&](uint32_t i) -> int64_t {  // shard i / k, rank i % k of query q
+        return ((int64_t)(i / (uint32_t)k) * nq + q) * k + (i % (uint32_t)k);
+    };
+    auto get = [&](uint32_t i) -> u64 {
+        const int64_t p = slot(i);
+        const int32_t id = cand_ids[p];
+        return id >= 0 ? make_key(cand_scores[p], (uint32_t)id) : 0ull;
+    };
+    uint32_t valid = 0;
+    for (uint32_t i = threadIdx.x; i < n_index; i += blockDim.x)
+        valid += cand_ids[slot(i)] >= 0;
+    uint32_t n_valid;
+    block_exclusive_sum(valid, st.red, &n_valid);
+    const uint32_t kp = min(n_valid, (uint32_t)k);
+    int sz = 1;
+    while ((uint32_t)sz < kp)
+        sz <<= 1;
+    u64* sel = reinterpret_cast<u64*>(smem);
+    for (int i = threadIdx.x; i < sz; i += blockDim.x)
+        sel[i] = 0ull;
+    if (threadIdx.x == 0)
+        st.ctr = 0;
+    __syncthreads();
+    block_select_idx<true>(st, n_index, n_valid, kp, 0, 0ull, get, [&](u64 key, uint32_t s) {
+        if (s < kp)
+            sel[s] = key;
+    });
+    finish_row(sel, sz, kp, k, 0.0, out_ids + (int64_t)q * k, out_scores + (int64_t)q * k, 0);
 }
 
 constexpr int64_t kCandBudget = int64_t(2) << 30;   // bytes of tile candidates per sub-batch
@@ -1599,6 +1678,27 @@ int reserve(const bm25_index* ix, bm25_workspace* ws, const Geometry& g, int64_t
 }
 
 }  // namespace
+
+int merge_topk_device(const int32_t* cand_ids, const float* cand_scores, int32_t n_shards,
+                      int32_t nq, int32_t k, int32_t* out_ids, float* out_scores, cudaStream_t s)
+{
+    if (nq == 0)
+        return BM25_OK;
+    int sz = 1;
+    while (sz < k)
+        sz <<= 1;
+    const size_t smem = (size_t)sz * sizeof(u64);
+    BM25_CUDA_TRY(cudaFuncSetAttribute(k_merge_shards, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    {
+        ProfileScope ps_("k_merge_shards", s);
+        k_merge_shards<<<nq, kMergeThreads, smem, s>>>(cand_ids, cand_scores, n_shards, nq, k,
+                                                       out_ids, out_scores);
+    }
+    count_launch();
+    BM25_LAUNCH_CHECK();
+    return BM25_OK;
+}
 
 int32_t tile_width(const Plan& plan, int64_t n_docs)
 {
@@ -1777,7 +1877,7 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
             ProfileScope ps_("k_merge", s);
             k_merge<<<nb, kMergeThreads, msmem, s>>>(ws->cand, ws->tcount, ws->lrec, ws->ctr,
                                                      n_tiles, kstride, kmax, ws->shift, ids,
-                                                     scores, buf_cap);
+                                                     scores, buf_cap, (int32_t)ix->doc_offset);
         }
         count_launch();
         BM25_LAUNCH_CHECK();
@@ -1787,7 +1887,7 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
             k_dense_topk<<<g4, kDenseThreads, g.dense_smem, s>>>(
                 q_tokens, n_tok, qo, ws->qkp, ws->shift, ix->indptr, ix->indices, ix->data,
                 ix->vocab, N, ws->sq, ws->ctr, ws->dslots, ws->dlists, g.list_cap, kstride, kmax,
-                ids, scores);
+                ids, scores, (int32_t)ix->doc_offset);
             count_launch();
             BM25_LAUNCH_CHECK();
         }

@@ -134,15 +134,28 @@ extern "C" int bm25_autotune(bm25_index* ix, const int32_t* query_tokens, int64_
         p.accumulator = BM25_ACC_SMEM_TILED;
         p.tile_docs = W;
         p.threads = def.threads;
+        p.stage_entries = def.stage_entries;
+        p.stages = def.stages;
         trial(p);
     }
     // 1b. the consumer threads per CTA at that width
     const Plan width = cur;
-    for (int32_t th : {128, 192, 256}) {
+    for (int32_t th : {128, 192, 256, 512}) {
         if (th == def.threads)
             continue;  // tried in step 1
         Plan p = width;
         p.threads = th;
+        trial(p);
+    }
+    // 1c. the staging ring (buffer size x count) with those
+    const Plan threads = cur;
+    for (auto ring : {std::make_pair(512, 2), std::make_pair(1024, 2), std::make_pair(1024, 3),
+                      std::make_pair(2048, 2)}) {
+        if (ring.first == threads.stage_entries && ring.second == threads.stages)
+            continue;  // the ring the earlier steps ran with
+        Plan p = threads;
+        p.stage_entries = ring.first;
+        p.stages = ring.second;
         trial(p);
     }
     // 2. the dense-path bound with that tile width

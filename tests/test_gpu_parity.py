@@ -110,12 +110,39 @@ def test_build_parity_random_small(torch_dev, seed):
     rng = np.random.default_rng(1000 + seed)
     c = synth.random_tiny_corpus(rng, max_docs=int(rng.integers(1, 400)),
                                  max_vocab=int(rng.integers(1, 3000)), max_len=40)
-    variant = VARIANTS[seed % 5]
+    variant = (VARIANTS + ["tfldp"])[seed % 6]
     k1, b, d = float(rng.uniform(0.3, 2.0)), float(rng.uniform(0, 1)), float(rng.uniform(0, 1))
+    if variant == "tfldp":
+        d = float(rng.uniform(0.38, 2.0))  # delta > 1/e
     ix = _build(torch_dev, c, variant, k1, b, d)
     orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.VARIANTS[variant], k1, b, d)
     _check_structure(ix, orc, k1, b, d)
     ix.close()
+
+
+@pytest.mark.parametrize("delta", [0.5, 1.0, 0.5314, 2.0])
+def test_tfldp_build_and_retrieve(torch_dev, delta):
+    """TF_{l o delta o p} x IDF (Sec. 2.1's third shiftable model) on the tiny
+    workload: negative S0 (delta = 0.5), S0 = IDF (delta = 1), S0 near 0
+    (delta = e^(1/e - 1) ~ 0.5314), a large lower bound (delta = 2); every
+    accumulator plan, k = 1, 10, 100."""
+    w = synth.WORKLOADS["tiny"]
+    c, q = w.corpus(), w.queries()
+    ix = _build(torch_dev, c, "tfldp", 1.5, 0.75, delta)
+    orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.TFLDP, 1.5, 0.75, delta)
+    _check_structure(ix, orc, 1.5, 0.75, delta)
+    for name in PLANS:
+        _plan(ix, name)
+        for k in (1, 10, 100):
+            _check_retrieval(torch_dev, ix, orc, q, k, where=f"tfldp d={delta} {name} k={k}")
+    ix.close()
+
+
+def test_tfldp_rejects_small_delta(torch_dev):
+    from paper_2407_03618_gb300 import bm25
+    c = synth.Corpus(np.array([0, 1], np.int32), np.array([0, 2], np.int64), 2)
+    with pytest.raises(bm25.BM25Error):
+        _build(torch_dev, c, "tfldp", 1.2, 0.75, 0.3)  # 1 + ln 0.3 < 0
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
