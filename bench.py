@@ -49,11 +49,16 @@ def parse():
                    help="queries per step of --impl reference")
     p.add_argument("--queries", type=int, default=0,
                    help="use only the first N queries of the batch (small profiler cases)")
+    p.add_argument("--docs", type=int, default=0,
+                   help="a corpus of N documents of the workload's law instead of its own size "
+                        "(small profiler cases; the workload is then named <name>:<N>docs)")
     p.add_argument("--no-extras", action="store_true",
                    help="only the timed steps (used for profiler runs)")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the library's default plan instead of autotuning it")
     p.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    p.add_argument("--no-zipf1m", action="store_true",
+                   help="skip the step measured on the 1M-document workload")
     return p.parse_args()
 
 
@@ -192,6 +197,16 @@ def oracle_rate(corpus, queries, variant, k, n_sample, threads, params):
                                    "queries": n1}}
 
 
+def workload_of(args):
+    """The workload to run: BASELINE-shaped as named, or (--docs N) the same
+    laws over N documents for a small profiler case."""
+    import dataclasses
+    w = synth.WORKLOADS[args.workload]
+    if args.docs:
+        w = dataclasses.replace(w, name=f"{w.name}:{args.docs}docs", n_docs=args.docs)
+    return w
+
+
 def bench_config(args, w, n_queries: int, world: int) -> dict:
     """The `config` both arms print: the workload, the variant and k, and what
     one step of the GPU arm runs."""
@@ -211,7 +226,7 @@ def reference_arm(args):
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
-    w = synth.WORKLOADS[args.workload]
+    w = workload_of(args)
     corpus = w.corpus()
     queries = rank_batch(w, 0, args.queries)
     threads = os.cpu_count() or 1
@@ -321,7 +336,7 @@ def main():
     __graft_entry__.build()
     from paper_2407_03618_gb300 import bm25
 
-    w = synth.WORKLOADS[args.workload]
+    w = workload_of(args)
     prm = w.params
     corpus = w.corpus()
     queries = rank_batch(w, rank, args.queries)  # each rank its own batch (weak scaling)
@@ -438,7 +453,7 @@ def extras(args, line, bm25, corpus, queries, tok, off, qt, qo, ids, sc, dev, pr
         ix.set_plan(**plan)
     used = ix.get_plan()
     info = ix.info()
-    ex_indptr = ix.export()["indptr"]
+    ex_indptr = ix.export(["indptr"])["indptr"]
     df = np.diff(ex_indptr)
     qlen = np.diff(queries.offsets)
     postings = int(df[queries.tokens].sum())
@@ -609,11 +624,65 @@ def extras(args, line, bm25, corpus, queries, tok, off, qt, qo, ids, sc, dev, pr
         line["serving"] = serving(args, bm25, corpus, queries, tok, off, dev, w, plan,
                                   line["plain_path"])
 
+    if w.name != "zipf-1m" and not args.no_zipf1m:
+        line["zipf1m"] = other_workload_step(args, bm25, dev, "1m", hbm_peak)
+
     # CPU oracle on a bounded sample (rank 0, N = 1 only)
     if line["n_gpus"] == 1:
         _, cpu = oracle_rate(corpus, queries, args.variant, k, args.cpu_sample_queries,
                              os.cpu_count() or 1, prm)
         line["cpu_baseline"] = cpu
+
+
+def other_workload_step(args, bm25, dev, name, hbm_peak):
+    """The same step (build + batched retrieval of the whole batch at k) on
+    another workload, its plan autotuned on its own batch."""
+    import torch
+    w = synth.WORKLOADS[name]
+    prm = w.params
+    c, q = w.corpus(), w.queries()
+    tok = torch.from_numpy(c.tokens).to(dev)
+    off = torch.from_numpy(c.doc_offsets).to(dev)
+    qt = torch.from_numpy(q.tokens).to(dev)
+    qo = torch.from_numpy(q.offsets).to(dev)
+    k = args.k
+    ix = bm25.Index.build(tok, off, c.vocab, args.variant, prm["k1"], prm["b"], prm["delta"])
+    plan = ix.autotune(qt, qo, k)[0]
+    ws = bm25.Workspace(ix, q.n_queries, qt.numel(), k)
+    ws.reserve(ix, q.n_queries, qt.numel(), k, plan=plan)
+    df = np.diff(ix.export(["indptr"])["indptr"])
+    ix.close()
+    out = (torch.empty((q.n_queries, k), dtype=torch.int32, device=dev),
+           torch.empty((q.n_queries, k), dtype=torch.float32, device=dev))
+
+    def step():
+        i2 = bm25.Index.build(tok, off, c.vocab, args.variant, prm["k1"], prm["b"], prm["delta"])
+        i2.retrieve(qt, qo, k, out=out, workspace=ws, plan=plan)
+        i2.close()
+
+    for _ in range(3):
+        step()
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    bm25.profile_begin()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 10
+    a.record(stream)
+    for _ in range(n):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    prof = bm25.profile_end()
+    ms = a.elapsed_time(b) / n
+    postings = int(df[q.tokens].sum())
+    res = {"workload": w.name, "queries_per_step": q.n_queries, "ms_per_step": ms,
+           "value": q.n_queries / (ms / 1e3), "unit": "queries/s", "plan": plan,
+           "postings_per_query": postings / q.n_queries}
+    if "k_tile_staged" in prof:
+        cnt, t = prof["k_tile_staged"]
+        res["k_tile_staged_ms"] = t / cnt
+    ws.close()
+    return res
 
 
 def serving(args, bm25, corpus, queries, tok, off, dev, w, plan, plain):

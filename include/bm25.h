@@ -98,7 +98,7 @@ enum bm25_accumulator {
 typedef struct bm25_plan {
     int32_t accumulator;        /* enum bm25_accumulator */
     int32_t tile_docs;          /* doc-tile width: a multiple of 1024 in [1024, 49152]
-                                   (default 10240) */
+                                   (default 6144) */
     int32_t block_threads;      /* consumer threads per CTA of the tiled kernel: 128, 192,
                                    256 or 512 (default 256; one producer warp is added) */
     int32_t dense_max_postings; /* dense-path bound for AUTO / L2_DENSE, in [0, 2^22]
@@ -270,12 +270,12 @@ int bm25_retrieve_batch(const bm25_index* index, bm25_workspace* ws,
                         float* out_scores, const bm25_plan* plan, void* cuda_stream);
 
 /* Retrieval that allocates nothing, for callers that cannot call cudaMalloc
- * at this point: code running where a device allocation would synchronise
- * the device or is not allowed (a host callback, a real-time serving loop
- * with a fixed memory budget, a process whose device memory is owned by
- * another allocator).  The paper has no counterpart; it is an operational
- * variant of bm25_retrieve (same arguments, same results up to the order of
- * FP32 additions).
+ * at this point: a real-time serving loop with a fixed memory budget (an
+ * allocation may synchronise the device), a process whose device memory is
+ * owned by another allocator.  It still calls the CUDA runtime, so it must
+ * not be called from a CUDA host function or stream callback.  The paper has
+ * no counterpart; it is an operational variant of bm25_retrieve (same
+ * arguments, same results up to the order of FP32 additions).
  *
  * Its scratch is one file-scope device array of 16 MiB that every GPU
  * loading the library holds until the process exits.  Every query takes the
@@ -284,9 +284,10 @@ int bm25_retrieve_batch(const bm25_index* index, bm25_workspace* ws,
  * doc tile and k' candidate slot) exceeds 16 MiB fails with BM25_E_INVALID;
  * split it.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress), so
- * make that first call before any stream capture.  Every call shares the
- * array: calls that overlap on the GPU (other streams, other threads) race
- * and must be serialised by the caller. */
+ * make that first call before any stream capture.  That address is kept, so
+ * the library must not be used across a cudaDeviceReset.  Every call shares
+ * the array: calls that overlap on the GPU (other streams, other threads)
+ * race and must be serialised by the caller. */
 int bm25_retrieve_noalloc(const bm25_index* index, const int32_t* query_tokens,
                           int64_t n_query_tokens, const int64_t* query_offsets,
                           int32_t n_queries, int32_t k, int32_t* out_ids,
@@ -318,6 +319,32 @@ int bm25_autotune(bm25_index* index, const int32_t* query_tokens, int64_t n_quer
                   const int64_t* query_offsets, int32_t n_queries, int32_t k,
                   void* cuda_stream, bm25_plan* best, double* best_ms, bm25_plan* tried,
                   double* tried_ms, int32_t tried_cap, int32_t* n_tried);
+
+/* ------------------------------------------------------ query-time scoring */
+
+/* The paper's index stores S(t,D) for fixed k1, b (and delta); its
+ * conclusion notes that Rank-BM25, which scores lazily, can change k1 at
+ * inference.  These two calls give an index that: the postings are kept a
+ * second time with TF and |D| in place of the score, and retrieval computes
+ * S(t,D) - S0(t) from them with the call's k1, b, delta (same formulas,
+ * same FP32 arithmetic per entry as the build, K_D in FP32), and adds
+ * sum_i S0(q_i) at those parameters.  IDF does not depend on k1, b, delta
+ * and is the index's.  With the index's own parameters the results equal
+ * bm25_retrieve's up to FP32 rounding.
+ *
+ * bm25_index_enable_lazy builds the lazy postings (nnz + vocab + 3 pairs;
+ * TF and |D| in 16 bits each when every TF and |D| fits, else TF in 32 bits
+ * and |D| read from the document lengths).  Synchronous; idempotent.
+ *
+ * bm25_retrieve_lazy: arguments and results as bm25_retrieve, plus the
+ * query-time k1 >= 0, 0 <= b <= 1, delta >= 0 (BM25L: k1 + delta > 0;
+ * TFLDP: delta > 1/e).  Every query takes the doc-tiled path.  Uses the
+ * index's default workspace.  BM25_E_INVALID without enable_lazy. */
+int bm25_index_enable_lazy(bm25_index* index, void* cuda_stream);
+int bm25_retrieve_lazy(const bm25_index* index, const int32_t* query_tokens,
+                       int64_t n_query_tokens, const int64_t* query_offsets, int32_t n_queries,
+                       int32_t k, double k1, double b, double delta, int32_t* out_ids,
+                       float* out_scores, void* cuda_stream);
 
 /* ------------------------------------------------------- doc-range shards */
 

@@ -152,14 +152,22 @@ def build(tokens, doc_offsets, vocab: int, variant: int = LUCENE, k1: float = 1.
                        indices[:nnz], csc_tf[:nnz], csc_delta[:nnz])
 
 
-def score_all(ix: OracleIndex, query, with_abs: bool = False):
+def _params(ix: OracleIndex, k1, b, delta):
+    """The index's k1, b, delta, or the ones a query passes (query-time
+    scoring: the lazy oracle evaluates S from TF anyway)."""
+    return (ix.k1 if k1 is None else float(k1), ix.b if b is None else float(b),
+            ix.delta if delta is None else float(delta))
+
+
+def score_all(ix: OracleIndex, query, with_abs: bool = False, k1=None, b=None, delta=None):
     """Lazy B(Q,D) for every document, FP64.  With with_abs, also returns
-    sum_i |S(q_i, D)| per document."""
+    sum_i |S(q_i, D)| per document.  k1 / b / delta override the index's."""
     q = np.ascontiguousarray(query, dtype=np.int32)
     out = np.zeros(ix.n_docs, np.float64)
     ab = np.zeros(ix.n_docs, np.float64) if with_abs else None
-    _load().oracle_score_all(_p(q), q.shape[0], ix.n_docs, ix.vocab, ix.variant, ix.k1,
-                             ix.b, ix.delta, _p(ix.doc_len), ix.lavg, _p(ix.pair_start),
+    pk1, pb, pd = _params(ix, k1, b, delta)
+    _load().oracle_score_all(_p(q), q.shape[0], ix.n_docs, ix.vocab, ix.variant, pk1,
+                             pb, pd, _p(ix.doc_len), ix.lavg, _p(ix.pair_start),
                              _p(ix.pair_term), _p(ix.pair_tf), _p(ix.idf), _p(out),
                              _p(ab) if with_abs else None)
     return (out, ab) if with_abs else out
@@ -173,8 +181,10 @@ def rank(scores: np.ndarray) -> np.ndarray:
     return order
 
 
-def topk(ix: OracleIndex, q_tokens, q_offsets, k: int, n_threads: int = 1):
-    """Top-k (ids int64, scores f64) for a batch of queries, lazy + full sort."""
+def topk(ix: OracleIndex, q_tokens, q_offsets, k: int, n_threads: int = 1, k1=None, b=None,
+         delta=None):
+    """Top-k (ids int64, scores f64) for a batch of queries, lazy + full sort.
+    k1 / b / delta override the index's."""
     qt = np.ascontiguousarray(q_tokens, dtype=np.int32)
     qo = np.ascontiguousarray(q_offsets, dtype=np.int64)
     nq = qo.shape[0] - 1
@@ -182,8 +192,9 @@ def topk(ix: OracleIndex, q_tokens, q_offsets, k: int, n_threads: int = 1):
     sc = np.zeros((max(nq, 1), k), np.float64)
     if qt.shape[0] == 0:
         qt = np.zeros(1, np.int32)
-    _load().oracle_topk(_p(qt), _p(qo), nq, k, ix.n_docs, ix.vocab, ix.variant, ix.k1,
-                        ix.b, ix.delta, _p(ix.doc_len), ix.lavg, _p(ix.pair_start),
+    pk1, pb, pd = _params(ix, k1, b, delta)
+    _load().oracle_topk(_p(qt), _p(qo), nq, k, ix.n_docs, ix.vocab, ix.variant, pk1,
+                        pb, pd, _p(ix.doc_len), ix.lavg, _p(ix.pair_start),
                         _p(ix.pair_term), _p(ix.pair_tf), _p(ix.idf), n_threads,
                         _p(ids), _p(sc))
     return ids[:nq], sc[:nq]

@@ -115,6 +115,8 @@ def load(path: str | None = None):
         "bm25_profile_end": (cint, []),
         "bm25_profile_count": (cint, []),
         "bm25_profile_get": (cint, [cint, ctypes.c_char_p, cint, P, P]),
+        "bm25_index_enable_lazy": (cint, [P, P]),
+        "bm25_retrieve_lazy": (cint, [P, P, i64, P, i32, i32, f64, f64, f64, P, P, P]),
         "bm25_index_df_device": (cint, [P, P, P]),
         "bm25_index_rescore": (cint, [P, P, i64, i64, i64, P]),
         "bm25_index_shard_info": (cint, [P, P, P, P]),
@@ -306,16 +308,17 @@ class Index:
                 "variant": var.value, "k1": k1.value, "b": b.value, "delta": d.value,
                 "lavg": la.value}
 
-    def export(self) -> dict:
+    def export(self, fields=None) -> dict:
+        """The index's arrays in host memory (all of them, or the named ones)."""
         inf = self.info()
         V, N, Z = inf["vocab"], inf["n_docs"], inf["nnz"]
-        out = {"indptr": np.zeros(V + 1, np.int64), "indices": np.zeros(Z, np.int32),
-               "data": np.zeros(Z, np.float32), "tf": np.zeros(Z, np.int32),
-               "df": np.zeros(V, np.int32), "doc_len": np.zeros(N, np.int32),
-               "idf": np.zeros(V, np.float64), "s0": np.zeros(V, np.float64)}
-        _check(load().bm25_index_export(self.handle, *[_ptr(out[k]) for k in
-                                                       ("indptr", "indices", "data", "tf", "df",
-                                                        "doc_len", "idf", "s0")]))
+        shapes = {"indptr": (V + 1, np.int64), "indices": (Z, np.int32), "data": (Z, np.float32),
+                  "tf": (Z, np.int32), "df": (V, np.int32), "doc_len": (N, np.int32),
+                  "idf": (V, np.float64), "s0": (V, np.float64)}
+        names = list(shapes) if fields is None else list(fields)
+        out = {k: np.zeros(shapes[k][0], shapes[k][1]) for k in names}
+        _check(load().bm25_index_export(self.handle, *[_ptr(out[k]) if k in out else None
+                                                       for k in shapes]))
         out.update(inf)
         return out
 
@@ -346,6 +349,29 @@ class Index:
         p = Plan()
         _check(load().bm25_index_get_plan(self.handle, ctypes.byref(p)))
         return p.as_dict()
+
+    def enable_lazy(self, stream=None):
+        """Add the lazy postings (doc id with TF and |D|) that query-time
+        scoring reads."""
+        _check(load().bm25_index_enable_lazy(self.handle, _stream(stream)))
+
+    def retrieve_lazy(self, q_tokens, q_offsets, k: int, k1: float, b: float, delta: float = 0.5,
+                      out=None, stream=None):
+        """Top k with S(t,D) computed at query time with k1, b, delta (CUDA
+        tensors as in retrieve)."""
+        import torch
+        qt = _dev_tensor(q_tokens, torch.int32)
+        qo = _dev_tensor(q_offsets, torch.int64)
+        nq = qo.numel() - 1
+        if out is None:
+            ids = torch.empty((nq, max(k, 0)), dtype=torch.int32, device=qo.device)
+            sc = torch.empty((nq, max(k, 0)), dtype=torch.float32, device=qo.device)
+        else:
+            ids, sc = out
+        _check(load().bm25_retrieve_lazy(self.handle, qt.data_ptr(), qt.numel(), qo.data_ptr(),
+                                         nq, k, float(k1), float(b), float(delta), ids.data_ptr(),
+                                         sc.data_ptr(), _stream(stream)))
+        return ids, sc
 
     def df_device(self, out=None, stream=None):
         """The index's DF as a CUDA int32 tensor [vocab]."""

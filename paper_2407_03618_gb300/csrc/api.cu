@@ -69,6 +69,28 @@ int device_info(DeviceInfo* out)
     return BM25_OK;
 }
 
+// Host-side checks shared by every retrieval entry point.
+int check_retrieve_args(const bm25_index* ix, int64_t n_tok, int32_t nq, int32_t k)
+{
+    if (!ix)
+        return set_error(BM25_E_INVALID, "index is NULL");
+    if (nq < 0 || n_tok < 0 || n_tok > (int64_t)INT32_MAX)
+        return set_error(BM25_E_INVALID, "bad batch size (n_queries %d, n_query_tokens %lld)", nq,
+                         (long long)n_tok);
+    if (k < 1)
+        return set_error(BM25_E_INVALID, "k = %d must be >= 1", k);
+    int64_t kp = k < ix->n_docs ? k : ix->n_docs;
+    if (kp > BM25_MAX_K)
+        return set_error(BM25_E_INVALID, "min(k, n_docs) = %lld exceeds BM25_MAX_K = %d",
+                         (long long)kp, BM25_MAX_K);
+    int dev = 0;
+    BM25_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != ix->device)
+        return set_error(BM25_E_INVALID, "current device %d is not the index's device %d", dev,
+                         ix->device);
+    return BM25_OK;
+}
+
 namespace {
 
 int check_build_args(int64_t n_tokens, int64_t n_docs, int32_t vocab, int variant, double k1,
@@ -93,27 +115,6 @@ int check_build_args(int64_t n_tokens, int64_t n_docs, int32_t vocab, int varian
         return set_error(BM25_E_INVALID, "BM25L needs k1 + delta > 0");
     if (variant == BM25_TFLDP && !(1.0 + log(delta) > 0.0))
         return set_error(BM25_E_INVALID, "TFLDP needs delta > 1/e (got %g)", delta);
-    return BM25_OK;
-}
-
-int check_retrieve_args(const bm25_index* ix, int64_t n_tok, int32_t nq, int32_t k)
-{
-    if (!ix)
-        return set_error(BM25_E_INVALID, "index is NULL");
-    if (nq < 0 || n_tok < 0 || n_tok > (int64_t)INT32_MAX)
-        return set_error(BM25_E_INVALID, "bad batch size (n_queries %d, n_query_tokens %lld)", nq,
-                         (long long)n_tok);
-    if (k < 1)
-        return set_error(BM25_E_INVALID, "k = %d must be >= 1", k);
-    int64_t kp = k < ix->n_docs ? k : ix->n_docs;
-    if (kp > BM25_MAX_K)
-        return set_error(BM25_E_INVALID, "min(k, n_docs) = %lld exceeds BM25_MAX_K = %d",
-                         (long long)kp, BM25_MAX_K);
-    int dev = 0;
-    BM25_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev != ix->device)
-        return set_error(BM25_E_INVALID, "current device %d is not the index's device %d", dev,
-                         ix->device);
     return BM25_OK;
 }
 
@@ -494,6 +495,46 @@ int bm25_retrieve(const bm25_index* ix, const int32_t* query_tokens, int64_t n_q
     return retrieve_device(ix, ws, query_tokens, query_offsets, n_queries, n_query_tokens,
                            nullptr, k, out_ids, out_scores, plan_of(ix),
                            (cudaStream_t)cuda_stream);
+}
+
+int bm25_index_enable_lazy(bm25_index* ix, void* cuda_stream)
+{
+    clear_error();
+    if (!ix)
+        return set_error(BM25_E_INVALID, "index is NULL");
+    int dev = 0;
+    BM25_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != ix->device)
+        return set_error(BM25_E_INVALID, "current device %d is not the index's device %d", dev,
+                         ix->device);
+    std::lock_guard<std::mutex> g(ix->mu);
+    return enable_lazy(ix, (cudaStream_t)cuda_stream);
+}
+
+int bm25_retrieve_lazy(const bm25_index* ix, const int32_t* query_tokens, int64_t n_query_tokens,
+                       const int64_t* query_offsets, int32_t n_queries, int32_t k, double k1,
+                       double b, double delta, int32_t* out_ids, float* out_scores,
+                       void* cuda_stream)
+{
+    clear_error();
+    BM25_TRY(check_retrieve_args(ix, n_query_tokens, n_queries, k));
+    if (!ix->posts_lazy)
+        return set_error(BM25_E_INVALID, "the index has no lazy postings: call "
+                         "bm25_index_enable_lazy first");
+    if (!(k1 >= 0.0) || !(b >= 0.0 && b <= 1.0) || !(delta >= 0.0))
+        return set_error(BM25_E_INVALID, "need k1 >= 0, 0 <= b <= 1, delta >= 0 (got %g, %g, %g)",
+                         k1, b, delta);
+    if (ix->variant == BM25_L && !(k1 + delta > 0.0))
+        return set_error(BM25_E_INVALID, "BM25L needs k1 + delta > 0");
+    if (ix->variant == BM25_TFLDP && !(1.0 + log(delta) > 0.0))
+        return set_error(BM25_E_INVALID, "TFLDP needs delta > 1/e (got %g)", delta);
+    bm25_workspace* ws = nullptr;
+    BM25_TRY(default_ws(ix, &ws));
+    Plan p = plan_of(ix);
+    p.accumulator = BM25_ACC_SMEM_TILED;
+    const QueryParams qp{k1, b, delta};
+    return retrieve_device(ix, ws, query_tokens, query_offsets, n_queries, n_query_tokens,
+                           nullptr, k, out_ids, out_scores, p, (cudaStream_t)cuda_stream, &qp);
 }
 
 int bm25_retrieve_ws(const bm25_index* ix, bm25_workspace* ws, const int32_t* query_tokens,

@@ -66,9 +66,7 @@ __global__ void k_doc_prep(const int64_t* __restrict__ off, int64_t n_docs, int6
         if (has) {
             const int64_t len = bad ? 0 : hi - lo;
             doc_len[d] = (int32_t)len;
-            const double kd = 1.0 - b + b * (double)len / lavg;
-            len_factor[d] =
-                (variant == BM25_L || variant == BM25_TFLDP) ? (float)(1.0 / kd) : (float)(k1 * kd);
+            len_factor[d] = length_factor(variant, k1, b, (double)len, lavg);
         }
         if (__any_sync(0xffffffffu, bad))
             continue;  // the build fails; only in-range writes happen above
@@ -443,17 +441,8 @@ __global__ void k_idf(const int64_t* __restrict__ indptr, int32_t vocab, int64_t
         const int64_t df_own = indptr[t + 1] - indptr[t];
         const int64_t df = df_global ? (int64_t)df_global[t] : df_own;
         double w = idf_of(variant, (double)n_docs, (double)df);
-        double s0 = 0.0, c = w;
-        if (variant == BM25_ATIRE || variant == BM25_PLUS)
-            c = w * (k1 + 1.0);
-        if (variant == BM25_L) {
-            s0 = w * (k1 + 1.0) * delta / (k1 + delta);
-            c = w * (k1 + 1.0) * k1 / (k1 + delta);
-        } else if (variant == BM25_PLUS) {
-            s0 = w * delta;
-        } else if (variant == BM25_TFLDP) {
-            s0 = w * (1.0 + log(1.0 + log(delta)));
-        }
+        double s0, c;
+        term_coef(variant, w, k1, delta, &c, &s0);
         df_out[t] = (int32_t)df_own;
         idf_out[t] = w;
         s0_out[t] = s0;
@@ -462,37 +451,8 @@ __global__ void k_idf(const int64_t* __restrict__ indptr, int32_t vocab, int64_t
 }
 
 // ---- K7: scores ----------------------------------------------------------
-// FP32 per entry, in forms free of cancellation (S - S0 written out):
-//   Lucene, Robertson:  coef TF / (TF + k1 K_D)                  coef = IDF
-//   ATIRE, BM25+:       coef TF / (TF + k1 K_D)                  coef = IDF (k1+1)
-//   BM25L:              coef c / (k1 + delta + c), c = TF / K_D  coef = IDF (k1+1) k1/(k1+delta)
-//   TF_ldp:             coef log1p(log1p(c / delta) / (1 + ln delta)), c = TF / K_D,
-//                       coef = IDF  (= IDF [ln(1 + ln(c + delta)) - ln(1 + ln delta)])
-struct ScoreConsts {
-    float k1_plus_delta;  // BM25L
-    float inv_delta;      // TF_ldp: 1 / delta
-    float inv_l0;         // TF_ldp: 1 / (1 + ln delta)
-};
-
-// S(t,D) - S0(t) of one entry: TF f, length factor a (k1 K_D, or 1 / K_D for
-// BM25L and TF_ldp), term coefficient c.  Never -0.0 (retrieval uses -0.0
-// as "untouched").
-__device__ __forceinline__ float entry_score(int variant, float f, float a, float c,
-                                             const ScoreConsts& k)
-{
-    float sc;
-    if (variant == BM25_L) {
-        const float cc = f * a;
-        sc = c * cc / (k.k1_plus_delta + cc);
-    } else if (variant == BM25_TFLDP) {
-        const float cc = f * a;
-        sc = c * log1pf(log1pf(cc * k.inv_delta) * k.inv_l0);
-    } else {
-        sc = c * f / (f + a);
-    }
-    return (sc == 0.0f) ? 0.0f : sc;
-}
-
+// FP32 S(t,D) - S0(t) per entry (entry_score in device.cuh), written to the
+// CSC and to the packed copy staged retrieval reads.
 __global__ void k_score(const int32_t* __restrict__ run_pos, const int32_t* __restrict__ run_term,
                         const int32_t* __restrict__ indices, const uint32_t* __restrict__ d_nnz,
                         const float* __restrict__ coef, const float* __restrict__ len_factor,
@@ -536,15 +496,6 @@ __global__ void k_score(const int32_t* __restrict__ run_pos, const int32_t* __re
     }
 }
 
-ScoreConsts score_consts(double k1, double delta)
-{
-    ScoreConsts k;
-    k.k1_plus_delta = (float)(k1 + delta);
-    k.inv_delta = delta > 0.0 ? (float)(1.0 / delta) : 0.0f;
-    k.inv_l0 = (1.0 + log(delta) > 0.0) ? (float)(1.0 / (1.0 + log(delta))) : 0.0f;
-    return k;
-}
-
 // The length factor of every document from |D| and a given Lavg (as
 // k_doc_prep computes it).
 __global__ void k_len_factor(const int32_t* __restrict__ doc_len, int64_t n_docs, int variant,
@@ -552,9 +503,7 @@ __global__ void k_len_factor(const int32_t* __restrict__ doc_len, int64_t n_docs
 {
     for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < n_docs;
          d += (int64_t)gridDim.x * blockDim.x) {
-        const double kd = 1.0 - b + b * (double)doc_len[d] / lavg;
-        len_factor[d] =
-            (variant == BM25_L || variant == BM25_TFLDP) ? (float)(1.0 / kd) : (float)(k1 * kd);
+        len_factor[d] = length_factor(variant, k1, b, (double)doc_len[d], lavg);
     }
 }
 
@@ -820,8 +769,110 @@ int rescore_index(bm25_index* ix, const int32_t* df_global, int64_t n_docs_globa
     return BM25_OK;
 }
 
+namespace {
+
+// The largest TF and |D| of an index (atomicMax into mx[0], mx[1]).
+__global__ void k_max_tf_len(const int32_t* __restrict__ tf, int64_t nnz,
+                             const int32_t* __restrict__ doc_len, int64_t n_docs, int32_t* mx)
+{
+    int32_t a = 0, b = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz; j += stride)
+        a = max(a, tf[j]);
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < n_docs; d += stride)
+        b = max(b, doc_len[d]);
+    a = __reduce_max_sync(0xffffffffu, a);
+    b = __reduce_max_sync(0xffffffffu, b);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&mx[0], a);
+        atomicMax(&mx[1], b);
+    }
+}
+
+// Lazy postings: each packed entry's second word becomes TF | |D| << 16
+// (packed) or TF; padding slots are copied as they are.
+__global__ void k_lazy_posts(const int64_t* __restrict__ indptr, int32_t vocab, int64_t nnz,
+                             const int32_t* __restrict__ indices, const int32_t* __restrict__ tf,
+                             const int32_t* __restrict__ doc_len, int packed,
+                             uint2* __restrict__ posts_lazy)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = 0, hi = vocab;  // last t with indptr[t] <= j
+        while (hi - lo > 1) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (indptr[mid] <= j)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const int64_t c0 = indptr[lo];
+        const int32_t d = indices[j];
+        const uint32_t w =
+            packed ? ((uint32_t)tf[j] | ((uint32_t)doc_len[d] << 16)) : (uint32_t)tf[j];
+        posts_lazy[post_start(c0, lo) + (j - c0)] = make_uint2((uint32_t)d, w);
+    }
+}
+
+}  // namespace
+
+int enable_lazy(bm25_index* ix, cudaStream_t s)
+{
+    if (ix->posts_lazy)
+        return BM25_OK;
+    DeviceInfo di;
+    BM25_TRY(device_info(&di));
+    cudaMemPool_t pool;
+    BM25_TRY(pool_for_device(di.device, &pool));
+    const int max_blocks = di.sm_count * 16;
+    int32_t h_mx[2] = {0, 0};
+    {
+        TempSet tmp(s);
+        int32_t* mx = nullptr;
+        BM25_TRY(tmp.alloc(&mx, 2, pool));
+        BM25_CUDA_TRY(cudaMemsetAsync(mx, 0, 2 * sizeof(int32_t), s));
+        {
+            ProfileScope ps_("k_max_tf_len", s);
+            k_max_tf_len<<<grid_for(std::max(ix->nnz, ix->n_docs), 256, max_blocks), 256, 0, s>>>(
+                ix->tf, ix->nnz, ix->doc_len, ix->n_docs, mx);
+        }
+        count_launch();
+        BM25_LAUNCH_CHECK();
+        BM25_CUDA_TRY(cudaMemcpyAsync(h_mx, mx, sizeof(h_mx), cudaMemcpyDeviceToHost, s));
+        BM25_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    const bool packed = h_mx[0] <= 0xffff && h_mx[1] <= 0xffff;
+    uint2* pl = nullptr;
+    BM25_TRY(pool_alloc(&pl, ix->n_posts, pool, s));
+    cudaError_t e = cudaMemcpyAsync(pl, ix->posts, sizeof(uint2) * (size_t)ix->n_posts,
+                                    cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && ix->nnz > 0) {
+        {
+            ProfileScope ps_("k_lazy_posts", s);
+            k_lazy_posts<<<grid_for(ix->nnz, 256, max_blocks), 256, 0, s>>>(
+                ix->indptr, ix->vocab, ix->nnz, ix->indices, ix->tf, ix->doc_len, packed ? 1 : 0,
+                pl);
+        }
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(pl, s);
+        return set_error(BM25_E_CUDA, "building the lazy postings failed: %s",
+                         cudaGetErrorString(e));
+    }
+    ix->posts_lazy = pl;
+    ix->lazy_packed = packed;
+    return BM25_OK;
+}
+
 void free_index_arrays(bm25_index* ix, cudaStream_t s)
 {
+    if (ix->posts_lazy)
+        cudaFreeAsync(ix->posts_lazy, s);
+    ix->posts_lazy = nullptr;
     void* ps[] = {ix->indptr, ix->indices, ix->data, ix->tf, ix->df,
                   ix->doc_len, ix->idf, ix->s0, ix->status, ix->posts};
     for (void* p : ps)

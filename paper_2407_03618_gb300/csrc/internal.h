@@ -82,7 +82,7 @@ constexpr uint32_t kPostPad = 0xffffffffu;  // doc id of a padding slot (beyond 
 
 struct Plan {
     int accumulator = BM25_ACC_AUTO;
-    int32_t tile_docs = 10240;
+    int32_t tile_docs = 6144;
     int32_t threads = 256;
     int32_t dense_max = 4096;   // postings bound of the dense path (AUTO, L2_DENSE)
     int32_t stage_entries = 1024; // packed postings per staging buffer of the tiled kernel
@@ -121,6 +121,10 @@ struct bm25_index {
     // stat_tokens tokens (this index's own counts unless rescored)
     int64_t doc_offset = 0;
     int64_t stat_docs = 0, stat_tokens = 0;
+    // query-time scoring (bm25_index_enable_lazy): the packed layout again,
+    // second word TF | |D| << 16 (lazy_packed) or TF alone
+    uint2* posts_lazy = nullptr;  // [n_posts]
+    bool lazy_packed = false;
     bm25::Plan plan;
     bm25_workspace* default_ws = nullptr;
     std::mutex mu;
@@ -175,15 +179,26 @@ void free_index_arrays(bm25_index* ix, cudaStream_t s);
 int pack_posts(bm25_index* ix, cudaStream_t s);
 int rescore_index(bm25_index* ix, const int32_t* df_global, int64_t n_docs_global,
                   int64_t n_tokens_global, cudaStream_t s);
+// Builds ix->posts_lazy from the CSC, TF and |D| (synchronous).
+int enable_lazy(bm25_index* ix, cudaStream_t s);
 int pool_for_current_device(cudaMemPool_t* out);
 
 // ---- retrieval (retrieve.cu) -------------------------------------------
+// Host-side checks of a retrieval call (api.cu): index, batch sizes, k and
+// BM25_MAX_K, the current device.
+int check_retrieve_args(const bm25_index* ix, int64_t n_tok, int32_t nq, int32_t k);
+// Query-time parameters of lazy scoring (bm25_retrieve_lazy).
+struct QueryParams {
+    double k1, b, delta;
+};
 // q_k: per-query k (device, NULL = k_max for every query); rows of the
-// outputs are k_max wide.
+// outputs are k_max wide.  qp: score at query time with these parameters
+// from the index's lazy postings (every query on the doc-tiled path), or
+// NULL for the stored scores.
 int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_tokens,
                     const int64_t* q_offsets, int32_t n_queries, int64_t n_query_tokens,
                     const int32_t* q_k, int32_t k_max, int32_t* out_ids, float* out_scores,
-                    const Plan& plan, cudaStream_t stream);
+                    const Plan& plan, cudaStream_t stream, const QueryParams* qp = nullptr);
 // Grows ws (unless fixed) to what retrieve_device needs for such a call;
 // allocates nothing when it already fits.  Fails while `stream` is being
 // captured and something would have to grow.

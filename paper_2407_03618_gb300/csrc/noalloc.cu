@@ -1,14 +1,20 @@
 // Retrieval for callers that cannot allocate device memory.
 //
 // bm25_retrieve keeps its scratch in a workspace that grows with cudaMalloc
-// on demand.  Some callers cannot allow that: code running where an
-// allocation would synchronise the device or is forbidden outright (inside a
-// host callback or a real-time serving loop with a fixed memory budget,
-// under an allocator that owns all device memory, or in a process that has
-// no right to grow its footprint).  bm25_retrieve_noalloc runs the same
-// kernels with their scratch carved from one file-scope device array of
-// kScratchBytes, so a call allocates nothing.  Every GPU that loads this
-// library holds that array for the life of the process.
+// on demand.  Some callers cannot allow that: a real-time serving loop with a
+// fixed memory budget (cudaMalloc may synchronise the device and stall every
+// stream), a process whose device memory is owned by another allocator that
+// has taken all of it, or one that must not grow its footprint after start.
+// bm25_retrieve_noalloc runs the same kernels with their scratch carved from
+// one file-scope device array of kScratchBytes, so a call allocates nothing.
+// Every GPU that loads this library holds that array for the life of the
+// process.  It still calls the CUDA runtime (launches, a memset), so it must
+// not be called from inside a CUDA host function or stream callback, where
+// CUDA calls are not allowed.
+//
+// The array's device address is looked up once per device and kept; after a
+// cudaDeviceReset the module is loaded again and the kept address is stale,
+// so the library must not be used across a device reset.
 //
 // The array is shared by every call: calls that overlap on the GPU (on
 // different streams, or from different threads) race on it and must be
@@ -64,23 +70,10 @@ extern "C" int bm25_retrieve_noalloc(const bm25_index* ix, const int32_t* query_
                                      float* out_scores, void* cuda_stream)
 {
     clear_error();
-    if (!ix)
-        return set_error(BM25_E_INVALID, "index is NULL");
-    if (n_queries < 0 || n_query_tokens < 0 || n_query_tokens > (int64_t)INT32_MAX)
-        return set_error(BM25_E_INVALID, "bad batch size (n_queries %d, n_query_tokens %lld)",
-                         n_queries, (long long)n_query_tokens);
-    if (k < 1)
-        return set_error(BM25_E_INVALID, "k = %d must be >= 1", k);
+    BM25_TRY(check_retrieve_args(ix, n_query_tokens, n_queries, k));
     const int64_t N = ix->n_docs;
     const int64_t kp = k < N ? k : N;
-    if (kp > BM25_MAX_K)
-        return set_error(BM25_E_INVALID, "min(k, n_docs) = %lld exceeds BM25_MAX_K = %d",
-                         (long long)kp, BM25_MAX_K);
-    int dev = 0;
-    BM25_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev != ix->device)
-        return set_error(BM25_E_INVALID, "current device %d is not the index's device %d", dev,
-                         ix->device);
+    int dev = ix->device;
     if (n_queries == 0)
         return BM25_OK;
 

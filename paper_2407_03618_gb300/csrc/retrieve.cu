@@ -62,7 +62,8 @@ __global__ void k_query_prep(const int32_t* __restrict__ q_tokens, int64_t n_tok
                              double* __restrict__ shift, int32_t* __restrict__ qkp,
                              int4* __restrict__ lrec, uint32_t* __restrict__ lpost,
                              uint32_t* __restrict__ thresh, int32_t* __restrict__ sq,
-                             uint32_t* __restrict__ ctr, int* status)
+                             uint32_t* __restrict__ ctr, int* status, int lazy_variant,
+                             double lazy_k1, double lazy_delta)
 {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -95,7 +96,13 @@ __global__ void k_query_prep(const int32_t* __restrict__ q_tokens, int64_t n_tok
                     set_status(status, BM25_E_TOKEN_RANGE);
                     continue;
                 }
-                sum += s0[t];
+                if (lazy_variant >= 0) {  // S0 at the call's k1, delta
+                    double c, z;
+                    term_coef(lazy_variant, idf[t], lazy_k1, lazy_delta, &c, &z);
+                    sum += z;
+                } else {
+                    sum += s0[t];
+                }
                 post += indptr[t + 1] - indptr[t];
                 neg |= idf[t] < 0.0;
             }
@@ -367,6 +374,31 @@ constexpr uint32_t kTouchCap = 2048; // touched-list entries kept (an item touch
 constexpr int kWaitPolls = kHandshakePolls;  // mbarrier polls before a copy wait gives up
 
 
+// Query-time scoring (an index with lazy postings: doc id and TF | |D| <<
+// 16, or TF alone with |D| read from doc_len when either exceeds 16 bits).
+// The scores are computed while scattering, with the call's k1, b, delta:
+// length factor from |D| and the index's Lavg, coefficient per query token
+// from its IDF (entry_score, term_coef).
+struct LazyArgs {
+    const int32_t* q_tokens;   // the batch's tokens (to look up each token's IDF)
+    const double* idf;         // [vocab]
+    const int32_t* doc_len;    // [n_docs] (unpacked layout)
+    int variant;
+    int packed;                // 1: second word = TF | |D| << 16
+    double k1, delta;
+    float one_minus_b, b_over_lavg;  // K_D = 1 - b + b |D| / Lavg
+    float k1f;
+    ScoreConsts kc;
+};
+
+// Per staging buffer of the lazy kernel: where each of the chunk's (up to)
+// 64 query tokens starts in the buffer (start[64] = entries in the buffer;
+// tokens with no entries start where the next one does) and its coefficient.
+struct __align__(16) SegTable {
+    uint16_t start[68];
+    float coef[64];
+};
+
 constexpr int32_t kModeList = 0;   // first touches listed, claimed after the scatter
 constexpr int32_t kModeCross = 1;  // threshold crossings listed, the tile reset in bulk
 
@@ -565,10 +597,11 @@ __device__ uint32_t consumer_first_untouched(const float* acc, int32_t wd, uint3
 // Shared memory of k_tile_staged: the front, W accumulators, the candidate
 // list, `stages` staging buffers of `entries` packed postings, the touched
 // list (tl_cap 16-bit entries, rounded to 16 bytes).
-size_t staged_smem_bytes(int32_t W, int stages, int entries, uint32_t tl_cap)
+size_t staged_smem_bytes(int32_t W, int stages, int entries, uint32_t tl_cap, bool lazy)
 {
     return kStagedFront + (size_t)W * sizeof(float) + (size_t)kCandCap * sizeof(u64) +
-           (size_t)stages * entries * sizeof(uint2) + ((size_t)tl_cap * sizeof(uint16_t) + 15) / 16 * 16;
+           (size_t)stages * entries * sizeof(uint2) + ((size_t)tl_cap * sizeof(uint16_t) + 15) / 16 * 16 +
+           (lazy ? (size_t)stages * sizeof(SegTable) : 0);
 }
 
 // seg (packed): for query token m and tile boundary j, the first slot of the
@@ -577,14 +610,14 @@ size_t staged_smem_bytes(int32_t W, int stages, int entries, uint32_t tl_cap)
 // Up to four CTAs per SM: the register bound allows four (67 registers per
 // thread at 6 consumer warps, the default, 56 at 8); shared memory allows
 // four up to W = 7168 and three at the default W = 10240 (73 KB).
-template <int CW>
-__global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
+template <int CW, bool LAZY>
+__global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : (LAZY ? 3 : 4))
     k_tile_staged(int64_t n_docs, const uint2* __restrict__ posts, const uint32_t* __restrict__ seg,
                   int32_t W, int32_t n_tiles, int32_t kstride, const int4* __restrict__ lrec,
                   const uint32_t* __restrict__ lpost, const uint32_t* __restrict__ ctr,
                   uint32_t* __restrict__ thresh, uint32_t* __restrict__ tcount,
                   u64* __restrict__ cand, int* __restrict__ status, int wait_polls,
-                  int n_stages, int stage_entries, uint32_t tl_cap)
+                  int n_stages, int stage_entries, uint32_t tl_cap, LazyArgs lz)
 {
     constexpr int NT = CW * 32;  // consumer threads
     constexpr int OW = CW - 1;   // the output warp (the fewest postings per item)
@@ -594,6 +627,8 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
     u64* clist = reinterpret_cast<u64*>(acc + W);
     uint2* stage = reinterpret_cast<uint2*>(clist + kCandCap);
     uint16_t* tl = reinterpret_cast<uint16_t*>(stage + (size_t)n_stages * stage_entries);
+    SegTable* segt = reinterpret_cast<SegTable*>(
+        reinterpret_cast<unsigned char*>(tl) + ((size_t)tl_cap * sizeof(uint16_t) + 15) / 16 * 16);
     SelectState& st = sh.st;
 
     const int32_t nq = (int32_t)ctr[0];
@@ -697,6 +732,18 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
                 const uint32_t s2 = n[0] + n[1];
                 const uint32_t inc = warp_inclusive_sum(s2);
                 const uint32_t off[2] = {inc - s2, inc - s2 + n[0]};
+                float cf[2] = {0.0f, 0.0f};
+                if (LAZY) {  // the chunk's per-token coefficients at the call's k1, delta
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const int32_t m = mb + 2 * lane + h;
+                        if (n[h] > 0u && m < m1) {
+                            double c, s0;
+                            term_coef(lz.variant, lz.idf[lz.q_tokens[m]], lz.k1, lz.delta, &c, &s0);
+                            cf[h] = (float)c;
+                        }
+                    }
+                }
                 const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
                 const bool last_chunk = (int64_t)mb + 64 >= (int64_t)m1;
                 if (total == 0u && !last_chunk)
@@ -715,6 +762,18 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
                             *(volatile uint32_t*)&sh.abort_flag = 1u;
                         }
                         break;
+                    }
+                    if (LAZY) {  // where each token's entries start in this buffer
+                        SegTable& tb = segt[s];
+#pragma unroll
+                        for (int h = 0; h < 2; h++) {
+                            const uint32_t st0 = min(max(off[h], e0), e1) - e0;
+                            tb.start[2 * lane + h] = (uint16_t)st0;
+                            tb.coef[2 * lane + h] = cf[h];
+                        }
+                        if (lane == 0)
+                            tb.start[64] = (uint16_t)(e1 - e0);
+                        __syncwarp();
                     }
                     if (lane == 0) {
                         StageHdr& hd = sh.hdr[s];
@@ -830,7 +889,37 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : 4)
                 const int32_t i = i0 + lane;
                 const uint4 pe = i < n_pairs ? sb4[i] : make_uint4(kPostPad, 0u, kPostPad, 0u);
                 const uint32_t dl0 = pe.x - d0u, dl1 = pe.z - d0u;
-                const float v0 = __uint_as_float(pe.y), v1 = __uint_as_float(pe.w);
+                float v0 = __uint_as_float(pe.y), v1 = __uint_as_float(pe.w);
+                if (LAZY) {
+                    // the pair's token: the last one starting at or before entry 2i
+                    const SegTable& tb = segt[s];
+                    int lo = 0, hi = 65;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if ((int32_t)tb.start[mid] <= 2 * i)
+                            lo = mid;
+                        else
+                            hi = mid;
+                    }
+                    const float c = tb.coef[min(lo, 63)];
+                    auto lazy_v = [&](uint32_t w, uint32_t dl) {
+                        uint32_t tfv, len;
+                        if (lz.packed) {
+                            tfv = w & 0xffffu;
+                            len = w >> 16;
+                        } else {
+                            tfv = w;
+                            len = dl < wdu ? (uint32_t)lz.doc_len[d0u + dl] : 0u;
+                        }
+                        const float kd = fmaf(lz.b_over_lavg, (float)len, lz.one_minus_b);
+                        const float a = (lz.variant == BM25_L || lz.variant == BM25_TFLDP)
+                                            ? 1.0f / kd
+                                            : lz.k1f * kd;
+                        return entry_score(lz.variant, (float)tfv, a, c, lz.kc);
+                    };
+                    v0 = lazy_v(pe.y, dl0);
+                    v1 = lazy_v(pe.w, dl1);
+                }
                 // the sums before the adds (-0.0 where nothing was added)
                 const float o0 = atom_add_if(acc, dl0, wdu, v0);
                 const float o1 = atom_add_if(acc, dl1, wdu, v1);
@@ -1791,10 +1880,11 @@ void workspace_release(bm25_workspace* ws)
 int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_tokens,
                     const int64_t* q_off, int32_t nq, int64_t n_tok, const int32_t* q_k,
                     int32_t kmax, int32_t* out_ids, float* out_scores, const Plan& plan,
-                    cudaStream_t s)
+                    cudaStream_t s, const QueryParams* qp)
 {
     if (nq == 0)
         return BM25_OK;
+    const bool lazy = qp != nullptr;
     DeviceInfo di;
     BM25_TRY(device_info(&di));
     const int64_t N = ix->n_docs;
@@ -1819,12 +1909,30 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
 
     // launch shapes that do not depend on the sub-batch
     const uint32_t tl_cap = std::min<uint32_t>((uint32_t)W, kTouchCap);
-    const size_t smem = staged_smem_bytes(W, plan.stages, plan.stage_entries, tl_cap);
+    const size_t smem = staged_smem_bytes(W, plan.stages, plan.stage_entries, tl_cap, lazy);
     // plan.threads consumer threads (4, 8 or 16 warps) and one producer warp
-    auto tile_kernel = plan.threads == 128   ? k_tile_staged<4>
-                       : plan.threads == 192 ? k_tile_staged<6>
-                       : plan.threads == 256 ? k_tile_staged<8>
-                                             : k_tile_staged<16>;
+    auto tile_kernel = lazy ? (plan.threads == 128   ? k_tile_staged<4, true>
+                               : plan.threads == 192 ? k_tile_staged<6, true>
+                               : plan.threads == 256 ? k_tile_staged<8, true>
+                                                     : k_tile_staged<16, true>)
+                            : (plan.threads == 128   ? k_tile_staged<4, false>
+                               : plan.threads == 192 ? k_tile_staged<6, false>
+                               : plan.threads == 256 ? k_tile_staged<8, false>
+                                                     : k_tile_staged<16, false>);
+    LazyArgs lz = {};
+    if (lazy) {
+        lz.q_tokens = q_tokens;
+        lz.idf = ix->idf;
+        lz.doc_len = ix->doc_len;
+        lz.variant = ix->variant;
+        lz.packed = ix->lazy_packed ? 1 : 0;
+        lz.k1 = qp->k1;
+        lz.delta = qp->delta;
+        lz.one_minus_b = (float)(1.0 - qp->b);
+        lz.b_over_lavg = (float)(qp->b / ix->lavg);
+        lz.k1f = (float)qp->k1;
+        lz.kc = score_consts(qp->k1, qp->delta);
+    }
     const int tile_threads = plan.threads + 32;
     BM25_CUDA_TRY(cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
@@ -1857,8 +1965,9 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
             ProfileScope ps_("k_query_prep", s);
             k_query_prep<<<std::max(g0, 1), 256, 0, s>>>(
                 q_tokens, n_tok, qo, nb, q0 == 0, q0 + nb == nq, q_k ? q_k + q0 : nullptr, kmax,
-                N, ix->s0, ix->idf, ix->indptr, ix->vocab, g.dense_max, ws->shift, ws->qkp, ws->lrec,
-                ws->lpost, ws->thresh, ws->sq, ws->ctr, ix->status);
+                N, ix->s0, ix->idf, ix->indptr, ix->vocab, lazy ? -1 : g.dense_max, ws->shift,
+                ws->qkp, ws->lrec, ws->lpost, ws->thresh, ws->sq, ws->ctr, ix->status,
+                lazy ? ix->variant : -1, lazy ? qp->k1 : 0.0, lazy ? qp->delta : 0.0);
         }
         count_launch();
         BM25_LAUNCH_CHECK();
@@ -1867,9 +1976,10 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
                                                   (int64_t)di.sm_count * per_sm);
             ProfileScope ps_("k_tile_staged", s);
             tile_kernel<<<g2, tile_threads, smem, s>>>(
-                N, ix->posts, reinterpret_cast<const uint32_t*>(ws->seg), W, n_tiles, kstride,
+                N, lazy ? ix->posts_lazy : ix->posts, reinterpret_cast<const uint32_t*>(ws->seg),
+                W, n_tiles, kstride,
                 ws->lrec, ws->lpost, ws->ctr, ws->thresh, ws->tcount, ws->cand, ix->status,
-                handshake_polls(), plan.stages, plan.stage_entries, tl_cap);
+                handshake_polls(), plan.stages, plan.stage_entries, tl_cap, lz);
         }
         count_launch();
         BM25_LAUNCH_CHECK();
@@ -1881,7 +1991,7 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
         }
         count_launch();
         BM25_LAUNCH_CHECK();
-        if (g.dense_ctas > 0) {
+        if (g.dense_ctas > 0 && !lazy) {
             const int g4 = std::min(g.dense_ctas, nb);
             ProfileScope ps_("k_dense_topk", s);
             k_dense_topk<<<g4, kDenseThreads, g.dense_smem, s>>>(

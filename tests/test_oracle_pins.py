@@ -303,3 +303,23 @@ def test_invalid_corpus_rejected(oracle_mod):
         oracle_mod.build(np.array([0, 5], np.int32), np.array([0, 2], np.int64), 3)
     with pytest.raises(ValueError):
         oracle_mod.build(np.array([0, 1], np.int32), np.array([0, 3], np.int64), 3)
+
+
+@pytest.mark.parametrize("variant", range(6))
+def test_query_time_parameters_equal_a_build_with_them(oracle_mod, variant):
+    """Lazy scoring with k1, b, delta given at query time equals scoring an
+    index built with those parameters (the IDF does not depend on them), and
+    differs from the build's own parameters where TF or |D| matter."""
+    rng = np.random.default_rng(60 + variant)
+    for _ in range(40):
+        c = synth.random_tiny_corpus(rng, allow_empty=False)
+        built = oracle_mod.build(c.tokens, c.doc_offsets, c.vocab, variant, 1.2, 0.75, 0.5)
+        k1, b = float(rng.uniform(0.1, 3.0)), float(rng.uniform(0, 1))
+        d = float(rng.uniform(0.4, 2.0))
+        other = oracle_mod.build(c.tokens, c.doc_offsets, c.vocab, variant, k1, b, d)
+        q = rng.integers(0, c.vocab, int(rng.integers(1, 6))).astype(np.int32)
+        a = oracle_mod.score_all(built, q, k1=k1, b=b, delta=d)
+        assert np.array_equal(a, oracle_mod.score_all(other, q))
+        ids, sc = oracle_mod.topk(built, q, np.array([0, q.shape[0]]), 3, k1=k1, b=b, delta=d)
+        ids2, sc2 = oracle_mod.topk(other, q, np.array([0, q.shape[0]]), 3)
+        assert np.array_equal(ids, ids2) and np.array_equal(sc, sc2)

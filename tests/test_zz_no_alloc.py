@@ -2,17 +2,19 @@
 memory (its scratch is a fixed device array inside the library).
 
 Called through the C ABI directly, twice in a row on different batches, and
-compared with bm25_retrieve on the same inputs: the same ids up to ties
-within the tolerance of the other parity tests, and scores within it.  Kept
-in a file of its own that pytest collects last; it passes alone in a fresh
-process and after the other tests.
+compared with bm25_retrieve on the same inputs (the same ids up to ties
+within the tolerance of the other parity tests, and scores within it) and
+with the FP64 oracle (check_topk), so that a mistake both paths shared would
+still fail.  Kept in a file of its own that pytest collects last; it passes
+alone in a fresh process and after the other tests.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
-from oracle.compare import RTOL
+import oracle
+from oracle.compare import RTOL, check_topk
 from paper_2407_03618_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -52,6 +54,7 @@ def test_noalloc_matches_retrieve_twice():
     c = synth.make_corpus(30_000, 20_000, 1.05, ("lognormal", 60, 0.6), seed=0)
     ix = bm25.Index.build(torch.from_numpy(c.tokens).to(dev),
                           torch.from_numpy(c.doc_offsets).to(dev), c.vocab, "bm25+")
+    orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.BM25PLUS, 1.5, 0.75, 0.5)
     for call, (seed, k) in enumerate([(1, 10), (2, 100)]):
         q = synth.make_queries(200, 20_000, 1.05, ("uniform", 1, 16), 10, seed=seed)
         qt = torch.from_numpy(q.tokens).to(dev)
@@ -59,8 +62,11 @@ def test_noalloc_matches_retrieve_twice():
         ids_n, sc_n = _noalloc(lib, ix, qt, qo, k, torch)
         ids_r, sc_r = ix.retrieve(qt, qo, k)
         ix.sync_status()
-        _same_result(ids_n.cpu().numpy(), sc_n.cpu().numpy(), ids_r.cpu().numpy(),
-                     sc_r.cpu().numpy())
+        ids_n, sc_n = ids_n.cpu().numpy(), sc_n.cpu().numpy()
+        _same_result(ids_n, sc_n, ids_r.cpu().numpy(), sc_r.cpu().numpy())
+        for i in range(q.n_queries):
+            full, ab = oracle.score_all(orc, q.query(i), with_abs=True)
+            check_topk(ids_n[i], sc_n[i], full, ab, k, where=f"noalloc call {call} q{i}")
     # a batch beyond the fixed scratch is refused with a clear message
     big = synth.make_queries(20_000, 20_000, 1.05, ("uniform", 8, 16), 10, seed=3)
     qt = torch.from_numpy(big.tokens).to(dev)
