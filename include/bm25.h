@@ -49,6 +49,7 @@ extern "C" {
 
 typedef struct bm25_index bm25_index;
 typedef struct bm25_workspace bm25_workspace;
+typedef struct bm25_vocab bm25_vocab;
 
 enum bm25_variant {
     BM25_LUCENE = 0,
@@ -104,8 +105,8 @@ typedef struct bm25_plan {
     int32_t dense_max_postings; /* dense-path bound for AUTO / L2_DENSE, in [0, 2^22]
                                    (default 4096) */
     int32_t stage_entries;      /* packed postings per shared-memory staging buffer of the
-                                   tiled kernel: a multiple of 64 in [128, 8192] (default 1024) */
-    int32_t stages;             /* staging buffers in its ring, in [2, 8] (default 3) */
+                                   tiled kernel: a multiple of 64 in [128, 8192] (default 1536) */
+    int32_t stages;             /* staging buffers in its ring, in [2, 8] (default 2) */
 } bm25_plan;
 
 /* ------------------------------------------------------------------ index */
@@ -304,7 +305,7 @@ int bm25_index_get_plan(const bm25_index* index, bm25_plan* plan);
  * the index's plan.  Candidates: tile widths 6144, 7168, 8192, 10240 and
  * 12288 with every query tiled and the default threads and staging ring,
  * then 128, 192, 256 and 512 consumer threads at the best width, then
- * staging rings of 2 x 512, 2 x 1024, 3 x 1024 and 2 x 2048 postings with
+ * staging rings of 2 x 512, 2 x 1024, 3 x 1024, 2 x 1536 and 2 x 2048 postings with
  * the best of those, then dense-path bounds of 2048 .. 32768 postings (the
  * accumulator per query-length bucket).  Each step tries the library's default first, and a
  * later candidate replaces the best so far only when more than 1 % faster, so
@@ -319,6 +320,49 @@ int bm25_autotune(bm25_index* index, const int32_t* query_tokens, int64_t n_quer
                   const int64_t* query_offsets, int32_t n_queries, int32_t k,
                   void* cuda_stream, bm25_plan* best, double* best_ms, bm25_plan* tried,
                   double* tried_ms, int32_t tried_cap, int32_t* n_tried);
+
+/* -------------------------------------------------------------- tokenizer */
+
+/* Text to term ids on the device (Sec. 2 "Tokenization": split with the
+ * pattern (?u)\b\w\w+\b, remove stopwords, map each distinct word to an
+ * integer id).  Read on UTF-8 bytes: ASCII letters, digits and '_' and every
+ * byte of a non-ASCII character are word characters, ASCII letters are
+ * lowercased, a token is a maximal run of word bytes inside one text with at
+ * least two characters, and a token equal to a stopword is dropped.  (The
+ * Snowball stemmer the paper offers as an option is not provided.)
+ *
+ * bm25_tokenize_corpus: text[n_bytes] (device bytes) holds n_docs texts,
+ * doc d at text[doc_offsets[d] .. doc_offsets[d+1]) (device int64, starting
+ * at 0 and ending at n_bytes); stopwords (HOST bytes, word i at
+ * stopwords[stop_offsets[i] .. stop_offsets[i+1]), any case) may be NULL
+ * with n_stopwords = 0.  Writes the corpus's term ids to token_ids (device,
+ * capacity entries; n_bytes / 2 + 1 always suffices) and
+ * token_offsets[n_docs+1] (device int64: doc d owns token_ids[offsets[d] ..
+ * offsets[d+1])) — the inputs bm25_index_build takes — sets *n_tokens
+ * (host), and returns a vocabulary: ids are given in order of first
+ * occurrence.  If the tokens exceed capacity, returns BM25_E_INVALID with
+ * *n_tokens set.  Words are told apart by a 64-bit hash checked against
+ * their bytes; two different words with the same hash fail with
+ * BM25_E_INVALID.  Synchronous.
+ *
+ * bm25_tokenize_queries: the same split with the vocabulary's stopwords;
+ * tokens the vocabulary does not know are dropped; token_offsets[n_texts+1].
+ *
+ * bm25_vocab_export: the words (lowercased bytes, HOST, n_bytes from
+ * bm25_vocab_info) in id order and word_offsets[n_words+1] (HOST); either
+ * may be NULL. */
+int bm25_tokenize_corpus(const uint8_t* text, int64_t n_bytes, const int64_t* doc_offsets,
+                         int64_t n_docs, const uint8_t* stopwords, const int64_t* stop_offsets,
+                         int32_t n_stopwords, int32_t* token_ids, int64_t capacity,
+                         int64_t* token_offsets, int64_t* n_tokens, bm25_vocab** vocab,
+                         void* cuda_stream);
+int bm25_tokenize_queries(const bm25_vocab* vocab, const uint8_t* text, int64_t n_bytes,
+                          const int64_t* offsets, int64_t n_texts, int32_t* token_ids,
+                          int64_t capacity, int64_t* token_offsets, int64_t* n_tokens,
+                          void* cuda_stream);
+int bm25_vocab_info(const bm25_vocab* vocab, int64_t* n_words, int64_t* n_bytes);
+int bm25_vocab_export(const bm25_vocab* vocab, uint8_t* words, int64_t* word_offsets);
+void bm25_vocab_free(bm25_vocab* vocab);
 
 /* ------------------------------------------------------ query-time scoring */
 

@@ -115,6 +115,11 @@ def load(path: str | None = None):
         "bm25_profile_end": (cint, []),
         "bm25_profile_count": (cint, []),
         "bm25_profile_get": (cint, [cint, ctypes.c_char_p, cint, P, P]),
+        "bm25_tokenize_corpus": (cint, [P, i64, P, i64, P, P, i32, P, i64, P, P, PP, P]),
+        "bm25_tokenize_queries": (cint, [P, P, i64, P, i64, P, i64, P, P, P]),
+        "bm25_vocab_info": (cint, [P, P, P]),
+        "bm25_vocab_export": (cint, [P, P, P]),
+        "bm25_vocab_free": (None, [P]),
         "bm25_index_enable_lazy": (cint, [P, P]),
         "bm25_retrieve_lazy": (cint, [P, P, i64, P, i32, i32, f64, f64, f64, P, P, P]),
         "bm25_index_df_device": (cint, [P, P, P]),
@@ -162,6 +167,83 @@ def merge_topk(cand_ids, cand_scores, k: int, out=None, stream=None):
     _check(load().bm25_merge_topk(ci.data_ptr(), cs.data_ptr(), g, nq, k, ids.data_ptr(),
                                   sc.data_ptr(), _stream(stream)))
     return ids, sc
+
+
+class Vocab:
+    """A vocabulary built on the device by tokenize_corpus."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def info(self) -> dict:
+        n, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().bm25_vocab_info(self.handle, ctypes.byref(n), ctypes.byref(b)))
+        return {"n_words": n.value, "n_bytes": b.value}
+
+    def words(self) -> list:
+        """The words (lowercased bytes) in id order."""
+        inf = self.info()
+        buf = np.zeros(max(inf["n_bytes"], 1), np.uint8)
+        off = np.zeros(inf["n_words"] + 1, np.int64)
+        _check(load().bm25_vocab_export(self.handle, _ptr(buf), _ptr(off)))
+        raw = buf.tobytes()
+        return [raw[off[i]:off[i + 1]] for i in range(inf["n_words"])]
+
+    def close(self):
+        if self.handle:
+            load().bm25_vocab_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stopword_arrays(stopwords):
+    words = [bytes(w) for w in stopwords]
+    off = np.zeros(len(words) + 1, np.int64)
+    off[1:] = np.cumsum([len(w) for w in words])
+    buf = np.frombuffer(b"".join(words) or b"\0", np.uint8).copy()
+    return buf, off
+
+
+def tokenize_corpus(text, doc_offsets, stopwords=(), stream=None):
+    """Term ids of a corpus of UTF-8 texts on the device: text CUDA uint8,
+    doc_offsets CUDA int64 [N+1].  Returns (token_ids CUDA int32 [T],
+    token_offsets CUDA int64 [N+1], Vocab)."""
+    import torch
+    tx = _dev_tensor(text, torch.uint8)
+    do = _dev_tensor(doc_offsets, torch.int64)
+    n = do.numel() - 1
+    cap = tx.numel() // 2 + 1
+    ids = torch.empty(cap, dtype=torch.int32, device=tx.device)
+    offs = torch.empty(n + 1, dtype=torch.int64, device=tx.device)
+    sb, so = _stopword_arrays(stopwords)
+    nt = ctypes.c_int64()
+    h = ctypes.c_void_p()
+    _check(load().bm25_tokenize_corpus(tx.data_ptr(), tx.numel(), do.data_ptr(), n, _ptr(sb),
+                                       _ptr(so), len(so) - 1, ids.data_ptr(), cap, offs.data_ptr(),
+                                       ctypes.byref(nt), ctypes.byref(h), _stream(stream)))
+    return ids[:nt.value], offs, Vocab(h.value)
+
+
+def tokenize_queries(vocab: Vocab, text, offsets, stream=None):
+    """Term ids of query texts with a corpus vocabulary (unknown words
+    dropped).  Returns (token_ids CUDA int32, token_offsets CUDA int64)."""
+    import torch
+    tx = _dev_tensor(text, torch.uint8)
+    qo = _dev_tensor(offsets, torch.int64)
+    n = qo.numel() - 1
+    cap = tx.numel() // 2 + 1
+    ids = torch.empty(cap, dtype=torch.int32, device=tx.device)
+    offs = torch.empty(n + 1, dtype=torch.int64, device=tx.device)
+    nt = ctypes.c_int64()
+    _check(load().bm25_tokenize_queries(vocab.handle, tx.data_ptr(), tx.numel(), qo.data_ptr(), n,
+                                        ids.data_ptr(), cap, offs.data_ptr(), ctypes.byref(nt),
+                                        _stream(stream)))
+    return ids[:nt.value], offs
 
 
 def release_cached():

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJ_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(PKG, "libbm25gpu.so")
 SOURCES = ["scan.cu", "index_build.cu", "retrieve.cu", "api.cu", "profile.cu", "noalloc.cu",
-           "tune.cu", "server.cu"]
+           "tune.cu", "server.cu", "tokenize.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -85,8 +85,8 @@ struct Plan {
     int32_t tile_docs = 6144;
     int32_t threads = 256;
     int32_t dense_max = 4096;   // postings bound of the dense path (AUTO, L2_DENSE)
-    int32_t stage_entries = 1024; // packed postings per staging buffer of the tiled kernel
-    int32_t stages = 3;           // staging buffers in its ring
+    int32_t stage_entries = 1536; // packed postings per staging buffer of the tiled kernel
+    int32_t stages = 2;           // staging buffers in its ring
 };
 // Fills zero fields of `in` from `base`; BM25_E_INVALID (nothing changed) if
 // a field is out of range.

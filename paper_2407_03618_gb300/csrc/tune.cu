@@ -150,7 +150,7 @@ extern "C" int bm25_autotune(bm25_index* ix, const int32_t* query_tokens, int64_
     // 1c. the staging ring (buffer size x count) with those
     const Plan threads = cur;
     for (auto ring : {std::make_pair(512, 2), std::make_pair(1024, 2), std::make_pair(1024, 3),
-                      std::make_pair(2048, 2)}) {
+                      std::make_pair(1536, 2), std::make_pair(2048, 2)}) {
         if (ring.first == threads.stage_entries && ring.second == threads.stages)
             continue;  // the ring the earlier steps ran with
         Plan p = threads;

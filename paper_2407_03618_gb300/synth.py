@@ -199,3 +199,73 @@ def random_queries(rng: np.random.Generator, vocab: int, n_queries: int, max_len
     off = offsets_from_lengths(lens)
     tok = rng.integers(0, vocab, int(off[-1])).astype(np.int32)
     return Queries(tok, off)
+
+
+# ---- text (for the tokenizer) ----------------------------------------------
+
+_ASCII_WORD = np.frombuffer(b"abcdefghijklmnopqrstuvwxyz", np.uint8)
+_ASCII_MIXED = np.frombuffer(b"ABCDEFGHIJKLMNOPQRSTUVWXYZ0123456789_", np.uint8)
+_NON_ASCII = ["é", "ü", "ß", "ñ", "ø", "中", "文", "ж",
+              "λ", "\U0001f600"]
+_SEPARATORS = [b" ", b" ", b" ", b" ", b" ", b", ", b". ", b"\n", b" - ", b"'", b" (", b") ",
+               b"; ", b"\t", b"!", b"\"", b"/", b" ... "]
+
+
+def make_lexicon(n_words: int, seed: int = 0) -> list:
+    """n_words synthetic word forms (bytes): 1-12 characters, mostly lowercase
+    ASCII letters, some upper case, digits, '_' and non-ASCII characters;
+    about a tenth are one character long.  Forms may repeat or differ only by
+    case."""
+    rng = np.random.default_rng(seed)
+    lens = np.where(rng.random(n_words) < 0.1, 1, rng.integers(2, 13, n_words))
+    out = []
+    for L in lens.tolist():
+        chars = []
+        for _ in range(L):
+            u = rng.random()
+            if u < 0.85:
+                chars.append(bytes([int(rng.choice(_ASCII_WORD))]))
+            elif u < 0.95:
+                chars.append(bytes([int(rng.choice(_ASCII_MIXED))]))
+            else:
+                chars.append(_NON_ASCII[int(rng.integers(0, len(_NON_ASCII)))].encode())
+        out.append(b"".join(chars))
+    return out
+
+
+def make_text_corpus(n_docs: int, n_words: int, zipf_s: float, length: tuple, seed: int = 0,
+                     lexicon_seed: int = 1000):
+    """UTF-8 texts: words of a synthetic lexicon drawn Zipf(zipf_s), joined by
+    ASCII separators (spaces, punctuation, newlines, apostrophes).  Returns
+    (text uint8 [bytes], offsets int64 [n_docs + 1], lexicon)."""
+    rng = np.random.default_rng(seed)
+    lex = make_lexicon(n_words, lexicon_seed)
+    if length[0] == "poisson":
+        lens = lengths_poisson(rng, n_docs, length[1], minimum=0)
+    else:
+        lens = lengths_lognormal(rng, n_docs, length[1], length[2], minimum=0)
+    words = zipf_sampler(n_words, zipf_s)(rng, int(lens.sum()))
+    seps = rng.integers(0, len(_SEPARATORS), int(lens.sum()))
+    pieces = lex + _SEPARATORS
+    plen = np.array([len(p) for p in pieces], np.int64)
+    pbuf = np.frombuffer(b"".join(pieces), np.uint8)
+    pstart = np.concatenate([[0], np.cumsum(plen)[:-1]])
+    # piece sequence: word, separator, word, separator, ... per document
+    seq = np.empty(2 * words.shape[0], np.int64)
+    seq[0::2] = words
+    seq[1::2] = len(lex) + seps
+    seq_len = plen[seq]
+    ends = np.cumsum(seq_len)
+    total = int(ends[-1]) if ends.shape[0] else 0
+    owner = np.repeat(np.arange(seq.shape[0]), seq_len)
+    within = np.arange(total) - np.repeat(ends - seq_len, seq_len)
+    text = pbuf[pstart[seq][owner] + within] if total else np.zeros(0, np.uint8)
+    tok_off = np.concatenate([[0], np.cumsum(lens)]) * 2  # piece index of each doc's start
+    byte_off = np.concatenate([[0], ends])[tok_off]
+    return np.ascontiguousarray(text, np.uint8), byte_off.astype(np.int64), lex
+
+
+def split_texts(text: np.ndarray, offsets: np.ndarray) -> list:
+    """The texts as a list of bytes."""
+    raw = text.tobytes()
+    return [raw[offsets[i]:offsets[i + 1]] for i in range(offsets.shape[0] - 1)]

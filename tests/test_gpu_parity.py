@@ -177,7 +177,7 @@ def test_sort_spans_many_tiles_and_passes(torch_dev):
 @pytest.mark.parametrize("tile_docs,threads,stage_entries,stages",
                          [(1024, 128, 512, 2), (2048, 256, 128, 8), (16384, 512, 4096, 3),
                           (4096, 512, 512, 2), (49152, 256, 256, 2), (3072, 192, 8192, 2),
-                          (10240, 192, 1024, 4), (8192, 256, 2048, 3)])
+                          (10240, 192, 1024, 4), (8192, 256, 2048, 3), (6144, 256, 1536, 2)])
 def test_retrieval_across_tiles(torch_dev, tile_docs, threads, stage_entries, stages):
     """Small doc tiles force many (query, tile) items and a ragged last tile;
     staging rings from eight 1 KB buffers (an item spans many) to two 64 KB
