@@ -74,3 +74,47 @@ def check_topk(ids, scores, full, abs_full, k: int, rtol: float = RTOL, where: s
     assert (ds <= 0).all(), f"{where}: scores not sorted descending at {np.nonzero(ds > 0)[0][:5]}"
     eq = ds == 0
     assert (np.diff(got)[eq] > 0).all(), f"{where}: equal scores not ordered by doc id"
+
+
+def check_topk_with_list(ids, scores, top_ids, top_scores, k: int, n_docs: int,
+                         rtol: float = RTOL, where: str = ""):
+    """check_topk when the oracle's full score vector is too large to score
+    for every query: the oracle's own top m > k list (ids, FP64 scores, as
+    oracle.topk returns them) stands in for it.  Valid for score vectors
+    whose terms are all >= 0 (sum_i |S| = B: every variant but Robertson).
+    Documents outside the list score at most the list's last score; that is
+    enough to apply the same rule as check_topk as long as the last score
+    lies more than the k-th tolerance below the k-th score (else the list is
+    too short to decide, and AssertionError says so)."""
+    ids = np.asarray(ids)
+    scores = np.asarray(scores, dtype=np.float64)
+    top_ids = np.asarray(top_ids, dtype=np.int64)
+    top_scores = np.asarray(top_scores, dtype=np.float64)
+    m = int((top_ids >= 0).sum())
+    kp = min(k, n_docs)
+    assert ids.shape[0] == k and scores.shape[0] == k, f"{where}: expected {k} slots"
+    if kp < k:
+        assert (ids[kp:] == -1).all(), f"{where}: padding ids must be -1"
+        assert np.isneginf(scores[kp:]).all(), f"{where}: padding scores must be -inf"
+    got = ids[:kp].astype(np.int64)
+    sc = scores[:kp]
+    assert ((got >= 0) & (got < n_docs)).all(), f"{where}: id out of range"
+    assert np.unique(got).shape[0] == kp, f"{where}: duplicate ids {got}"
+    kth = top_scores[kp - 1]
+    tol_k = rtol * abs(kth)
+    if m < n_docs:
+        assert top_scores[m - 1] < kth - tol_k, (f"{where}: the oracle list of {m} is too short "
+                                                 f"to decide ties at the k-th score")
+    pos = {int(d): i for i, d in enumerate(top_ids[:m])}
+    for r, d in enumerate(got.tolist()):
+        assert d in pos, f"{where}: returned id {d} is not within the tolerance of the top {kp}"
+        b = top_scores[pos[d]]
+        assert abs(sc[r] - b) <= rtol * abs(b), \
+            f"{where}: score mismatch at rank {r}: got {sc[r]} want {b}"
+        assert b >= kth - tol_k, f"{where}: returned id {d} ({b}) below the k-th score {kth}"
+    must = top_ids[:kp][top_scores[:kp] > kth + tol_k]
+    missing = np.setdiff1d(must, got)
+    assert missing.shape[0] == 0, f"{where}: top ids {missing[:5]} missing"
+    ds = np.diff(sc)
+    assert (ds <= 0).all(), f"{where}: scores not sorted descending"
+    assert (np.diff(got)[ds == 0] > 0).all(), f"{where}: equal scores not ordered by doc id"

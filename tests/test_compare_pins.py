@@ -178,3 +178,46 @@ def test_against_oracle_on_random_corpora():
             _expect_fail(bad, s2, full=full, ab=ab, k=k)
             checked += 1
     assert checked >= 10
+
+
+def test_list_checker_agrees_with_the_full_checker():
+    """check_topk_with_list (the oracle's top-m list in place of its full
+    score vector) accepts and rejects what check_topk does, on random
+    non-negative score vectors with ties and on perturbed answers."""
+    from oracle.compare import check_topk_with_list
+    rng = np.random.default_rng(77)
+    n_same = 0
+    for trial in range(400):
+        n = int(rng.integers(5, 60))
+        full = np.round(rng.exponential(1.0, n), 2)  # ties
+        k = int(rng.integers(1, 8))
+        order = np.lexsort((np.arange(n), -full))
+        m = min(n, k + 20)
+        top_ids, top_sc = order[:m], full[order[:m]]
+        ids, sc = _exact(full, k)
+        mode = trial % 4
+        if mode == 1 and min(k, n) >= 2:  # swap in a document from below
+            ids = ids.copy()
+            ids[-1] = order[min(n - 1, k + int(rng.integers(0, 5)))]
+            sc = sc.copy()
+            sc[-1] = full[ids[-1]]
+        elif mode == 2:  # a score off
+            sc = sc.copy()
+            sc[0] *= 1 + 3e-5
+        elif mode == 3 and min(k, n) >= 2:  # unsorted
+            ids, sc = ids[::-1].copy(), sc[::-1].copy()
+        try:
+            check_topk(ids, sc, full, full, k)
+            ok_full = True
+        except AssertionError:
+            ok_full = False
+        try:
+            check_topk_with_list(ids, sc, top_ids, top_sc, k, n)
+            ok_list = True
+        except AssertionError as e:
+            ok_list = False
+            if "too short" in str(e):
+                continue
+        assert ok_full == ok_list, (trial, mode, full, ids, sc)
+        n_same += 1
+    assert n_same > 300

@@ -1,19 +1,24 @@
-"""Full-size parity on the 1M-document workload, in the launch configuration
-the benchmark times (one batched call over all 10,000 queries).
+"""Full-size parity, in the launch configuration the benchmark times (one
+batched call over each workload's whole query batch).
 
-1,000,000 documents, vocab 200,000 Zipf(1.05), lognormal(60, 0.6) lengths;
-10,000 queries of 1..16 tokens with the 100 head terms removed; k = 10 and
-100; all five variants.  Structure (|D|, TF, DF, indptr, indices) is compared
-in full against the oracle's; scores S - S0 in full within 1e-5 of their
-scale; the top-k of a seeded sample of queries against the oracle's lazy
-exhaustive scores (each oracle query scores all 1M documents).
+zipf-1m: 1,000,000 documents, vocab 200,000 Zipf(1.05), lognormal(60, 0.6)
+lengths; 10,000 queries of 1..16 tokens with the 100 head terms removed;
+k = 10 and 100; all five variants.  Structure (|D|, TF, DF, indptr, indices)
+is compared in full against the oracle's; scores S - S0 in full within 1e-5
+of their scale; the top-k of a seeded sample of queries against the oracle's
+lazy exhaustive scores; and, for Lucene at k = 10, every one of the 10,000
+queries against the oracle's own top 42 (lazy exhaustive, all host cores).
 """
+import os
+
 import numpy as np
 import pytest
 
 import oracle
-from oracle.compare import check_topk
+from oracle.compare import check_topk, check_topk_with_list
 from paper_2407_03618_gb300 import synth
+
+THREADS = os.cpu_count() or 1
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -64,6 +69,11 @@ def test_fullsize_parity(workload, variant):
         for i in W["sample"]:
             full, ab = oracle.score_all(orc, q.query(int(i)), with_abs=True)
             check_topk(ids[i], sc[i], full, ab, k, where=f"{variant} k={k} q{i}")
+        if variant == "lucene" and k == 10:  # every query of the batch
+            top_ids, top_sc = oracle.topk(orc, q.tokens, q.offsets, k + 32, n_threads=THREADS)
+            for i in range(q.n_queries):
+                check_topk_with_list(ids[i], sc[i], top_ids[i], top_sc[i], k, c.n_docs,
+                                     where=f"all {variant} k={k} q{i}")
     ix.close()
 
 
@@ -71,11 +81,13 @@ def test_fullsize_parity(workload, variant):
 # passage-8.8m at full size: 8.8M documents (lognormal(56, 0.5)), vocab 1M
 # Zipf(1.0), ~433M CSC entries, 7,000 queries of geometric length (mean 6, at
 # most 32) with head terms, k = 10 / 100 / 1000 in the batched launch the
-# bench would time; structure checked in full on sampled columns, the top-k
-# of a seeded query sample against the oracle's exhaustive scores.
-# long-5m's shape (lognormal(300, 0.8) documents, vocab 2M Zipf(1.1), 20..60
-# tokens per query including head terms, BM25+, k = 100) at 1M documents:
-# 1.5 G tokens would take the oracle minutes to build.
+# bench times; structure bit-exact in full, stored scores on sampled columns,
+# the top 10 of a seeded sample of 200 queries against the oracle's top 42
+# and the top 100 / 1000 of 8 of them against its exhaustive scores.
+# long-5m at full size: 5M documents of lognormal(300, 0.8) lengths, vocab 2M
+# Zipf(1.1), ~0.9G CSC entries, 5,000 queries of 20..60 tokens including head
+# terms, BM25+ with its shift, k = 100; structure bit-exact in full, the top
+# 100 of a seeded sample of 40 queries against the oracle's top 164.
 
 @pytest.mark.parametrize("name", ["passage", "long"])
 def test_large_shapes(name):
@@ -85,12 +97,11 @@ def test_large_shapes(name):
     from paper_2407_03618_gb300 import bm25
     w = synth.WORKLOADS[name]
     dev = torch.device("cuda:0")
+    c, q = w.corpus(), w.queries()
     if name == "passage":
-        c, q, variant, ks, n_sample = w.corpus(), w.queries(), "lucene", (10, 100, 1000), 8
+        variant, ks, n_list, n_full = "lucene", (10, 100, 1000), 200, 8
     else:
-        c = synth.make_corpus(1_000_000, w.vocab, w.zipf_s, w.doc_length, seed=0)
-        q = w.queries()
-        variant, ks, n_sample = "bm25+", (100,), 8
+        variant, ks, n_list, n_full = "bm25+", (100,), 40, 0
     prm = w.params
     ix = bm25.Index.build(torch.from_numpy(c.tokens).to(dev),
                           torch.from_numpy(c.doc_offsets).to(dev), c.vocab, variant,
@@ -99,31 +110,39 @@ def test_large_shapes(name):
                        prm["b"], prm["delta"])
     info = ix.info()
     assert info["nnz"] == orc.nnz
-    ex = ix.export()
     # the structure in full (bit-exact), the stored scores on sampled columns
-    assert np.array_equal(ex["df"], orc.df.astype(np.int32))
-    assert np.array_equal(ex["indptr"], orc.indptr)
-    assert np.array_equal(ex["doc_len"], orc.doc_len.astype(np.int32))
-    assert np.array_equal(ex["indices"], orc.indices)
-    assert np.array_equal(ex["tf"], orc.csc_tf)
+    for key, want in (("df", orc.df.astype(np.int32)), ("indptr", orc.indptr),
+                      ("doc_len", orc.doc_len.astype(np.int32)), ("indices", orc.indices),
+                      ("tf", orc.csc_tf)):
+        got = ix.export([key])[key]
+        assert np.array_equal(got, want), key
+        del got
+    data = ix.export(["data"])["data"]
     rng = np.random.default_rng(5)
     cols = np.unique(np.concatenate([np.arange(20), rng.integers(0, c.vocab, 200)]))
     for t in cols:  # the head terms and a random sample
         a, b = orc.indptr[t], orc.indptr[t + 1]
         full_s = orc.csc_delta[a:b] + orc.s0[t]
         scale = np.maximum(np.abs(orc.csc_delta[a:b]), np.abs(full_s))
-        assert (np.abs(ex["data"][a:b] - orc.csc_delta[a:b]) <= 1e-5 * scale + 1e-30).all()
-    del ex
+        assert (np.abs(data[a:b] - orc.csc_delta[a:b]) <= 1e-5 * scale + 1e-30).all()
+    del data
     qt = torch.from_numpy(q.tokens).to(dev)
     qo = torch.from_numpy(q.offsets).to(dev)
-    sample = rng.choice(q.n_queries, n_sample, replace=False)
+    sample = rng.choice(q.n_queries, n_list, replace=False)
     rows = {}
     for k in ks:
         ids, sc = ix.retrieve(qt, qo, k)
         ix.sync_status()
         rows[k] = (ids.cpu().numpy()[sample], sc.cpu().numpy()[sample])
     ix.close()
+    sub = q.subset(sample)
+    k0 = ks[0]
+    top_ids, top_sc = oracle.topk(orc, sub.tokens, sub.offsets, k0 + max(32, k0 * 64 // 100),
+                                  n_threads=THREADS)
     for j, i in enumerate(sample):
+        check_topk_with_list(rows[k0][0][j], rows[k0][1][j], top_ids[j], top_sc[j], k0,
+                             c.n_docs, where=f"{name} k={k0} q{i}")
+    for j, i in enumerate(sample[:n_full]):
         full, ab = oracle.score_all(orc, q.query(int(i)), with_abs=True)
-        for k in ks:
+        for k in ks[1:]:
             check_topk(rows[k][0][j], rows[k][1][j], full, ab, k, where=f"{name} k={k} q{i}")
