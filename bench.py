@@ -724,40 +724,21 @@ def serving(args, bm25, corpus, queries, tok, off, dev, w, plan, plain):
                 reqs.append(queries.query(int(rng.integers(0, queries.n_queries))))
             else:
                 reqs.append(synth.zipf_sampler(vocabs[which[i]], 1.05)(rng, int(lens[i])))
-        gaps = rng.exponential(1.0 / rate, n_req)
+        arrival = np.cumsum(rng.exponential(1.0 / rate, n_req))
         srv.stats(reset=True)
-        tickets = []
         t0 = time.perf_counter()
-        due = t0
-        for i in range(n_req):
-            due += gaps[i]
-            while time.perf_counter() < due:
-                pass
-            tickets.append(srv.submit(int(which[i]), reqs[i], int(ks[i])))
+        tickets = srv.replay(which, reqs, ks, arrival)  # submitted natively at their times
         t_sub = time.perf_counter() - t0
         for i, tk in enumerate(tickets):
             srv.poll(tk, int(ks[i]))
         st = srv.stats()
-        # the same requests and arrival times through the plain path: one
-        # query per call (host buffers in and out, one launch sequence per
-        # query), served in arrival order by one thread
-        plain_lat = []
-        houts = {kk: (np.zeros((1, kk), np.int32), np.zeros((1, kk), np.float32))
-                 for kk in (10, 100, 1000)}
+        # the same requests at the same arrival times through the plain path:
+        # one query per call (host buffers in and out), served in order
         t0 = time.perf_counter()
-        due = t0
-        for i in range(n_req):
-            due += gaps[i]
-            while time.perf_counter() < due:
-                pass
-            qq = np.asarray(reqs[i], np.int32)
-            idx[int(which[i])].retrieve_host(qq, np.array([0, qq.shape[0]], np.int64),
-                                             int(ks[i]), out=houts[int(ks[i])])
-            plain_lat.append(time.perf_counter() - due)
+        plain_lat = np.sort(bm25.replay_plain(idx, which, reqs, ks, arrival)) / 1e3
         p_span = time.perf_counter() - t0
-        plain_lat.sort()
         out["rates"].append({"offered_qps": rate, "requests": n_req,
-                             "submit_s": t_sub,
+                             "submit_s": t_sub, "arrivals_s": float(arrival[-1]),
                              "achieved_qps": st["completed"] / max(st["span_us"] / 1e6, 1e-9),
                              "span_s": st["span_us"] / 1e6,
                              "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
@@ -766,18 +747,20 @@ def serving(args, bm25, corpus, queries, tok, off, dev, w, plan, plain):
                              "failed": st["failed"],
                              "plain_same_arrivals": {
                                  "achieved_qps": n_req / p_span,
-                                 "p50_ms": plain_lat[len(plain_lat) // 2] * 1e3,
-                                 "p99_ms": plain_lat[int(0.99 * (len(plain_lat) - 1))] * 1e3,
-                                 "max_ms": plain_lat[-1] * 1e3}})
+                                 "p50_ms": float(plain_lat[len(plain_lat) // 2]),
+                                 "p99_ms": float(plain_lat[int(0.99 * (len(plain_lat) - 1))]),
+                                 "max_ms": float(plain_lat[-1])}})
     srv.close()
     for ix in idx:
         ix.close()
     out["plain_path_host"] = plain.get("host")
-    out["note"] = ("achieved_qps = completed / (first submit .. last completion, recorded by "
-                   "the server); latency = submit to result on the host.  plain_same_arrivals: "
-                   "the same requests at the same arrival times through the one-query-per-call "
-                   "host entry point, served in order by one thread (latency = arrival to "
-                   "result).  plain_path_host: that entry point back to back, no queueing")
+    out["note"] = ("requests submitted at their Poisson arrival times by a native loop "
+                   "(bm25_server_replay); achieved_qps = completed / (first submit .. last "
+                   "completion, recorded by the server); latency = submit to result on the host.  "
+                   "plain_same_arrivals: the same requests at the same arrival times through the "
+                   "one-query-per-call host entry point, served in order natively "
+                   "(bm25_replay_plain; latency = arrival to result).  plain_path_host: that "
+                   "entry point back to back, no queueing")
     return out
 
 

@@ -490,6 +490,30 @@ int bm25_server_submit(bm25_server* server, int32_t index_id, const int32_t* tok
 int bm25_server_poll(bm25_server* server, int64_t ticket, int32_t* ids, float* scores,
                      int32_t timeout_us);
 
+/* Load replay, for measuring a server against the plain path under one
+ * arrival process (the paper has no serving layer).  Request i asks index
+ * index_ids[i] for its top ks[i] of the query tokens[offsets[i] ..
+ * offsets[i+1]) (HOST arrays) and arrives arrival_s[i] seconds after the
+ * call starts (non-decreasing).
+ *
+ * bm25_server_replay submits each request at its arrival time from the
+ * calling thread and returns after the last submit; tickets[n] (HOST) get
+ * the tickets (poll them as usual; the server's statistics time each request
+ * from its submit).
+ *
+ * bm25_replay_plain answers the same requests one at a time, in order, each
+ * by its own bm25_retrieve_host call (one query per call: copies in, the
+ * launches, copies out, synchronise) on cuda_stream, starting each at its
+ * arrival time or when the previous one is done; latency_us[n] (HOST) gets
+ * each request's time from its arrival to its result. */
+int bm25_server_replay(bm25_server* server, int32_t n, const int32_t* index_ids,
+                       const int32_t* tokens, const int64_t* offsets, const int32_t* ks,
+                       const double* arrival_s, int64_t* tickets);
+int bm25_replay_plain(const bm25_index* const* indexes, int32_t n_indexes, int32_t n,
+                      const int32_t* index_ids, const int32_t* tokens, const int64_t* offsets,
+                      const int32_t* ks, const double* arrival_s, double* latency_us,
+                      void* cuda_stream);
+
 /* Counters and latency percentiles since the last reset (reset != 0 clears them). */
 int bm25_server_stats_get(bm25_server* server, int reset, bm25_server_stats* out);
 

@@ -105,6 +105,8 @@ def load(path: str | None = None):
         "bm25_server_submit": (cint, [P, i32, P, i32, i32, P]),
         "bm25_server_poll": (cint, [P, i64, P, P, i32]),
         "bm25_server_stats_get": (cint, [P, cint, P]),
+        "bm25_server_replay": (cint, [P, i32, P, P, P, P, P, P]),
+        "bm25_replay_plain": (cint, [P, i32, i32, P, P, P, P, P, P, P]),
         "bm25_server_destroy": (None, [P]),
         "bm25_index_set_plan": (cint, [P, P]),
         "bm25_index_get_plan": (cint, [P, P]),
@@ -244,6 +246,24 @@ def tokenize_queries(vocab: Vocab, text, offsets, stream=None):
                                         ids.data_ptr(), cap, offs.data_ptr(), ctypes.byref(nt),
                                         _stream(stream)))
     return ids[:nt.value], offs
+
+
+def replay_plain(indexes: list, index_ids, queries: list, ks, arrival_s, stream=None):
+    """The same requests through the one-query-per-call host path, served
+    in order natively; returns each request's latency in microseconds."""
+    n = len(queries)
+    arr_ix = (ctypes.c_void_p * len(indexes))(*[ix.handle.value for ix in indexes])
+    ids_a = np.ascontiguousarray(index_ids, np.int32)
+    ks_a = np.ascontiguousarray(ks, np.int32)
+    arr = np.ascontiguousarray(arrival_s, np.float64)
+    off = np.zeros(n + 1, np.int64)
+    off[1:] = np.cumsum([len(x) for x in queries])
+    tok = (np.concatenate([np.asarray(x, np.int32) for x in queries]) if off[-1]
+           else np.zeros(1, np.int32))
+    lat = np.zeros(max(n, 1), np.float64)
+    _check(load().bm25_replay_plain(arr_ix, len(indexes), n, _ptr(ids_a), _ptr(tok), _ptr(off),
+                                    _ptr(ks_a), _ptr(arr), _ptr(lat), _stream(stream)))
+    return lat[:n]
 
 
 def release_cached():
@@ -621,6 +641,22 @@ class Server:
             return None
         _check(rc)
         return ids, sc
+
+    def replay(self, index_ids, queries: list, ks, arrival_s) -> list:
+        """Submit request i (queries[i] on index_ids[i] at k = ks[i]) at
+        arrival_s[i] seconds from now, natively; returns the tickets."""
+        n = len(queries)
+        ids_a = np.ascontiguousarray(index_ids, np.int32)
+        ks_a = np.ascontiguousarray(ks, np.int32)
+        arr = np.ascontiguousarray(arrival_s, np.float64)
+        off = np.zeros(n + 1, np.int64)
+        off[1:] = np.cumsum([len(x) for x in queries])
+        tok = (np.concatenate([np.asarray(x, np.int32) for x in queries]) if off[-1]
+               else np.zeros(1, np.int32))
+        tickets = np.zeros(max(n, 1), np.int64)
+        _check(load().bm25_server_replay(self.handle, n, _ptr(ids_a), _ptr(tok), _ptr(off),
+                                         _ptr(ks_a), _ptr(arr), _ptr(tickets)))
+        return tickets[:n].tolist()
 
     def stats(self, reset: bool = False) -> dict:
         st = ServerStats()

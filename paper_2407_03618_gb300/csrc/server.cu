@@ -460,6 +460,56 @@ int bm25_server_submit(bm25_server* sv, int32_t index_id, const int32_t* tokens,
     return BM25_OK;
 }
 
+int bm25_server_replay(bm25_server* sv, int32_t n, const int32_t* index_ids,
+                       const int32_t* tokens, const int64_t* offsets, const int32_t* ks,
+                       const double* arrival_s, int64_t* tickets)
+{
+    clear_error();
+    if (!sv || n < 0 || (n > 0 && (!index_ids || !offsets || !ks || !arrival_s || !tickets)))
+        return set_error(BM25_E_INVALID, "bad argument");
+    const auto t0 = Clock::now();
+    for (int32_t i = 0; i < n; i++) {
+        const auto due = t0 + std::chrono::duration_cast<Clock::duration>(
+                                  std::chrono::duration<double>(arrival_s[i]));
+        while (Clock::now() < due) {
+        }
+        const int64_t a = offsets[i], b = offsets[i + 1];
+        BM25_TRY(bm25_server_submit(sv, index_ids[i], tokens ? tokens + a : nullptr,
+                                    (int32_t)(b - a), ks[i], &tickets[i]));
+    }
+    return BM25_OK;
+}
+
+int bm25_replay_plain(const bm25_index* const* indexes, int32_t n_indexes, int32_t n,
+                      const int32_t* index_ids, const int32_t* tokens, const int64_t* offsets,
+                      const int32_t* ks, const double* arrival_s, double* latency_us,
+                      void* cuda_stream)
+{
+    clear_error();
+    if (!indexes || n_indexes < 1 || n < 0 ||
+        (n > 0 && (!index_ids || !offsets || !ks || !arrival_s || !latency_us)))
+        return set_error(BM25_E_INVALID, "bad argument");
+    int32_t kmax = 1;
+    for (int32_t i = 0; i < n; i++)
+        kmax = std::max(kmax, ks[i]);
+    std::vector<int32_t> ids((size_t)kmax);
+    std::vector<float> scores((size_t)kmax);
+    const auto t0 = Clock::now();
+    for (int32_t i = 0; i < n; i++) {
+        if (index_ids[i] < 0 || index_ids[i] >= n_indexes)
+            return set_error(BM25_E_INVALID, "index id %d out of range", index_ids[i]);
+        const auto due = t0 + std::chrono::duration_cast<Clock::duration>(
+                                  std::chrono::duration<double>(arrival_s[i]));
+        while (Clock::now() < due) {
+        }
+        const int64_t off[2] = {0, offsets[i + 1] - offsets[i]};
+        BM25_TRY(bm25_retrieve_host(indexes[index_ids[i]], tokens ? tokens + offsets[i] : nullptr,
+                                    off, 1, ks[i], ids.data(), scores.data(), cuda_stream));
+        latency_us[i] = std::chrono::duration<double, std::micro>(Clock::now() - due).count();
+    }
+    return BM25_OK;
+}
+
 int bm25_server_poll(bm25_server* sv, int64_t ticket, int32_t* ids, float* scores,
                      int32_t timeout_us)
 {
