@@ -19,7 +19,10 @@
 //                     the ones that clear the query's running threshold and
 //                     select the tile's best k' (including the lowest-id
 //                     untouched documents, score 0, when they can matter)
-//   R3 k_merge        per tiled query: the k' best of the tiles' candidates,
+//   R3 k_merge_level  (large k' over many tiles) merge tree: groups of tiles
+//                     of one query cut to their k' best, in place, until
+//                     the candidates left fit one block's shared memory
+//      k_merge        per tiled query: the k' best of the tiles' candidates,
 //                     re-keyed on the final score, sorted, written out
 //   R4 k_dense_topk   per dense-path query: scatter into a dense FP32 vector
 //                     in global memory (L2-resident), claim, select, write out
@@ -38,6 +41,7 @@ typedef unsigned long long u64;
 constexpr int kTokChunk = 64;          // query tokens staged in shared memory at a time
 constexpr int kMergeThreads = 256;
 constexpr int kMergeBufCap = 4096;     // candidates a merge gathers into shared memory
+constexpr int kTreeKeys = 8192;        // candidates a merge-tree block gathers at most
 constexpr uint32_t kZeroKey = 0x80000000u;  // order_f32(0.0f)
 // A tiled-path record's k field: k' in the low 16 bits, and kNegScores when
 // one of the query's columns holds negative scores (Robertson terms with
@@ -1238,14 +1242,80 @@ __device__ void finish_row(u64* sel, int sz, uint32_t kp, int32_t kout, double s
 }
 
 // ---- R3 -----------------------------------------------------------------------
-// Per query of the tiled path (block b: record b): gather the tiles'
-// candidates (tcount[tile * n_long + b] of them in that item's kstride
-// slots), select the k' best and finish the query's row.  Dynamic shared
-// memory: sel[pow2 >= kstride] | buf[buf_cap] keys | pre[n_tiles + 1].
+// Merge tree.  A query's tiles all start with no threshold when they run in
+// the same wave (a small batch), so each hands over its k' best: up to
+// n_tiles x k' candidates, too many for one block to select from quickly
+// when k' is large.  One level merges groups of `fan` consecutive virtual
+// tiles (tile j * tstride, j = 0, 1, ...) of each query in place: block
+// (g, b) = (blockIdx.x / nb, blockIdx.x % nb) gathers the candidates of
+// group g of query record b into shared memory (fan * kstride keys at
+// most), keeps their k' best (all of them when there are no more than k')
+// and writes them, with their count, to the slots of the group's first
+// tile.  The next level, or k_merge, then reads the tiles at stride
+// tstride * fan.  A group of one tile is left as it is.  Any k' keys of a
+// query's candidates that are not among its k' best stay out of the final
+// selection either way, so the result is the one selection over all of
+// them would give.
+__global__ void __launch_bounds__(kMergeThreads)
+    k_merge_level(u64* __restrict__ cand, uint32_t* __restrict__ tcount,
+                  const int4* __restrict__ lrec, const uint32_t* __restrict__ ctr,
+                  int32_t n_tiles, int32_t tstride, int32_t fan, int32_t kstride, int32_t nb)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SelectState st;
+    __shared__ uint32_t pre[kMergeThreads + 1];
+    const int32_t nl = (int32_t)ctr[0];
+    const int32_t b = (int32_t)(blockIdx.x % (uint32_t)nb);
+    const int32_t g = (int32_t)(blockIdx.x / (uint32_t)nb);
+    if (b >= nl)
+        return;
+    const int64_t n_v = ((int64_t)n_tiles + tstride - 1) / tstride;
+    const int64_t v0 = (int64_t)g * fan;
+    const int32_t nv = (int32_t)min((int64_t)fan, n_v - v0);  // fan <= kMergeThreads
+    if (nv <= 1)
+        return;
+    const uint32_t kp = (uint32_t)(lrec[b].w & kKpMask);
+    u64* buf = reinterpret_cast<u64*>(smem);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    auto slot0 = [&](int64_t v) { return (v * tstride * nl + b); };  // item of virtual tile v
+    const uint32_t c = tid < nv ? min(tcount[slot0(v0 + tid)], (uint32_t)kstride) : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_sum(c, st.red, &tot);
+    if (tid < nv)
+        pre[tid] = ex;
+    if (tid == 0) {
+        pre[nv] = tot;
+        st.ctr = 0;
+    }
+    __syncthreads();
+    for (int j = warp; j < nv; j += kMergeThreads / 32) {  // one warp per tile
+        const u64* src = cand + slot0(v0 + j) * kstride;
+        const uint32_t a = pre[j], cj = pre[j + 1] - a;
+        for (uint32_t s = lane; s < cj; s += 32)
+            buf[a + s] = src[s];
+    }
+    __syncthreads();  // every key read before the group's first slots are rewritten
+    u64* out = cand + slot0(v0) * kstride;
+    if (tot <= kp) {
+        for (uint32_t i = tid; i < tot; i += kMergeThreads)
+            out[i] = buf[i];
+    } else {
+        block_select_idx<false>(st, tot, tot, kp, 0, 0ull, [&](uint32_t i) { return buf[i]; },
+                                [&](u64 key, uint32_t slot) { out[slot] = key; });
+    }
+    if (tid == 0)
+        tcount[slot0(v0)] = min(tot, kp);
+}
+
+// Per query of the tiled path (block b: record b): gather the candidates of
+// the virtual tiles j * tstride (tcount[tile * n_long + b] of them in that
+// item's kstride slots), select the k' best and finish the query's row.
+// Dynamic shared memory: sel[pow2 >= kstride] | buf[buf_cap] keys |
+// pre[n_v + 1], n_v = ceil(n_tiles / tstride).
 __global__ void __launch_bounds__(kMergeThreads)
     k_merge(const u64* __restrict__ cand, const uint32_t* __restrict__ tcount,
             const int4* __restrict__ lrec, const uint32_t* __restrict__ ctr, int32_t n_tiles,
-            int32_t kstride, int32_t kout, const double* __restrict__ shift,
+            int32_t tstride, int32_t kstride, int32_t kout, const double* __restrict__ shift,
             int32_t* __restrict__ out_ids, float* __restrict__ out_scores, int32_t buf_cap,
             int32_t id_base)
 {
@@ -1268,33 +1338,35 @@ __global__ void __launch_bounds__(kMergeThreads)
     u64* buf = sel + sz_all;
     uint32_t* pre = reinterpret_cast<uint32_t*>(buf + buf_cap);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t n_v = (int32_t)(((int64_t)n_tiles + tstride - 1) / tstride);
+    auto item_of = [&](int32_t v) { return (int64_t)v * tstride * nl + b; };
 
     // exclusive scan of the per-tile counts
     uint32_t carry = 0;
-    for (int t0 = 0; t0 < n_tiles; t0 += kMergeThreads) {
+    for (int t0 = 0; t0 < n_v; t0 += kMergeThreads) {
         const int t = t0 + tid;
         // (at most kstride: a count left unwritten by a tile kernel that gave
         // up must not send the gather past the item's slots)
-        const uint32_t c = t < n_tiles ? min(tcount[(int64_t)t * nl + b], (uint32_t)kstride) : 0u;
+        const uint32_t c = t < n_v ? min(tcount[item_of(t)], (uint32_t)kstride) : 0u;
         uint32_t tot;
         const uint32_t ex = block_exclusive_sum(c, st.red, &tot);
-        if (t < n_tiles)
+        if (t < n_v)
             pre[t] = carry + ex;
         carry += tot;
     }
     if (tid == 0)
-        pre[n_tiles] = carry;
+        pre[n_v] = carry;
     for (int i = tid; i < sz; i += kMergeThreads)
         sel[i] = 0ull;
     if (tid == 0)
         st.ctr = 0;
     __syncthreads();
-    const uint32_t total = pre[n_tiles];  // >= k': the tiles hold enough candidates
+    const uint32_t total = pre[n_v];  // >= k': the tiles hold enough candidates
     const bool gathered = total <= (uint32_t)buf_cap;
     if (gathered) {  // one warp per tile copies its candidates
-        for (int t = warp; t < n_tiles; t += kMergeThreads / 32) {
+        for (int t = warp; t < n_v; t += kMergeThreads / 32) {
             const uint32_t c = pre[t + 1] - pre[t];
-            const u64* src = cand + ((int64_t)t * nl + b) * kstride;
+            const u64* src = cand + item_of(t) * kstride;
             for (uint32_t s = lane; s < c; s += 32)
                 buf[pre[t] + s] = src[s];
         }
@@ -1303,7 +1375,7 @@ __global__ void __launch_bounds__(kMergeThreads)
     auto get = [&](uint32_t i) -> u64 {
         if (gathered)
             return buf[i];
-        int a = 0, e = n_tiles;  // pre[a] <= i < pre[e]
+        int a = 0, e = n_v;  // pre[a] <= i < pre[e]
         while (e - a > 1) {
             const int mid = (a + e) >> 1;
             if (pre[mid] <= i)
@@ -1311,7 +1383,7 @@ __global__ void __launch_bounds__(kMergeThreads)
             else
                 e = mid;
         }
-        return cand[((int64_t)a * nl + b) * kstride + (i - pre[a])];
+        return cand[item_of(a) * kstride + (i - pre[a])];
     };
     block_select_idx<true>(st, total, total, kp, 0, 0ull, get, [&](u64 key, uint32_t slot) {
         if (slot < kp)
@@ -1941,12 +2013,29 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
                                                                 tile_threads, smem));
     if (per_sm < 1)
         return set_error(BM25_E_INVALID, "doc tile of %d documents does not fit on an SM", W);
+    // the merge tree's levels: groups of `fan` tiles while the candidates a
+    // query can have left exceed what k_merge gathers
+    const int32_t fan = (int32_t)std::min<int64_t>(kMergeThreads,
+                                                   std::max<int64_t>(2, kTreeKeys / kstride));
+    const size_t tsmem = (size_t)fan * kstride * sizeof(u64);
+    int32_t tstride = 1, levels = 0;
+    if (tsmem <= (size_t)di.max_smem_optin) {
+        for (int64_t n_v = n_tiles; n_v > 1 && n_v * kstride > kMergeBufCap;
+             n_v = (n_v + fan - 1) / fan)
+            levels++;
+        if (levels > 0)
+            BM25_CUDA_TRY(cudaFuncSetAttribute(
+                k_merge_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
+    }
+    int32_t n_final = n_tiles;
+    for (int l = 0; l < levels; l++)
+        n_final = (n_final + fan - 1) / fan;
     int sz_all = 1;
     while (sz_all < kstride)
         sz_all <<= 1;
-    const int32_t buf_cap = (int32_t)std::min<int64_t>(kMergeBufCap, (int64_t)n_tiles * kstride);
+    const int32_t buf_cap = (int32_t)std::min<int64_t>(kMergeBufCap, (int64_t)n_final * kstride);
     const size_t msmem = (size_t)sz_all * sizeof(u64) + (size_t)buf_cap * sizeof(u64) +
-                         (size_t)(n_tiles + 1) * sizeof(uint32_t);
+                         (size_t)(n_final + 1) * sizeof(uint32_t);
     BM25_CUDA_TRY(cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)msmem));
     if (g.dense_ctas > 0)
@@ -1983,11 +2072,23 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
         }
         count_launch();
         BM25_LAUNCH_CHECK();
+        tstride = 1;
+        for (int l = 0; l < levels; l++) {
+            const int64_t n_v = ((int64_t)n_tiles + tstride - 1) / tstride;
+            const int64_t n_groups = (n_v + fan - 1) / fan;
+            ProfileScope ps_("k_merge_level", s);
+            k_merge_level<<<(unsigned)(n_groups * nb), kMergeThreads, tsmem, s>>>(
+                ws->cand, ws->tcount, ws->lrec, ws->ctr, n_tiles, tstride, fan, kstride, nb);
+            count_launch();
+            BM25_LAUNCH_CHECK();
+            tstride *= fan;
+        }
         {
             ProfileScope ps_("k_merge", s);
             k_merge<<<nb, kMergeThreads, msmem, s>>>(ws->cand, ws->tcount, ws->lrec, ws->ctr,
-                                                     n_tiles, kstride, kmax, ws->shift, ids,
-                                                     scores, buf_cap, (int32_t)ix->doc_offset);
+                                                     n_tiles, tstride, kstride, kmax, ws->shift,
+                                                     ids, scores, buf_cap,
+                                                     (int32_t)ix->doc_offset);
         }
         count_launch();
         BM25_LAUNCH_CHECK();

@@ -440,6 +440,27 @@ def test_sub_batches_when_candidates_exceed_the_budget(torch_dev):
     ix.close()
 
 
+@pytest.mark.parametrize("k", [100, 1000, 2500])
+def test_merge_tree_for_large_k(torch_dev, k):
+    """Six queries over 98 doc tiles of 1024: all their tiles run in the first
+    wave with no threshold, so each hands over its k' best, and the merge tree
+    cuts groups of tiles to their k' best in place before the final merge
+    (groups of 81, 8 and 3 tiles: one, two and five levels, with ragged last
+    groups and groups of one tile).  Also per-query k below the row width."""
+    c = synth.make_corpus(100_000, 20_000, 1.05, ("poisson", 20), seed=61)
+    q = synth.make_queries(6, 20_000, 1.05, ("uniform", 2, 8), seed=62)
+    ix = _build(torch_dev, c, "lucene")
+    orc = oracle.build(c.tokens, c.doc_offsets, c.vocab, oracle.LUCENE)
+    ix.set_plan(2, 1024, 256)
+    _check_retrieval(torch_dev, ix, orc, q, k, where=f"tree k={k}")
+    ks = np.array([1, k, 7, k // 2, 100, 3], np.int32)
+    ids, sc = ix.retrieve_batch(_to(torch_dev, q.tokens), _to(torch_dev, q.offsets), k,
+                                q_k=_to(torch_dev, ks))
+    ix.sync_status()
+    _check_rows(ids.cpu().numpy(), sc.cpu().numpy(), orc, q, ks, c.n_docs, f"tree per-k k={k}")
+    ix.close()
+
+
 @pytest.mark.parametrize("name", ["tiled", "mixed"])
 def test_cuda_graph_capture_and_replay(torch_dev, name):
     """A reserved workspace lets a call be captured in a CUDA graph; replays
