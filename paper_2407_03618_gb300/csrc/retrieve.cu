@@ -883,30 +883,33 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : (LAZY ? 3 : 4))
                 d0u = (uint32_t)tile * (uint32_t)W;
                 wdu = (uint32_t)min((int64_t)W, n_docs - (int64_t)d0u);
             }
-            // Entries come in pairs of one column (segments start on even slots
-            // and span an even number of them), so one 16-byte load gives a lane
-            // two postings of distinct documents.  Pair i is taken by lane
-            // i % 32 of warp (i / 32) % CW.
-            const int32_t n_pairs = min(max(nl.x, 0), stage_entries) >> 1;
-            const uint4* sb4 = reinterpret_cast<const uint4*>(stage + (size_t)s * stage_entries);
-            for (int32_t i0 = warp * 32; i0 < n_pairs; i0 += NT) {
-                const int32_t i = i0 + lane;
-                const uint4 pe = i < n_pairs ? sb4[i] : make_uint4(kPostPad, 0u, kPostPad, 0u);
-                const uint32_t dl0 = pe.x - d0u, dl1 = pe.z - d0u;
-                float v0 = __uint_as_float(pe.y), v1 = __uint_as_float(pe.w);
+            // Lane l of a warp takes entries 64 j + l and 64 j + 32 + l of the
+            // buffer (chunk j of 64 entries to warp j % CW), so the 32 adds of one
+            // instruction go to consecutive postings: a dense column's documents
+            // then fall in distinct shared-memory banks.
+            const int32_t n_e = min(max(nl.x, 0), stage_entries);
+            const uint2* sb = stage + (size_t)s * stage_entries;
+            for (int32_t e0 = warp * 64; e0 < n_e; e0 += 2 * NT) {
+                const int32_t ea = e0 + lane, eb = ea + 32;
+                const uint2 pa = ea < n_e ? sb[ea] : make_uint2(kPostPad, 0u);
+                const uint2 pb = eb < n_e ? sb[eb] : make_uint2(kPostPad, 0u);
+                const uint32_t dl0 = pa.x - d0u, dl1 = pb.x - d0u;
+                float v0 = __uint_as_float(pa.y), v1 = __uint_as_float(pb.y);
                 if (LAZY) {
-                    // the pair's token: the last one starting at or before entry 2i
+                    // an entry's token: the last one starting at or before it
                     const SegTable& tb = segt[s];
-                    int lo = 0, hi = 65;
-                    while (hi - lo > 1) {
-                        const int mid = (lo + hi) >> 1;
-                        if ((int32_t)tb.start[mid] <= 2 * i)
-                            lo = mid;
-                        else
-                            hi = mid;
-                    }
-                    const float c = tb.coef[min(lo, 63)];
-                    auto lazy_v = [&](uint32_t w, uint32_t dl) {
+                    auto coef_of = [&](int32_t e) {
+                        int lo = 0, hi = 65;
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if ((int32_t)tb.start[mid] <= e)
+                                lo = mid;
+                            else
+                                hi = mid;
+                        }
+                        return tb.coef[min(lo, 63)];
+                    };
+                    auto lazy_v = [&](uint32_t w, uint32_t dl, float c) {
                         uint32_t tfv, len;
                         if (lz.packed) {
                             tfv = w & 0xffffu;
@@ -921,8 +924,8 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : (LAZY ? 3 : 4))
                                             : lz.k1f * kd;
                         return entry_score(lz.variant, (float)tfv, a, c, lz.kc);
                     };
-                    v0 = lazy_v(pe.y, dl0);
-                    v1 = lazy_v(pe.w, dl1);
+                    v0 = lazy_v(pa.y, dl0, coef_of(ea));
+                    v1 = lazy_v(pb.y, dl1, coef_of(eb));
                 }
                 // the sums before the adds (-0.0 where nothing was added)
                 const float o0 = atom_add_if(acc, dl0, wdu, v0);
