@@ -405,12 +405,13 @@ struct __align__(16) SegTable {
 
 constexpr int32_t kModeList = 0;   // first touches listed, claimed after the scatter
 constexpr int32_t kModeCross = 1;  // threshold crossings listed, the tile reset in bulk
+constexpr int32_t kModeEnd = 3;    // no item: the CTA's work is done
 
 struct __align__(16) StageHdr {
     int32_t n;       // entries in the buffer
     int32_t last;    // 1: the item's last buffer
-    int32_t mode;    // kModeList or kModeCross (the same for all buffers of an item)
-    int32_t tile, qi;        // the item's doc tile and query record
+    int32_t mode;    // kModeList or kModeCross (the same for all buffers of an item), or kModeEnd
+    int32_t item, qi;        // the item (doc tile * n_long + query record) and its query record
     uint32_t kp, post, tau;  // the query's k', postings, threshold when staged
 };
 
@@ -619,7 +620,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : (LAZY ? 3 : 4))
     k_tile_staged(int64_t n_docs, const uint2* __restrict__ posts, const uint32_t* __restrict__ seg,
                   int32_t W, int32_t n_tiles, int32_t kstride, const int4* __restrict__ lrec,
                   const uint32_t* __restrict__ lpost, const uint32_t* __restrict__ ctr,
-                  uint32_t* __restrict__ thresh, uint32_t* __restrict__ tcount,
+                  uint32_t* queue, uint32_t* __restrict__ thresh, uint32_t* __restrict__ tcount,
                   u64* __restrict__ cand, int* __restrict__ status, int wait_polls,
                   int n_stages, int stage_entries, uint32_t tl_cap, LazyArgs lz)
 {
@@ -656,29 +657,30 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : (LAZY ? 3 : 4))
     }
     __syncthreads();
     const volatile uint32_t* abort_flag = &sh.abort_flag;
-    // tile-major items: item = tile * nq + q; (tile, q) advance by the grid
-    // stride without dividing
-    const int32_t step_t = (int32_t)(gridDim.x / nq), step_q = (int32_t)(gridDim.x % nq);
-    auto advance = [&](int32_t& t, int32_t& qq) {
-        t += step_t;
-        qq += step_q;
-        if (qq >= nq) {
-            qq -= nq;
-            t++;
-        }
-    };
+    // Tile-major items (item = tile * nq + q) from a work queue: CTA b starts
+    // with item b, then takes the next unclaimed one, G + (*queue)++, so that
+    // CTAs that drew cheap items take more of them and all finish together.
     const int64_t per = (int64_t)n_tiles + 1;
 
     if (warp == CW) {
         // ================================ producer ================================
-        // Loads run one item (segments, threshold) and two items (records)
-        // ahead of the item being staged.
-        int32_t t0 = (int32_t)(blockIdx.x / nq), q0 = (int32_t)(blockIdx.x % nq);
-        int32_t t1 = t0, q1 = q0;
-        advance(t1, q1);
-        int32_t t2 = t1, q2 = q1;
-        advance(t2, q2);
+        // Items are claimed two ahead of the one being staged; loads run one
+        // item (segments, threshold) and two items (records) ahead of it.
+        // Once the queue is empty the warp stages one fill of kModeEnd.
         const int32_t G = (int32_t)gridDim.x;
+        auto claim = [&]() -> int32_t {  // n_items when none is left
+            uint32_t v = 0u;
+            if (lane == 0)
+                v = atomicAdd(queue, 1u);
+            v = __shfl_sync(0xffffffffu, v, 0);
+            return (int64_t)G + v < (int64_t)n_items ? G + (int32_t)v : n_items;
+        };
+        int32_t it0 = (int32_t)blockIdx.x;
+        int32_t it1 = claim();
+        int32_t it2 = claim();
+        int32_t t0 = it0 / nq, q0 = it0 - t0 * nq;
+        int32_t t1 = it1 / nq, q1 = it1 - t1 * nq;
+        int32_t t2 = it2 / nq, q2 = it2 - t2 * nq;
         auto load_pair = [&](int32_t t_, int4 r_, uint32_t* lo, uint32_t* hi) {
 #pragma unroll
             for (int h = 0; h < 2; h++) {
@@ -692,7 +694,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : (LAZY ? 3 : 4))
         };
         int4 rec0 = lrec[q0];
         int4 rec1 = make_int4(0, 0, 0, 0), rec2 = make_int4(0, 0, 0, 0);
-        if ((int64_t)blockIdx.x + G < n_items)
+        if (it1 < n_items)
             rec1 = lrec[q1];
         uint32_t lo0[2], hi0[2];
         load_pair(t0, rec0, lo0, hi0);
@@ -701,10 +703,10 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : (LAZY ? 3 : 4))
         int s = 0;
         uint32_t round = 0;
         bool aborted = false;
-        for (int32_t item = blockIdx.x; item < n_items; item += G) {
+        while (it0 < n_items) {
             // next items' loads (consumed in the next iteration)
-            const bool has1 = (int64_t)item + G < n_items;
-            const bool has2 = (int64_t)item + 2 * (int64_t)G < n_items;
+            const bool has1 = it1 < n_items;
+            const bool has2 = it2 < n_items;
             if (has2)
                 rec2 = lrec[q2];
             uint32_t lo1[2] = {0u, 0u}, hi1[2] = {0u, 0u}, tau1 = 0u, post1 = 0u;
@@ -786,7 +788,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : (LAZY ? 3 : 4))
                         // a sum can cross the threshold only once when it only grows
                         hd.mode = (tau0 > kZeroKey && !(rec0.w & kNegScores)) ? kModeCross
                                                                               : kModeList;
-                        hd.tile = t0;
+                        hd.item = it0;
                         hd.qi = q0;
                         hd.kp = (uint32_t)(rec0.w & kKpMask);
                         hd.post = post0;
@@ -822,11 +824,36 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : (LAZY ? 3 : 4))
             hi0[1] = hi1[1];
             tau0 = tau1;
             post0 = post1;
+            it0 = it1;
             t0 = t1;
             q0 = q1;
+            it1 = it2;
             t1 = t2;
             q1 = q2;
-            advance(t2, q2);
+            it2 = claim();
+            t2 = it2 / nq;
+            q2 = it2 - t2 * nq;
+        }
+        if (!aborted) {  // the end: a fill without postings that names no item
+            if (!warp_wait(&sh.empty[s], (round & 1u) ^ 1u, abort_flag, wait_polls)) {
+                if (lane == 0) {
+                    set_status(status, BM25_E_TIMEOUT);
+                    *(volatile uint32_t*)&sh.abort_flag = 1u;
+                }
+            } else {
+                if (lane == 0) {
+                    StageHdr& hd = sh.hdr[s];
+                    hd.n = 0;
+                    hd.last = 1;
+                    hd.mode = kModeEnd;
+                    mbar_arrive_expect_tx(&sh.full[s], 0u);
+                }
+                __syncwarp();
+                if (++s == n_stages) {
+                    s = 0;
+                    round++;
+                }
+            }
         }
         // The copies of the last fill of every stage have landed before the
         // warp leaves, also after giving up (an earlier fill of a stage
@@ -850,8 +877,9 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : (LAZY ? 3 : 4))
     bool aborted = false;
     auto csync = [] { consumer_sync<NT>(); };
     const uint32_t ltmask = lanemask_lt();
-    for (int32_t item = blockIdx.x; item < n_items; item += gridDim.x, par ^= 1u) {
-        int32_t tile = 0, qi = 0, mode = kModeList;
+    for (;; par ^= 1u) {
+        int32_t item = 0, tile = 0, qi = 0, mode = kModeList;
+        bool done = false;
         uint32_t qkp = 1, post = 0, tau = 0;
         uint32_t d0u = 0, wdu = 0;
         float tau_f = 0.0f;
@@ -872,8 +900,13 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : (LAZY ? 3 : 4))
             const int2 nl = *reinterpret_cast<const int2*>(&hd.n);  // entries, last fill
             if (first_fill) {  // the item's fields, the same in all its fills
                 first_fill = false;
-                tile = hd.tile;
+                if (hd.mode == kModeEnd) {  // (the same fill for every consumer warp)
+                    done = true;
+                    break;
+                }
+                item = hd.item;
                 qi = hd.qi;
+                tile = (item - qi) / nq;
                 qkp = hd.kp;
                 post = hd.post;
                 tau = hd.tau;
@@ -966,6 +999,8 @@ __global__ void __launch_bounds__((CW + 1) * 32, CW >= 16 ? 2 : (LAZY ? 3 : 4))
             if (nl.y != 0)
                 break;
         }
+        if (done)
+            return;
         // every posting added, every first touch (crossing) listed; if any
         // consumer warp gave up, all of them leave here together, so that no
         // warp waits at a later barrier for one that left
@@ -2070,7 +2105,8 @@ int retrieve_device(const bm25_index* ix, bm25_workspace* ws, const int32_t* q_t
             tile_kernel<<<g2, tile_threads, smem, s>>>(
                 N, lazy ? ix->posts_lazy : ix->posts, reinterpret_cast<const uint32_t*>(ws->seg),
                 W, n_tiles, kstride,
-                ws->lrec, ws->lpost, ws->ctr, ws->thresh, ws->tcount, ws->cand, ix->status,
+                ws->lrec, ws->lpost, ws->ctr, ws->ctr + 3, ws->thresh, ws->tcount, ws->cand,
+                ix->status,
                 handshake_polls(), plan.stages, plan.stage_entries, tl_cap, lz);
         }
         count_launch();
