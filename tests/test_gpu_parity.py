@@ -458,6 +458,10 @@ def test_merge_tree_for_large_k(torch_dev, k):
                                 q_k=_to(torch_dev, ks))
     ix.sync_status()
     _check_rows(ids.cpu().numpy(), sc.cpu().numpy(), orc, q, ks, c.n_docs, f"tree per-k k={k}")
+    if k == 2500:  # past the largest k' (BM25_MAX_K = 4096) the call is refused on the host
+        from paper_2407_03618_gb300 import bm25
+        with pytest.raises(bm25.BM25Error):
+            ix.retrieve(_to(torch_dev, q.tokens), _to(torch_dev, q.offsets), 4097)
     ix.close()
 
 
