@@ -305,12 +305,15 @@ def read_traffic(path, stamp, workload, plan):
         return None
 
 
-def kernel_bytes(name, ctx):
-    """Algorithmic bytes per launch of the kernels a roofline is quoted for."""
+def kernel_bytes(name, ctx, launches_per_step=1.0):
+    """Algorithmic bytes per launch of the kernels a roofline is quoted for.
+    The retrieval kernels' bytes are those of the whole batch, which a call
+    splits into launches_per_step sub-batches when the tile candidates of
+    all its queries do not fit the candidate budget."""
     if name == "k_tile_staged":
-        return ctx["tile_bytes"]
+        return ctx["tile_bytes"] / max(launches_per_step, 1.0)
     if name == "k_dense_topk":
-        return ctx["dense_bytes"]
+        return ctx["dense_bytes"] / max(launches_per_step, 1.0)
     if name == "k_radix_downsweep":
         return 16 * ctx["n_tokens"]  # read key + doc, write key + doc, 4 B each
     if name == "k_radix_upsweep":
@@ -483,7 +486,7 @@ def extras(args, line, bm25, corpus, queries, tok, off, qt, qo, ids, sc, dev, pr
     top = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
 
     def roofline_for(name, c, t):
-        b = kernel_bytes(name, ctx)
+        b = kernel_bytes(name, ctx, c / max(args.steps, 1))
         if b is None:
             return None
         avg_s = t / c / 1e3

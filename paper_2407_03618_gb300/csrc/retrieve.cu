@@ -11,9 +11,10 @@
 //                     first posting of the token's column at or past the
 //                     boundary (binary search: doc ids ascend in a column),
 //                     as a slot of the packed (doc, score) layout
-//   R2 k_tile_staged  persistent CTAs over (doc tile, query) items: a
-//                     producer warp stages each item's posting segments into
-//                     shared memory with bulk asynchronous copies; consumer
+//   R2 k_tile_staged  persistent CTAs over (doc tile, query) items taken from
+//                     a device work queue: a producer warp stages each
+//                     item's posting segments into shared memory with
+//                     bulk asynchronous copies; consumer
 //                     warps scatter-add them into the tile's FP32
 //                     accumulators, claim each touched document once, keep
 //                     the ones that clear the query's running threshold and
@@ -1290,10 +1291,10 @@ __device__ void finish_row(u64* sel, int sz, uint32_t kp, int32_t kout, double s
 // most), keeps their k' best (all of them when there are no more than k')
 // and writes them, with their count, to the slots of the group's first
 // tile.  The next level, or k_merge, then reads the tiles at stride
-// tstride * fan.  A group of one tile is left as it is.  Any k' keys of a
-// query's candidates that are not among its k' best stay out of the final
-// selection either way, so the result is the one selection over all of
-// them would give.
+// tstride * fan.  A group of one tile is left as it is.  A key left out of
+// its group's k' best has k' keys above it and so is not among the query's
+// k' best either: the result is the one selection over all the candidates
+// would give.
 __global__ void __launch_bounds__(kMergeThreads)
     k_merge_level(u64* __restrict__ cand, uint32_t* __restrict__ tcount,
                   const int4* __restrict__ lrec, const uint32_t* __restrict__ ctr,
