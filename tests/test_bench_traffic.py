@@ -81,3 +81,16 @@ def test_code_stamp_ignores_include_paths(monkeypatch):
     assert build_ext.code_stamp() == s0
     monkeypatch.setattr(build_ext, "NVCC_FLAGS", flags + ["-DX=1"])
     assert build_ext.code_stamp() != s0
+
+
+def test_kernel_bytes_per_launch_of_a_split_call():
+    """A retrieval call split into sub-batches launches the tile and dense
+    kernels once per sub-batch: each launch moves its share of the batch's
+    algorithmic bytes.  The sort's passes each move all tokens."""
+    ctx = {"tile_bytes": 1000, "dense_bytes": 300, "n_tokens": 10, "nnz": 7}
+    assert bench.kernel_bytes("k_tile_staged", ctx) == 1000
+    assert bench.kernel_bytes("k_tile_staged", ctx, 2.0) == 500
+    assert bench.kernel_bytes("k_dense_topk", ctx, 3.0) == 100
+    assert bench.kernel_bytes("k_radix_downsweep", ctx, 3.0) == 160
+    assert bench.kernel_bytes("k_score", ctx, 1.0) == 140
+    assert bench.kernel_bytes("k_merge", ctx) is None
